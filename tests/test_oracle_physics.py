@@ -1,0 +1,205 @@
+"""Physics pins of the oracle's whole time step: closed-form solutions the
+paper's model must reproduce in its limits (Darcy's law, two-phase fractional
+flow, Poiseuille flow, hydrostatic balance, Young-Laplace jump, the
+gravity-capillary equilibrium of section 4.1.3), plus the invariants of the
+saturation update (exact conservation, boundedness) and the interface
+compression of Eq. 22."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.api import OracleSim
+from paper_2003_08374_gb300 import workloads as W
+
+
+def make_case(nx, ny, nz, h, phi, k, alpha, **kw):
+    c = W.Case(name="pin", nx=nx, ny=ny, nz=nz, h=h, **kw)
+    c.porosity = np.ascontiguousarray(np.broadcast_to(phi, (nx * ny * nz,)), dtype=float)
+    c.permeability = np.ascontiguousarray(np.broadcast_to(k, (nx * ny * nz,)), dtype=float)
+    c.alpha = np.ascontiguousarray(np.broadcast_to(alpha, (nx * ny * nz,)), dtype=float)
+    W._zero_fields(c)
+    return c
+
+
+def test_darcy_block_pressure_drop():
+    """Single-phase flow through a uniform porous block: dp/dx = -mu u / k (Darcy's law, the
+    porous limit of Eq. 21 with Eq. 42).  The 1-row channel's wall shear adds 4 mu/h^2 to the
+    drag, 4e-6 of mu/k here."""
+    nx, h, u, k, mu = 40, 1e-3, 1e-4, 1e-12, 1e-3
+    c = make_case(nx, 1, 1, h, 0.5, k, 1.0, inlet_u=u, p_tol=1e-13, max_cg=500, mu_l=mu, dt=1e-3)
+    W._plug_flow(c, u)
+    s = OracleSim(c)
+    s.step(2)
+    p = s.fields()["p"]
+    x = (np.arange(nx) + 0.5) * h
+    expect = mu * u / k * (nx * h - x)
+    assert np.max(np.abs(p - expect)) <= 1e-4 * expect.max()
+
+
+def test_two_phase_fractional_flow_and_mobility():
+    """Uniform saturation 0.5 in a porous block (Brooks-Corey m=2: k_rl = k_rg = 1/4):
+    dp/dx = -u/M with M = k0 (k_rl/mu_l + k_rg/mu_g) (Eq. 42), and the liquid flux across a
+    face equals u f_w with f_w = M_l/M = mu_g/(mu_l + mu_g) (Buckley-Leverett fractional flow,
+    carried by the porous relative velocity of Eq. 34)."""
+    nx, h, u, k = 40, 1e-3, 1e-4, 1e-12
+    mu_l, mu_g = 1e-3, 1.8e-5
+    c = make_case(nx, 1, 1, h, 0.5, k, 0.5, inlet_u=u, inlet_alpha=0.5, p_tol=1e-13,
+                  max_cg=500, mu_l=mu_l, mu_g=mu_g, dt=1e-4, kr_m=2.0)
+    W._plug_flow(c, u)
+    s = OracleSim(c)
+    s.step(2)
+    p = s.fields()["p"]
+    M = k * 0.25 * (1 / mu_l + 1 / mu_g)
+    mid = slice(nx // 4, 3 * nx // 4)
+    dpdx = np.diff(p)[mid] / h
+    assert np.allclose(dpdx, -u / M, rtol=1e-4)
+    flux = (s.array("FLOx") + s.array("AFx"))[nx // 4: 3 * nx // 4]
+    fw = mu_g / (mu_l + mu_g)
+    assert np.allclose(flux, u * h * h * fw, rtol=1e-6)
+
+
+def _poiseuille(ny, steps=600):
+    nx = 4 * ny
+    c = make_case(nx, ny, 1, 1.0, 1.0, 0.0, 1.0, rho_l=1.0, mu_l=1.0, rho_g=1.0, mu_g=1.0,
+                  inlet_u=1.0, dt=0.5, p_tol=1e-12, max_cg=500, mom_sweeps=4)
+    W._plug_flow(c, 1.0)
+    s = OracleSim(c)
+    s.step(steps)
+    f = s.fields()
+    p = f["p"].reshape(ny, nx)
+    ux = f["ux"].reshape(ny, nx + 1)
+    H = float(ny)
+    G = -np.mean(np.diff(p[:, 3 * nx // 4: nx - 2], axis=1))
+    y = np.arange(ny) + 0.5
+    prof = ux[:, 3 * nx // 4]
+    exact = 6.0 * y * (H - y) / H ** 2
+    return G, 12.0 / H ** 2, np.max(np.abs(prof - exact)) / 1.5
+
+
+def test_poiseuille_channel():
+    """Solid-free channel (Navier-Stokes limit of Eq. 21): developed profile
+    u = 6 U y (H - y)/H^2 and pressure gradient 12 mu U / H^2, with second-order
+    convergence of the profile error."""
+    G16, G16x, e16 = _poiseuille(16)
+    G8, G8x, e8 = _poiseuille(8, steps=300)
+    assert G16 == pytest.approx(G16x, rel=1e-2)
+    assert e16 < 1e-2
+    assert e8 / e16 > 3.0  # second order: ratio 4 expected
+
+
+def test_hydrostatic_rest():
+    """Two fluid layers at rest under gravity with an open top: the face-based (balanced)
+    gravity keeps u = 0 (to the pressure solver's tolerance; the velocity scale is
+    g dt = 1e-3 m/s) and p_{j+1} - p_j = h rho_f g exactly.  Surface tension is off: a flat
+    but numerically sharp interface gives CSF parasitic currents, a property of Eq. 27."""
+    nx, ny, h = 8, 12, 1e-3
+    alpha = np.zeros((ny, nx))
+    alpha[:6] = 1.0
+    c = make_case(nx, ny, 1, h, 1.0, 0.0, alpha.ravel(), g=(0.0, -9.81, 0.0),
+                  bc=(W.WALL, W.WALL, W.WALL, W.OUTLET, W.WALL, W.WALL), inlet_u=0.0,
+                  dt=1e-4, p_tol=1e-13, max_cg=500, sigma=0.0)
+    s = OracleSim(c)
+    s.step(5)
+    f = s.fields()
+    umax = max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max())
+    assert umax < 1e-8
+    p = f["p"].reshape(ny, nx)
+    rho = np.where(alpha > 0.5, 1000.0, 1.0)
+    dp = np.diff(p, axis=0)
+    expect = h * 0.5 * (rho[1:] + rho[:-1]) * -9.81
+    assert np.max(np.abs(dp - expect)) <= 1e-10 * np.abs(expect).max()
+
+
+def _disk_fraction(n, R, h, sub=8):
+    c = np.zeros((n, n))
+    off = (np.arange(sub) + 0.5) / sub
+    for a in off:
+        for b in off:
+            x = np.arange(n)[None, :] + a - n / 2
+            y = np.arange(n)[:, None] + b - n / 2
+            c += (x * x + y * y <= R * R)
+    return c / sub ** 2
+
+
+def test_young_laplace_jump():
+    """Static 2-D drop: p_in - p_out = sigma / R (CSF of Eq. 27 with the physical sign, R2)."""
+    n, R, h, sigma = 48, 12.0, 1e-4, 0.07
+    a = _disk_fraction(n, R, h)
+    c = make_case(n, n, 1, h, 1.0, 0.0, a.ravel(), rho_l=1000.0, rho_g=1000.0, mu_l=1e-3,
+                  mu_g=1e-3, sigma=sigma, bc=(W.WALL, W.WALL, W.WALL, W.OUTLET, W.WALL, W.WALL),
+                  inlet_u=0.0, dt=1e-5, p_tol=1e-12, max_cg=500, theta_deg=90.0)
+    s = OracleSim(c)
+    s.step(10)
+    p = s.fields()["p"].reshape(n, n)
+    yy, xx = np.mgrid[0:n, 0:n] + 0.5 - n / 2
+    r = np.sqrt(xx * xx + yy * yy)
+    dp = p[r < R - 3].mean() - p[r > R + 3].mean()
+    assert dp == pytest.approx(sigma / (R * h), rel=0.05)
+
+
+def _bc_alpha_of_pc(pc, p0=100.0, beta=0.5):
+    return (pc / p0) ** (-1.0 / beta)
+
+
+def test_gravity_capillary_equilibrium_column():
+    """Section 4.1.3, Eqs. 55-56: a porous column at capillary-gravity equilibrium,
+    dp_c/dy = (rho_g - rho_l) g_y, stays at rest: the porous capillary force (Eq. 38), the
+    relative velocity (Eq. 34) and the mobility-weighted density (Eq. 45) balance.  A sign
+    error in any of them drives Darcy velocities of order k0 (rho_l - rho_g) g / mu_l."""
+    ny, L = 64, 0.02
+    h = L / ny
+    k0, rho_l, rho_g, g = 1e-11, 1000.0, 1.0, 9.81
+    y = (np.arange(ny) + 0.5) * h
+    pc = 100.0 / math.sqrt(0.9) + (rho_l - rho_g) * g * y
+    alpha = _bc_alpha_of_pc(pc)
+    c = make_case(1, ny, 1, h, 0.5, k0, alpha, rho_l=rho_l, rho_g=rho_g, mu_l=1e-3,
+                  mu_g=1.8e-5, g=(0.0, -g, 0.0), kr_m=3.0, pc0=100.0, pc_beta=0.5, pc_eps=1e-6,
+                  bc=(W.WALL, W.WALL, W.WALL, W.OUTLET, W.WALL, W.WALL), inlet_u=0.0,
+                  dt=1e-3, p_tol=1e-13, max_cg=500)
+    s = OracleSim(c)
+    s.step(1)  # the first step starts from p = 0 and projects it to equilibrium
+    a1 = s.fields()["alpha"]
+    s.step(3)
+    Ug = k0 * (rho_l - rho_g) * g / 1e-3
+    f = s.fields()
+    assert np.abs(f["uy"]).max() < 1e-9 * Ug
+    rel_flux = np.abs(s.array("AFy")) / (h * h)
+    assert rel_flux.max() < 1e-3 * Ug
+    assert np.abs(f["alpha"] - a1).max() < 1e-6
+
+
+def test_alpha_conservation_and_bounds():
+    """Eq. 15 in conservative form: sum(phi alpha V) changes exactly by the boundary flux;
+    the flux-corrected update keeps alpha in [0, 1]."""
+    c = W.fracture_2d(nx=32, ny=24, p_tol=1e-10)
+    s = OracleSim(c)
+    m0 = s.stats()["mass"]
+    for _ in range(20):
+        s.step(1)
+        st = s.stats()
+        assert abs(st["mass"] - m0 - st["boundary_in"]) <= 1e-12 * m0
+        assert st["alpha_min"] >= -1e-12 and st["alpha_max"] <= 1 + 1e-12
+
+
+def _front_width(c_alpha):
+    nx = 80
+    alpha = np.zeros(nx)
+    alpha[:10] = 1.0
+    c = make_case(nx, 1, 1, 1e-4, 1.0, 0.0, alpha, rho_g=1000.0, mu_g=1e-3, inlet_u=0.1,
+                  c_alpha=c_alpha, dt=2e-4, p_tol=1e-12, sigma=0.0)
+    W._plug_flow(c, 0.1)
+    s = OracleSim(c)
+    s.step(200)
+    a = s.fields()["alpha"]
+    return int(np.sum((a > 1e-3) & (a < 1 - 1e-3))), a
+
+
+def test_interface_compression_sharpens():
+    """Eq. 22 with the sign of Eq. 41 (R3): with C_alpha = 1 an advected step stays within a
+    few cells; without compression it spreads."""
+    w1, a1 = _front_width(1.0)
+    w0, a0 = _front_width(0.0)
+    assert w1 <= 4 and w0 > w1, (w1, w0)
+    # the front sits where the volume says: 10 + u t / h = 10 + 0.1*0.04/1e-4 = 50 cells
+    assert a1.sum() == pytest.approx(50.0, abs=1e-9)
