@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 micro-continuum DBS-VOF time step (cell-steps/s).
+
+Default workload: the 3-D 128^3 fractured porous block (log-normal
+permeability, Gaussian random field with correlation length 8 cells,
+sigma_lnk 1, mean k 1e-13 m^2, porosity 0.2-0.6 tied to k, a 6-cell solid-free
+fracture, water injected into oil with viscosity ratio 10, gravity on),
+pressure residual 1e-8, FP64 (value) and the FP32-preconditioned variant
+(``mixed``).  A step is one full pressure-velocity step (saturation update,
+properties, momentum predictor, two PISO correctors with GMG-PCG).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the workload:
+the single-domain step has no data-parallel split, so the GPUs run
+independent replicas (weak scaling) and the job throughput is the sum.
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
+workload (a 16-layer slab), on rank 0 only.
+"""
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "cell-steps/s FP64 vs mixed precision at 1e-8 residual; p50/p99 request latency"
+UNIT = "cell-steps/s"
+DOMINANT = "smooth_fine"  # red-black Gauss-Seidel half sweep on the finest level
+SLAB = (56, 72)  # z layers of the bounded CPU sample
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="mdbs", choices=["mdbs", "reference"])
+    ap.add_argument("--n", type=int, default=128, help="cells per axis of the workload")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    from paper_2003_08374_gb300 import workloads as W
+    return W.grf_3d(n=n, seed=2, p_tol=1e-8, max_cg=200)
+
+
+def slab_of(case):
+    """Layers SLAB of the workload as a stand-alone case (same recipe, same fields)."""
+    from paper_2003_08374_gb300 import workloads as W
+    z0, z1 = SLAB
+    nx, ny, nz = case.nx, case.ny, case.nz
+    z0, z1 = min(z0, nz - 1), min(z1, nz)
+    s = case.replace(nz=z1 - z0, name=case.name + "_slab%d_%d" % (z0, z1))
+    cut = lambda a: a.reshape(nz, ny, nx)[z0:z1].ravel().copy()
+    s.porosity, s.permeability, s.alpha, s.p = (cut(a) for a in (case.porosity, case.permeability,
+                                                                 case.alpha, case.p))
+    W._zero_fields(s)
+    s.ux[:] = case.inlet_u
+    return s
+
+
+def time_oracle(case, steps, warmup):
+    from oracle.api import OracleSim
+    o = OracleSim(case)
+    for _ in range(warmup):
+        o.step(1)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(1)
+    dt = time.perf_counter() - t0
+    return case.cells * steps / dt, dt
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def reference_arm(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    case = workload(args.n)
+    sample = slab_of(case)
+    value, secs = time_oracle(sample, args.steps, args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": case.name + " (FP64 CPU oracle, bounded sample)", "cells": sample.cells,
+                   "p_tol": case.p_tol},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "%d oracle steps on z-layers %d-%d (%dx%dx%d cells) of the %s workload"
+                                   % (args.steps, SLAB[0], SLAB[1], sample.nx, sample.ny, sample.nz, case.name)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[5 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("pressure.cu", "mdbs_internal.cuh"):
+        h.update(open(os.path.join(ROOT, "paper_2003_08374_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:12]
+
+
+def measured_traffic(kernel, precision_tag, cells):
+    """DRAM bytes per launch from the committed ncu summary, scaled to `cells`, if the kernel
+    source is unchanged since the capture; else None."""
+    path = os.path.join(ROOT, "profiles", "%s_%s.md" % (kernel, precision_tag))
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    kv = {}
+    for line in txt.splitlines():
+        if ":" in line and line.strip().startswith("- "):
+            k, v = line.strip()[2:].split(":", 1)
+            kv[k.strip()] = v.strip().strip("`")
+    if kv.get("source_hash") != kernel_source_hash():
+        return None
+    try:
+        per_cell = float(kv["dram_bytes_per_launch"]) / float(kv["cells"])
+    except (KeyError, ValueError):
+        return None
+    return per_cell * cells
+
+
+def gpu_arm(args):
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2003_08374_gb300.build import build_library
+    build_library()
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(sim, steps, warmup, profile_kernel=None):
+        for _ in range(warmup):
+            sim.step(1)
+        if profile_kernel:
+            sim.profile(True, only=profile_kernel)
+        l0 = sim.stats()["kernel_launches"]
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local) as clk:
+            e0.record(stream)
+            for _ in range(steps):
+                sim.step(1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = sim.profile_read() if profile_kernel else {}
+        if profile_kernel:
+            sim.profile(False)
+        st = sim.stats()
+        return ms, prof, clk.summary(), st["kernel_launches"] - l0, st
+
+    case = workload(args.n)
+    sim = mdbs.Simulation(case)
+    sim.set_stream(stream.cuda_stream)
+    ms, prof, clocks, launches, st = timed(sim, args.steps, args.warmup, DOMINANT)
+    ms = max_over_ranks(ms)
+    value = case.cells * args.steps * world / (ms / 1e3)
+    cg_iters = st["cg_iters"]
+
+    # roofline of the dominant kernel: finest-level RBGS half sweep, FP64.
+    # algorithmic bytes per launch: b, diag, own x written and neighbour x read on half the
+    # cells (4 x 8 B / 2) plus the three face-coefficient arrays read in full (3 x 8 B).
+    alg_bytes = (4 * 8 / 2 + 3 * 8) * case.cells
+    pk = peaks()
+    roof = None
+    if DOMINANT in prof:
+        tot_ms, cnt = prof[DOMINANT]
+        avg_s = tot_ms / cnt / 1e3
+        achieved = alg_bytes / avg_s / 1e9
+        peak = pk["hbm_gbs"] if pk else 6800.0
+        traffic = measured_traffic(DOMINANT, "fp64_grf128", case.cells)
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": DOMINANT, "launches": cnt, "avg_us": avg_s * 1e6,
+                "alg_bytes_per_launch": alg_bytes,
+                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6800 GB/s"}
+
+    mixed = None
+    if not args.no_mixed:
+        mcase = case.replace(precision=W.MIXED)
+        msim = mdbs.Simulation(mcase)
+        msim.set_stream(stream.cuda_stream)
+        mms, _, _, _, mst = timed(msim, args.steps, args.warmup)
+        mms = max_over_ranks(mms)
+        mval = case.cells * args.steps * world / (mms / 1e3)
+        mixed = {"value": mval, "ms_per_step": mms / args.steps, "speedup_vs_fp64": mval / value,
+                 "cg_iters_last_step": mst["cg_iters"]}
+        msim.close()
+
+    # end to end through the public API with host buffers: each step copies the state in
+    # from pinned host memory (mdbs_set_fields), steps, and reads it back (mdbs_get_fields)
+    pin = lambda n: torch.empty(n, dtype=torch.float64, pin_memory=True).numpy()
+    host = {k: pin(v.size) for k, v in sim.fields().items() if v.size}
+    for k, v in sim.fields().items():
+        if v.size:
+            host[k][:] = v
+    nbytes = sum(v.nbytes for v in host.values())
+    lib = mdbs.lib()
+    P = mdbs._ptr
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        sim._check(lib.mdbs_set_fields(sim.h, P(host["alpha"]), P(host["ux"]), P(host["uy"]), P(host["uz"]),
+                                       P(host["p"])))
+        sim.step(1)
+        sim._check(lib.mdbs_get_fields(sim.h, P(host["alpha"]), P(host["ux"]), P(host["uy"]), P(host["uz"]),
+                                       P(host["p"])))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ems = max_over_ranks(e0.elapsed_time(e1))
+    e2e = {"value": case.cells * args.steps * world / (ems / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
+    sim.close()
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        sample = slab_of(case)
+        cval, csec = time_oracle(sample, 2, 0)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "2 oracle steps on z-layers %d-%d (%dx%dx%d cells) of the workload, %.1f s"
+                         % (SLAB[0], SLAB[1], sample.nx, sample.ny, sample.nz, csec)}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": case.name, "cells": case.cells, "p_tol": case.p_tol, "n_corr": case.n_corr,
+                       "mom_sweeps": case.mom_sweeps, "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "inputs larger than L2 (%.1f GB device state)" % (mdbs.bytes_required(case) / 1e9),
+                       "cg_iters_last_step": cg_iters},
+            "mixed": mixed, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "gpu_launches": launches,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return gpu_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

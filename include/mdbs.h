@@ -1,0 +1,203 @@
+/*
+ * mdbs.h -- C-ABI of the GB300 micro-continuum multiphase Darcy-Brinkman-Stokes
+ * volume-of-fluid step (Carrillo, Bourg & Soulaine, "A micro-continuum
+ * approach for multiphase flow in hybrid-scale porous media", arXiv 2003.08374).
+ *
+ * One call of mdbs_step advances one or more pressure-velocity time steps of
+ * the model of section 2 (Eq. 21: total mass, saturation and momentum
+ * equations with the multiscale closures of section 2.3, Eqs. 41-45) by the
+ * solution algorithm of section 3.2: explicit flux-corrected saturation update,
+ * property update, momentum predictor (Eq. 50), PISO pressure correction
+ * (Eqs. 51-53).  Every step runs in CUDA kernels on the current device; there is
+ * no CPU path.
+ *
+ * Grid and layout.  Uniform Cartesian grid, spacing h, nx*ny*nz cells (nz == 1:
+ * two-dimensional run, no z faces).  Scalars (porosity, permeability, alpha, p)
+ * are cell-centred; velocities live on cell faces (staggered/MAC), so the face
+ * velocity times the face area is the conservative volumetric flux.  All host
+ * arrays are float64, x fastest:
+ *   cells   : nx*ny*nz         index i + nx*(j + ny*k)
+ *   x faces : (nx+1)*ny*nz     index i + (nx+1)*(j + ny*k), i in [0, nx]
+ *   y faces : nx*(ny+1)*nz     index i + nx*(j + (ny+1)*k)
+ *   z faces : nx*ny*(nz+1)     index i + nx*(j + ny*k)  (ignored when nz == 1)
+ * Face velocities are positive along +x, +y, +z.
+ *
+ * Boundaries.  Each of the six sides (x-, x+, y-, y+, z-, z+) is a no-slip
+ * wall, an inlet (normal velocity inlet_u into the domain, saturation
+ * inlet_alpha, zero normal pressure gradient) or an outlet (p = 0 on the face,
+ * zero normal gradient of velocity and saturation).  At least one side must be
+ * an outlet, which makes the pressure equation non-singular.
+ *
+ * Ownership.  The caller owns every host array; the library copies them in and
+ * out and keeps no pointer to them.  A simulation owns its device memory until
+ * mdbs_destroy.  Calls on one simulation are not thread safe.
+ *
+ * Errors.  Every int-returning call returns MDBS_OK (0) or a negative code; a
+ * message is kept per simulation (mdbs_last_error).  After MDBS_ERR_DIVERGED or
+ * MDBS_ERR_CUDA the fields hold the state reached when the error was found.
+ */
+#ifndef MDBS_H
+#define MDBS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MDBS_OK 0
+#define MDBS_ERR_ARG (-1)           /* bad size, pointer, option or field value */
+#define MDBS_ERR_OOM (-2)           /* device allocation failed */
+#define MDBS_ERR_CUDA (-3)          /* a CUDA call failed */
+#define MDBS_ERR_DIVERGED (-4)      /* a non-finite value appeared in the fields */
+#define MDBS_ERR_NOT_CONVERGED (-5) /* reserved: pressure solves that hit max_cg are counted in stats */
+
+#define MDBS_BC_WALL 0
+#define MDBS_BC_INLET 1
+#define MDBS_BC_OUTLET 2
+
+#define MDBS_BROOKS_COREY 0
+#define MDBS_VAN_GENUCHTEN 1
+
+#define MDBS_FP64 0        /* FP64 everywhere */
+#define MDBS_MIXED 1       /* FP32 multigrid preconditioner inside FP64 flexible CG */
+#define MDBS_MIXED_BF16 2  /* as MDBS_MIXED with coarse-level coefficients stored in BF16 */
+
+typedef struct {
+  int32_t nx, ny, nz; /* cells per axis; nz == 1 selects a 2-D run */
+  double h;           /* cell size [m] */
+} mdbs_grid;
+
+/* Fluid pair (Table 1): l = wetting liquid, g = non-wetting phase. */
+typedef struct {
+  double rho_l, mu_l, rho_g, mu_g; /* densities [kg/m^3], viscosities [Pa s] */
+  double sigma;                    /* interfacial tension [N/m] (Eq. 27) */
+  double g[3];                     /* gravity [m/s^2] */
+} mdbs_fluids;
+
+/* Relative permeability and capillary pressure closures (Appendix A, Table 2). */
+typedef struct {
+  int32_t kr_model, pc_model;  /* MDBS_BROOKS_COREY or MDBS_VAN_GENUCHTEN */
+  double kr_m;                 /* exponent m of the kr model */
+  double a_l_irr, a_g_irr;     /* irreducible saturations of the kr effective saturation */
+  double pc0, pc_beta, pc_m;   /* entry pressure [Pa], Brooks-Corey beta, Van Genuchten m */
+  double a_pc_irr, a_pc_max;   /* bounds of the p_c effective saturation */
+  double pc_eps;               /* the p_c effective saturation is clamped to [eps, 1-eps] */
+} mdbs_closures;
+
+typedef struct {
+  double dt;        /* time step [s] (the first one when cfl > 0) */
+  double cfl;       /* > 0: next dt = min(cfl h / max|u_f/phi_f|, 1.2 dt, dt_max) */
+  double dt_max;    /* upper bound of the adaptive time step */
+  double c_alpha;   /* interface compression coefficient C_alpha (Eq. 22) */
+  double p_tol;     /* pressure solve stops at ||b - A p||_2 <= p_tol ||b||_2 */
+  int32_t n_corr;   /* PISO correctors per step (section 3.2: at least 2) */
+  int32_t mom_sweeps; /* Jacobi sweeps of the momentum predictor */
+  int32_t max_cg;   /* CG iteration cap per pressure solve */
+  int32_t mg_nu1, mg_nu2;     /* red-black Gauss-Seidel pre/post sweep pairs per level */
+  int32_t mg_coarse_sweeps;   /* sweep pairs (forward, then as many backward) on the coarsest level */
+  int32_t precision;          /* MDBS_FP64, MDBS_MIXED or MDBS_MIXED_BF16 */
+  int32_t bc[6];              /* side types, order x-, x+, y-, y+, z-, z+ */
+  double inlet_u;             /* inlet normal velocity into the domain [m/s] */
+  double inlet_alpha;         /* inlet saturation */
+} mdbs_options;
+
+typedef struct {
+  int64_t steps;          /* steps taken since mdbs_set_fields */
+  double time;            /* simulated time [s] */
+  double dt;              /* time step of the next step [s] */
+  int32_t cg_iters[8];    /* CG iterations per corrector of the last step */
+  double cg_resid[8];     /* final relative residual per corrector of the last step */
+  int64_t cg_iters_total; /* since mdbs_set_fields */
+  int32_t not_converged;  /* pressure solves that stopped at max_cg */
+  double mass;            /* sum of porosity * alpha * cell volume [m^3] */
+  double boundary_in;     /* time-integrated net liquid volume entering through boundaries [m^3] */
+  double alpha_min, alpha_max;
+  int64_t kernel_launches; /* CUDA kernels this library launched since mdbs_set_fields */
+} mdbs_stats;
+
+typedef struct mdbs_sim mdbs_sim;
+
+/*
+ * Creates a simulation on the current CUDA device (problem statement of
+ * section 2: porosity field, Eqs. 7-8; absolute permeability k0, Eq. 30; fluid
+ * pair; contact angle, Eq. 40).
+ *   porosity     : host, nx*ny*nz, each in (0, 1]; exactly 1 marks a solid-free cell
+ *   permeability : host, nx*ny*nz, k0 [m^2] > 0 where porosity < 1 (ignored elsewhere)
+ *   contact_angle_deg : angle through the wetting phase at the free/porous interface
+ * Returns MDBS_ERR_ARG for invalid sizes or values, MDBS_ERR_OOM / MDBS_ERR_CUDA on
+ * device failure; *out is NULL then.  Velocities and pressure start at zero; call
+ * mdbs_set_fields before stepping.
+ */
+int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* permeability,
+                const mdbs_fluids* fluids, double contact_angle_deg, const mdbs_closures* closures,
+                const mdbs_options* options, mdbs_sim** out);
+
+/*
+ * Sets the state (saturation alpha_l in [0, 1], Eq. 8; face velocities, Eq. 10;
+ * pressure, Eq. 9) from host arrays laid out as above; uz may be NULL in 2-D.
+ * Wall and inlet face velocities are overwritten by their boundary values.
+ * Resets the statistics.  MDBS_ERR_ARG if alpha is outside [0, 1] or not finite.
+ */
+int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const double* uy,
+                    const double* uz, const double* p);
+
+/*
+ * Advances n >= 1 time steps (section 3.2).  Runs on the simulation's stream and
+ * returns after the last step has finished on the device.  MDBS_ERR_DIVERGED if
+ * a non-finite value appears.
+ */
+int mdbs_step(mdbs_sim* sim, int32_t n);
+
+/* Copies the state to host arrays (any pointer may be NULL to skip it). */
+int mdbs_get_fields(const mdbs_sim* sim, double* alpha, double* ux, double* uy, double* uz,
+                    double* p);
+
+/* Releases the device memory; NULL is accepted. */
+void mdbs_destroy(mdbs_sim* sim);
+
+/* ---------------- helpers ---------------- */
+
+/* Statistics of the last step (see mdbs_stats). */
+int mdbs_get_stats(const mdbs_sim* sim, mdbs_stats* out);
+
+/* Last error message of sim, or of the last failed mdbs_create when sim is NULL. */
+const char* mdbs_last_error(const mdbs_sim* sim);
+
+/* Runs the simulation's kernels on the given cudaStream_t (NULL: legacy default
+ * stream).  The caller keeps ownership of the stream. */
+int mdbs_set_stream(mdbs_sim* sim, void* cuda_stream);
+
+/* Device bytes mdbs_create allocates for this grid and precision. */
+size_t mdbs_bytes_required(const mdbs_grid* grid, int32_t precision);
+
+/*
+ * Per-kernel device timing (a measurement aid with no counterpart in the paper):
+ * when enabled, each launch of kernel only_id (every kernel when only_id is -1)
+ * is bracketed by CUDA events on the simulation's stream and the elapsed times
+ * are summed per kernel.  Enabling or disabling resets the sums.  Each timed
+ * launch adds two event records of host overhead.
+ */
+int mdbs_profile_enable(mdbs_sim* sim, int32_t enable, int32_t only_id);
+/* Number of kernel ids understood by mdbs_profile_read. */
+int32_t mdbs_profile_count(void);
+/* Name, summed device time [ms] and timed launches of kernel id since enabling
+ * (sim may be NULL to read the name only); MDBS_ERR_ARG for an id outside
+ * [0, mdbs_profile_count()). */
+int mdbs_profile_read(const mdbs_sim* sim, int32_t id, const char** name, double* total_ms, int64_t* launches);
+
+/*
+ * Copies an internal device array to host memory for inspection (names: "rho",
+ * "mu", "drag", "pc", "cf", "Ml", "Mg", "kappa", "mx", "my", "mz", "Tx", "Ty", "Tz",
+ * "Dd", "b", "aL", "Rp", "Rm", "aPx", "aPy", "aPz", "rhs0x", "rhs0y", "rhs0z", "Bx", "By",
+ * "Bz", "hbyax", "hbyay", "hbyaz", "FLOx", "FLOy", "FLOz", "AFx", "AFy", "AFz").
+ * Returns the element count (and copies min(count, capacity) values when out is
+ * not NULL), or MDBS_ERR_ARG for an unknown name.
+ */
+int64_t mdbs_debug_array(const mdbs_sim* sim, const char* name, double* out, int64_t capacity);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

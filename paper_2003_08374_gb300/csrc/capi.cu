@@ -1,0 +1,543 @@
+// capi.cu -- C-ABI of libmdbs (include/mdbs.h): device arena, field transfer and
+// the host-side orchestration of the time step of section 3.2.  Every numerical
+// step runs in the kernels of step_kernels.cu and pressure.cu.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include "../../include/mdbs.h"
+#include "mdbs_internal.cuh"
+
+using namespace mdbs;
+
+namespace mdbs {
+
+const char* const kKernelNames[K_COUNT] = {
+    "alpha_flux", "alpha_lo", "alpha_limit", "alpha_update", "finalize", "properties", "normals",
+    "curvature", "momentum_assemble", "jacobi", "hbya", "correct", "boundary", "field_stats", "cfl",
+    "static_geometry", "pressure_assemble", "diag", "convert", "coarsen", "smooth_fine", "smooth_coarse",
+    "zero", "restrict_fine", "restrict_coarse", "prolong_fine", "prolong_coarse", "cg_resid0",
+    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d"};
+
+// Per-simulation launch counter and optional event timer.
+struct Profiler {
+  bool on = false;
+  int only = -1;  // time only this kernel id (-1: all)
+  long long launches = 0;
+  std::vector<cudaEvent_t> pool;
+  size_t next = 0;
+  struct Rec {
+    int id;
+    size_t e0, e1;
+  };
+  std::vector<Rec> recs;
+  int open_id = -1;
+  size_t open_ev = 0;
+  double ms[K_COUNT] = {};
+  long long count[K_COUNT] = {};
+
+  size_t event(cudaStream_t s) {
+    if (next == pool.size()) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return (size_t)-1;
+      pool.push_back(e);
+    }
+    cudaEventRecord(pool[next], s);
+    return next++;
+  }
+  void resolve() {
+    if (recs.empty()) return;
+    cudaEventSynchronize(pool[recs.back().e1]);
+    for (const Rec& r : recs) {
+      float t = 0.f;
+      if (cudaEventElapsedTime(&t, pool[r.e0], pool[r.e1]) == cudaSuccess) {
+        ms[r.id] += t;
+        count[r.id] += 1;
+      }
+    }
+    recs.clear();
+    next = 0;
+  }
+  void reset() {
+    for (int i = 0; i < K_COUNT; i++) {
+      ms[i] = 0.0;
+      count[i] = 0;
+    }
+  }
+  ~Profiler() {
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+  }
+};
+
+static thread_local Profiler* g_active = nullptr;
+
+void prof_begin(int id, cudaStream_t s) {
+  Profiler* p = g_active;
+  if (!p) return;
+  p->launches++;
+  if (!p->on || (p->only >= 0 && p->only != id)) return;
+  p->open_id = id;
+  p->open_ev = p->event(s);
+}
+
+void prof_end(int id, cudaStream_t s) {
+  Profiler* p = g_active;
+  if (!p || !p->on || p->open_id != id || p->open_ev == (size_t)-1) return;
+  size_t e1 = p->event(s);
+  if (e1 != (size_t)-1) p->recs.push_back({id, p->open_ev, e1});
+  p->open_id = -1;
+}
+
+}  // namespace mdbs
+
+struct mdbs_sim {
+  Profiler prof;
+  Prm P;
+  Fld F;
+  mdbs_options opt;
+  int precision;
+  cudaStream_t stream;
+  void* arena;
+  size_t arena_bytes;
+  PressureSolver* ps;
+  double* partials;   // kMaxPartials * 4
+  double* scal;       // step scalars: 0 mass, 1 amin, 2 amax, 3 bad, 4 umax, 5 boundary_in
+  double* host_scal;  // pinned
+  double dt, time;
+  mdbs_stats st;
+  bool fields_set;
+  std::string err;
+};
+
+static thread_local std::string g_create_error;
+
+namespace {
+
+struct Activate {
+  Profiler* prev;
+  explicit Activate(mdbs_sim* s) : prev(g_active) { g_active = &s->prof; }
+  ~Activate() {
+    if (g_active && g_active->on) g_active->resolve();
+    g_active = prev;
+  }
+};
+
+size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+struct Layout {
+  long long cells, nf[3];
+  int dim;
+};
+
+Layout layout_of(const mdbs_grid* g) {
+  Layout L;
+  L.dim = g->nz == 1 ? 2 : 3;
+  L.cells = (long long)g->nx * g->ny * g->nz;
+  L.nf[0] = (long long)(g->nx + 1) * g->ny * g->nz;
+  L.nf[1] = (long long)g->nx * (g->ny + 1) * g->nz;
+  L.nf[2] = (long long)g->nx * g->ny * (g->nz + 1);
+  return L;
+}
+
+
+// carve the arena; base == nullptr only measures
+size_t carve(mdbs_sim* s, const Layout& L, char* base) {
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += a256(bytes);
+    return p;
+  };
+  auto cd = [&]() { return (double*)take(L.cells * 8); };
+  Fld F{};
+  F.phi = cd();
+  F.k0 = cd();
+  F.is_free = (uint8_t*)take(L.cells);
+  for (int e = 0; e < 3; e++) F.nw[e] = cd();
+  F.alpha = cd();
+  F.p = cd();
+  F.Ml = cd();
+  F.Mg = cd();
+  F.pc = cd();
+  F.cf = cd();
+  F.rho = cd();
+  F.rho_old = cd();
+  F.mu = cd();
+  F.drag = cd();
+  for (int e = 0; e < 3; e++) F.m[e] = cd();
+  F.kappa = cd();
+  F.aL = cd();
+  F.Rp = cd();
+  F.Rm = cd();
+  for (int e = 0; e < 3; e++) F.T[e] = cd();
+  F.Dd = cd();
+  F.diag = cd();
+  F.b = cd();
+  for (int d = 0; d < 3; d++) {
+    const long long nf = (d < L.dim) ? L.nf[d] : 1;
+    auto fd = [&]() { return (double*)take(nf * 8); };
+    F.u[d] = fd();
+    F.FLO[d] = fd();
+    F.AF[d] = fd();
+    F.aP[d] = fd();
+    F.anb[d] = (double*)take(6 * nf * 8);
+    F.rhs0[d] = fd();
+    F.B[d] = fd();
+    F.hbya[d] = fd();
+    F.utmp[d] = fd();
+  }
+  double* partials = (double*)take(4 * kMaxPartials * 8);
+  double* scal = (double*)take(16 * 8);
+  if (s) {
+    s->F = F;
+    s->partials = partials;
+    s->scal = scal;
+  }
+  return off;
+}
+
+int fail(mdbs_sim* s, int code, const std::string& msg) {
+  if (s)
+    s->err = msg;
+  else
+    g_create_error = msg;
+  return code;
+}
+
+int cuda_fail(mdbs_sim* s, cudaError_t e, const char* where) {
+  return fail(s, MDBS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(call)                                   \
+  do {                                             \
+    cudaError_t e_ = (call);                       \
+    if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
+  } while (0)
+
+int refresh_stats(mdbs_sim* s) {
+  launch_field_stats(s->P, s->F, s->partials, s->scal, s->stream);
+  CK(cudaMemcpyAsync(s->host_scal, s->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->st.kernel_launches = s->prof.launches;
+  s->st.mass = s->host_scal[0];
+  s->st.alpha_min = s->host_scal[1];
+  s->st.alpha_max = s->host_scal[2];
+  s->st.boundary_in = s->host_scal[5];
+  if (s->host_scal[3] != 0.0) return fail(s, MDBS_ERR_DIVERGED, "non-finite alpha or pressure");
+  return MDBS_OK;
+}
+
+int one_step(mdbs_sim* s) {
+  Prm& P = s->P;
+  Fld& F = s->F;
+  cudaStream_t st = s->stream;
+  const double dt = s->dt;
+  // 1. saturation (Eq. 15) by flux-corrected transport
+  launch_alpha_step(P, F, dt, s->partials, s->scal, 5, st);
+  // 3. properties at alpha^{k+1}; the old density stays for the Euler source (Eq. 46)
+  std::swap(F.rho, F.rho_old);
+  launch_properties(P, F, st);
+  // 4. momentum predictor (Eq. 50) from u^k and p^k
+  launch_momentum_assemble(P, F, dt, st);
+  for (int it = 0; it < s->opt.mom_sweeps; it++) {
+    launch_jacobi_sweep(P, F, st);
+    for (int d = 0; d < 3; d++) std::swap(F.u[d], F.utmp[d]);
+  }
+  // 5. PISO correctors (Eqs. 51-53)
+  for (int c = 0; c < s->opt.n_corr; c++) {
+    launch_hbya(P, F, st);
+    launch_pressure_assemble(P, F, st);
+    double res = 0.0;
+    int it = pressure_solve(s->ps, P, F, s->opt.p_tol, s->opt.max_cg, s->opt.mg_nu1, s->opt.mg_nu2,
+                            s->opt.mg_coarse_sweeps, &res, st);
+    if (it < 0) return cuda_fail(s, cudaGetLastError(), "pressure_solve");
+    if (c < 8) {
+      s->st.cg_iters[c] = it;
+      s->st.cg_resid[c] = res;
+    }
+    s->st.cg_iters_total += it;
+    if (!(res <= s->opt.p_tol)) s->st.not_converged++;
+    launch_correct(P, F, st);
+  }
+  CK(cudaGetLastError());
+  // 6. time step
+  s->time += dt;
+  s->st.steps++;
+  if (s->opt.cfl > 0.0) {
+    launch_cfl(P, F, s->partials, s->scal, st);
+    CK(cudaMemcpyAsync(s->host_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double umax = s->host_scal[4];
+    double dtn = umax > 0.0 ? s->opt.cfl * P.h / umax : s->opt.dt_max;
+    dtn = fmin(dtn, 1.2 * dt);
+    dtn = fmin(dtn, s->opt.dt_max);
+    s->dt = dtn;
+  }
+  s->st.time = s->time;
+  s->st.dt = s->dt;
+  return refresh_stats(s);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t mdbs_bytes_required(const mdbs_grid* grid, int32_t precision) {
+  if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return 0;
+  Layout L = layout_of(grid);
+  int n[3] = {grid->nx, grid->ny, grid->nz};
+  return carve(nullptr, L, nullptr) + pressure_bytes(n, precision == 0 ? 0 : 1);
+}
+
+int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* permeability,
+                const mdbs_fluids* fl, double contact_angle_deg, const mdbs_closures* cl,
+                const mdbs_options* op, mdbs_sim** out) {
+  mdbs_sim* s = nullptr;
+  if (!out) return fail(s, MDBS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!grid || !porosity || !permeability || !fl || !cl || !op) return fail(s, MDBS_ERR_ARG, "NULL argument");
+  if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->h > 0.0))
+    return fail(s, MDBS_ERR_ARG, "grid sizes must be >= 1 and h > 0");
+  const long long cells = (long long)grid->nx * grid->ny * grid->nz;
+  for (long long c = 0; c < cells; c++) {
+    const double ph = porosity[c];
+    if (!(ph > 0.0 && ph <= 1.0)) return fail(s, MDBS_ERR_ARG, "porosity must lie in (0, 1]");
+    if (ph < 1.0 && !(permeability[c] > 0.0 && isfinite(permeability[c])))
+      return fail(s, MDBS_ERR_ARG, "permeability must be > 0 where porosity < 1");
+  }
+  bool outlet = false;
+  for (int i = 0; i < 6; i++) {
+    if (op->bc[i] < 0 || op->bc[i] > 2) return fail(s, MDBS_ERR_ARG, "bc must be 0, 1 or 2");
+    if (grid->nz == 1 && i >= 4) continue;
+    outlet |= op->bc[i] == MDBS_BC_OUTLET;
+  }
+  if (!outlet) return fail(s, MDBS_ERR_ARG, "at least one side must be an outlet");
+  if (op->n_corr < 1 || op->n_corr > 8 || op->mom_sweeps < 0 || op->max_cg < 1 || op->mg_nu1 < 0 ||
+      op->mg_nu2 < 0 || op->mg_coarse_sweeps < 0 || op->precision < 0 || op->precision > 2 || !(op->dt > 0.0))
+    return fail(s, MDBS_ERR_ARG, "invalid options");
+  if (cl->kr_model < 0 || cl->kr_model > 1 || cl->pc_model < 0 || cl->pc_model > 1)
+    return fail(s, MDBS_ERR_ARG, "invalid closure model");
+
+  s = new (std::nothrow) mdbs_sim();
+  if (!s) return fail(nullptr, MDBS_ERR_OOM, "host allocation failed");
+  Prm& P = s->P;
+  P.n[0] = grid->nx;
+  P.n[1] = grid->ny;
+  P.n[2] = grid->nz;
+  Layout L = layout_of(grid);
+  P.dim = L.dim;
+  P.cells = L.cells;
+  for (int d = 0; d < 3; d++) P.nf[d] = L.nf[d];
+  P.h = grid->h;
+  P.A = grid->h * grid->h;
+  P.V = grid->h * grid->h * grid->h;
+  for (int i = 0; i < 6; i++) P.bc[i] = op->bc[i];
+  P.inlet_u = op->inlet_u;
+  P.inlet_alpha = op->inlet_alpha;
+  P.rho_l = fl->rho_l;
+  P.mu_l = fl->mu_l;
+  P.rho_g = fl->rho_g;
+  P.mu_g = fl->mu_g;
+  P.sigma = fl->sigma;
+  for (int e = 0; e < 3; e++) P.g[e] = fl->g[e];
+  P.kr_model = cl->kr_model;
+  P.pc_model = cl->pc_model;
+  P.kr_m = cl->kr_m;
+  P.a_l_irr = cl->a_l_irr;
+  P.a_g_irr = cl->a_g_irr;
+  P.pc0 = cl->pc0;
+  P.pc_beta = cl->pc_beta;
+  P.pc_m = cl->pc_m;
+  P.a_pc_irr = cl->a_pc_irr;
+  P.a_pc_max = cl->a_pc_max;
+  P.pc_eps = cl->pc_eps;
+  const double th = contact_angle_deg * M_PI / 180.0;
+  P.cos_t = cos(th);
+  P.sin_t = sin(th);
+  P.c_alpha = op->c_alpha;
+  s->opt = *op;
+  s->precision = op->precision;
+  s->dt = op->dt;
+  s->stream = nullptr;
+
+  s->arena_bytes = carve(nullptr, L, nullptr);
+  cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
+    fail(nullptr, code, std::string("device arena: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    delete s;
+    return code;
+  }
+  cudaMemset(s->arena, 0, s->arena_bytes);
+  carve(s, L, (char*)s->arena);
+  e = cudaMallocHost(&s->host_scal, 16 * sizeof(double));
+  if (e == cudaSuccess) s->ps = pressure_create(P, s->precision, &e);
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
+    fail(nullptr, code, std::string("pressure solver: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    if (s->host_scal) cudaFreeHost(s->host_scal);
+    cudaFree(s->arena);
+    delete s;
+    return code;
+  }
+  e = cudaMemcpy((void*)s->F.phi, porosity, cells * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy((void*)s->F.k0, permeability, cells * 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    Activate act(s);
+    double* nw[3] = {(double*)s->F.nw[0], (double*)s->F.nw[1], (double*)s->F.nw[2]};
+    launch_static_geometry(P, s->F.phi, (uint8_t*)s->F.is_free, nw, nullptr);
+    launch_set_boundary_velocities(P, s->F, nullptr);
+    e = cudaDeviceSynchronize();
+  }
+  if (e != cudaSuccess) {
+    fail(nullptr, MDBS_ERR_CUDA, std::string("setup: ") + cudaGetErrorString(e));
+    mdbs_destroy(s);
+    return MDBS_ERR_CUDA;
+  }
+  *out = s;
+  return MDBS_OK;
+}
+
+int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const double* uy, const double* uz,
+                    const double* p) {
+  if (!s) return MDBS_ERR_ARG;
+  if (!alpha || !ux || !uy || !p || (s->P.dim == 3 && !uz)) return fail(s, MDBS_ERR_ARG, "NULL field");
+  Activate act(s);
+  for (long long c = 0; c < s->P.cells; c++)
+    if (!(alpha[c] >= 0.0 && alpha[c] <= 1.0)) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1]");
+  const double* src[3] = {ux, uy, uz};
+  CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->F.p, p, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
+  for (int d = 0; d < s->P.dim; d++)
+    CK(cudaMemcpyAsync(s->F.u[d], src[d], s->P.nf[d] * 8, cudaMemcpyHostToDevice, s->stream));
+  launch_set_boundary_velocities(s->P, s->F, s->stream);
+  launch_properties(s->P, s->F, s->stream);
+  CK(cudaMemsetAsync(s->scal, 0, 16 * sizeof(double), s->stream));
+  CK(cudaGetLastError());
+  memset(&s->st, 0, sizeof(s->st));
+  s->prof.launches = 0;
+  s->dt = s->opt.dt;
+  s->time = 0.0;
+  s->st.dt = s->dt;
+  s->fields_set = true;
+  return refresh_stats(s);
+}
+
+int mdbs_step(mdbs_sim* s, int32_t n) {
+  if (!s) return MDBS_ERR_ARG;
+  if (n < 1) return fail(s, MDBS_ERR_ARG, "n must be >= 1");
+  if (!s->fields_set) return fail(s, MDBS_ERR_ARG, "mdbs_set_fields has not been called");
+  Activate act(s);
+  for (int i = 0; i < n; i++) {
+    int rc = one_step(s);
+    if (rc != MDBS_OK) return rc;
+  }
+  return MDBS_OK;
+}
+
+int mdbs_get_fields(const mdbs_sim* cs, double* alpha, double* ux, double* uy, double* uz, double* p) {
+  mdbs_sim* s = const_cast<mdbs_sim*>(cs);
+  if (!s) return MDBS_ERR_ARG;
+  double* dst[3] = {ux, uy, uz};
+  if (alpha) CK(cudaMemcpyAsync(alpha, s->F.alpha, s->P.cells * 8, cudaMemcpyDeviceToHost, s->stream));
+  if (p) CK(cudaMemcpyAsync(p, s->F.p, s->P.cells * 8, cudaMemcpyDeviceToHost, s->stream));
+  for (int d = 0; d < s->P.dim; d++)
+    if (dst[d]) CK(cudaMemcpyAsync(dst[d], s->F.u[d], s->P.nf[d] * 8, cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  return MDBS_OK;
+}
+
+void mdbs_destroy(mdbs_sim* s) {
+  if (!s) return;
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  pressure_destroy(s->ps);
+  if (s->host_scal) cudaFreeHost(s->host_scal);
+  cudaFree(s->arena);
+  delete s;
+}
+
+int mdbs_get_stats(const mdbs_sim* s, mdbs_stats* out) {
+  if (!s || !out) return MDBS_ERR_ARG;
+  *out = s->st;
+  return MDBS_OK;
+}
+
+const char* mdbs_last_error(const mdbs_sim* s) { return s ? s->err.c_str() : g_create_error.c_str(); }
+
+int mdbs_set_stream(mdbs_sim* s, void* stream) {
+  if (!s) return MDBS_ERR_ARG;
+  s->stream = (cudaStream_t)stream;
+  return MDBS_OK;
+}
+
+int mdbs_profile_enable(mdbs_sim* s, int32_t enable, int32_t only_id) {
+  if (!s || only_id < -1 || only_id >= K_COUNT) return MDBS_ERR_ARG;
+  if (s->prof.on) s->prof.resolve();
+  s->prof.on = enable != 0;
+  s->prof.only = only_id;
+  s->prof.reset();
+  return MDBS_OK;
+}
+
+int32_t mdbs_profile_count(void) { return K_COUNT; }
+
+int mdbs_profile_read(const mdbs_sim* s, int32_t id, const char** name, double* total_ms, int64_t* launches) {
+  if (id < 0 || id >= K_COUNT) return MDBS_ERR_ARG;
+  if (name) *name = kKernelNames[id];
+  if (total_ms) *total_ms = s ? s->prof.ms[id] : 0.0;
+  if (launches) *launches = s ? s->prof.count[id] : 0;
+  return MDBS_OK;
+}
+
+int64_t mdbs_debug_array(const mdbs_sim* cs, const char* name, double* out, int64_t capacity) {
+  mdbs_sim* s = const_cast<mdbs_sim*>(cs);
+  if (!s || !name) return MDBS_ERR_ARG;
+  const Fld& F = s->F;
+  const long long nc = s->P.cells;
+  struct Ent {
+    const char* nm;
+    const double* a;
+    long long n;
+  } tab[] = {
+      {"rho", F.rho, nc},          {"rho_old", F.rho_old, nc},  {"mu", F.mu, nc},
+      {"drag", F.drag, nc},        {"pc", F.pc, nc},            {"cf", F.cf, nc},
+      {"Ml", F.Ml, nc},            {"Mg", F.Mg, nc},            {"kappa", F.kappa, nc},
+      {"mx", F.m[0], nc},          {"my", F.m[1], nc},          {"mz", F.m[2], nc},
+      {"Tx", F.T[0], nc},          {"Ty", F.T[1], nc},          {"Tz", F.T[2], nc},
+      {"Dd", F.Dd, nc},            {"b", F.b, nc},              {"aL", F.aL, nc},
+      {"Rp", F.Rp, nc},            {"Rm", F.Rm, nc},            {"nwx", F.nw[0], nc},
+      {"nwy", F.nw[1], nc},        {"nwz", F.nw[2], nc},        {"aPx", F.aP[0], s->P.nf[0]},
+      {"aPy", F.aP[1], s->P.nf[1]}, {"aPz", F.aP[2], s->P.nf[2]}, {"rhs0x", F.rhs0[0], s->P.nf[0]},
+      {"rhs0y", F.rhs0[1], s->P.nf[1]}, {"rhs0z", F.rhs0[2], s->P.nf[2]}, {"Bx", F.B[0], s->P.nf[0]},
+      {"By", F.B[1], s->P.nf[1]},  {"Bz", F.B[2], s->P.nf[2]},  {"hbyax", F.hbya[0], s->P.nf[0]},
+      {"hbyay", F.hbya[1], s->P.nf[1]}, {"hbyaz", F.hbya[2], s->P.nf[2]}, {"FLOx", F.FLO[0], s->P.nf[0]},
+      {"FLOy", F.FLO[1], s->P.nf[1]}, {"FLOz", F.FLO[2], s->P.nf[2]}, {"AFx", F.AF[0], s->P.nf[0]},
+      {"AFy", F.AF[1], s->P.nf[1]}, {"AFz", F.AF[2], s->P.nf[2]},
+  };
+  for (const Ent& e : tab) {
+    if (strcmp(e.nm, name) != 0) continue;
+    long long n = e.n;
+    if (s->P.dim == 2 && (name[strlen(name) - 1] == 'z') && strcmp(name, "mz") != 0 && strcmp(name, "Tz") != 0 &&
+        strcmp(name, "nwz") != 0)
+      n = 0;
+    if (out && capacity > 0) {
+      long long m = n < capacity ? n : capacity;
+      if (m > 0) {
+        cudaError_t er = cudaMemcpyAsync(out, e.a, m * 8, cudaMemcpyDeviceToHost, s->stream);
+        if (er == cudaSuccess) er = cudaStreamSynchronize(s->stream);
+        if (er != cudaSuccess) return cuda_fail(s, er, "debug copy");
+      }
+    }
+    return n;
+  }
+  return fail(s, MDBS_ERR_ARG, std::string("unknown array ") + name);
+}
+
+}  // extern "C"

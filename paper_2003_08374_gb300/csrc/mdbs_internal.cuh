@@ -1,0 +1,147 @@
+// mdbs_internal.cuh -- device-side data structures shared by the CUDA
+// translation units of libmdbs (sm_103a).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace mdbs {
+
+constexpr int kWall = 0, kInlet = 1, kOutlet = 2;
+constexpr int kMaxLevels = 16;
+constexpr int kBlock = 256;
+constexpr int kMaxPartials = 2048;  // blocks per deterministic reduction
+
+// Geometry and physical parameters, passed by value to every kernel.
+struct Prm {
+  int n[3];      // cells per axis
+  int dim;       // 2 or 3
+  long long cells;
+  long long nf[3];  // faces per direction
+  double h, A, V;
+  int bc[6];
+  double inlet_u, inlet_alpha;
+  double rho_l, mu_l, rho_g, mu_g, sigma, g[3];
+  int kr_model, pc_model;
+  double kr_m, a_l_irr, a_g_irr, pc0, pc_beta, pc_m, a_pc_irr, a_pc_max, pc_eps;
+  double cos_t, sin_t;  // contact angle
+  double c_alpha;
+};
+
+// Device arrays of one simulation.
+struct Fld {
+  // static
+  const double* phi;
+  const double* k0;
+  const uint8_t* is_free;
+  const double* nw[3];  // wall normal (zero outside contact cells)
+  // state
+  double* alpha;
+  double* p;
+  double* u[3];
+  // properties
+  double *Ml, *Mg, *pc, *cf, *rho, *rho_old, *mu, *drag, *m[3], *kappa;
+  // saturation step
+  double *FLO[3], *AF[3], *aL, *Rp, *Rm;
+  // momentum
+  double *aP[3], *anb[3], *rhs0[3], *B[3], *hbya[3], *utmp[3];
+  // pressure system (level 0)
+  double *T[3], *Dd, *diag, *b;
+};
+
+// One multigrid level (T is stored per cell for the face towards +axis).
+template <typename R>
+struct Level {
+  int n[3];
+  int cz[3];  // axis coarsened relative to the finer level
+  long long cells;
+  R* T[3];
+  R* Dd;
+  R* diag;
+  R* x;
+  R* b;
+};
+
+// ---------------------------------------------------------------- helpers
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+__device__ __forceinline__ long long cell_index(const int n[3], int i, int j, int k) {
+  return i + (long long)n[0] * (j + (long long)n[1] * k);
+}
+
+// face index of direction d at face coordinates (i, j, k), c[d] in [0, n[d]]
+__device__ __forceinline__ long long face_index(const int n[3], int d, int i, int j, int k) {
+  long long fx = n[0] + (d == 0), fy = n[1] + (d == 1);
+  return i + fx * (j + fy * k);
+}
+
+// read with zero-gradient ghost cells (coordinates clamped into the grid)
+__device__ __forceinline__ double ghost_read(const double* __restrict__ a, const int n[3], int i, int j,
+                                             int k) {
+  i = clampi(i, 0, n[0] - 1);
+  j = clampi(j, 0, n[1] - 1);
+  k = clampi(k, 0, n[2] - 1);
+  return a[cell_index(n, i, j, k)];
+}
+
+// warp + block sum; result valid in thread 0
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double warp_part[32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_part[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? warp_part[threadIdx.x] : 0.0;
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// ---------------------------------------------------------------- launch accounting
+// Every kernel launch goes through MDBS_LAUNCH: it counts the launch for the
+// active simulation and, when profiling is on, brackets it with CUDA events on
+// the launch stream.
+enum KernelId {
+  K_ALPHA_FLUX, K_ALPHA_LO, K_ALPHA_LIMIT, K_ALPHA_UPDATE, K_FINALIZE, K_PROPERTIES, K_NORMALS,
+  K_CURVATURE, K_MOM_ASSEMBLE, K_JACOBI, K_HBYA, K_CORRECT, K_BOUNDARY, K_STATS, K_CFL, K_STATIC,
+  K_ASSEMBLE, K_DIAG, K_CONVERT, K_COARSEN, K_SMOOTH0, K_SMOOTHC, K_ZERO, K_RESTRICT0, K_RESTRICTC,
+  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_COUNT
+};
+extern const char* const kKernelNames[K_COUNT];
+void prof_begin(int id, cudaStream_t s);
+void prof_end(int id, cudaStream_t s);
+
+#define MDBS_LAUNCH(ID, GRID, BLOCK, STREAM, KERNEL, ...)   \
+  do {                                                     \
+    ::mdbs::prof_begin((ID), (STREAM));                    \
+    KERNEL<<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); \
+    ::mdbs::prof_end((ID), (STREAM));                      \
+  } while (0)
+
+// ---------------------------------------------------------------- launchers
+// step_kernels.cu
+void launch_alpha_step(const Prm& P, const Fld& F, double dt, double* partials, double* scal, int slot,
+                       cudaStream_t s);
+void launch_properties(const Prm& P, const Fld& F, cudaStream_t s);
+void launch_momentum_assemble(const Prm& P, const Fld& F, double dt, cudaStream_t s);
+void launch_jacobi_sweep(const Prm& P, const Fld& F, cudaStream_t s);  // u -> utmp
+void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s);
+void launch_correct(const Prm& P, const Fld& F, cudaStream_t s);
+void launch_set_boundary_velocities(const Prm& P, const Fld& F, cudaStream_t s);
+void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
+void launch_cfl(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
+void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s);
+
+// pressure.cu
+struct PressureSolver;
+PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err);
+void pressure_destroy(PressureSolver* ps);
+size_t pressure_bytes(const int n[3], int precision);
+void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s);
+// solves A p = b (level-0 arrays of F) by GMG-preconditioned CG; returns iterations,
+// writes the final relative residual; negative on a CUDA error
+int pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1, int nu2,
+                   int coarse_sweeps, double* resid, cudaStream_t s);
+
+}  // namespace mdbs

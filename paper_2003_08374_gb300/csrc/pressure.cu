@@ -1,0 +1,606 @@
+// pressure.cu -- pressure equation of the PISO corrector (Eq. 53) on sm_103a:
+// assembly of the 7-point (5-point in 2-D) variable-coefficient operator,
+// geometric multigrid V-cycle (red-black Gauss-Seidel, cell-centred 2:1
+// coarsening with series/parallel transmissibilities) and preconditioned CG in
+// FP64 with deterministic block reductions.  In mixed precision the V-cycle
+// runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.
+#include <math.h>
+
+#include <new>
+
+#include "mdbs_internal.cuh"
+
+namespace mdbs {
+
+namespace {
+
+int grid_for(long long n, int cap = 1 << 30) {
+  long long b = (n + kBlock - 1) / kBlock;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+__device__ __forceinline__ void decode3(const int n[3], long long c, int& i, int& j, int& k) {
+  i = (int)(c % n[0]);
+  long long r = c / n[0];
+  j = (int)(r % n[1]);
+  k = (int)(r / n[1]);
+}
+
+// ------------------------------------------------------------------ assembly
+// T_f = A^2 / a_P,f between cells, 2 A^2 / a_P,f on outlet faces (Dirichlet
+// through the ghost p_ghost = -p), b = -sum_f s_f A ubar_f with ubar = HbyA on
+// unknown faces and the fixed velocity on wall / inlet faces.
+__global__ void k_assemble(Prm P, Fld F) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int q[3];
+  decode3(P.n, c, q[0], q[1], q[2]);
+  const double A = P.A, A2 = P.A * P.A;
+  double div = 0.0, Dd = 0.0;
+  for (int d = 0; d < 3; d++) {
+    if (d >= P.dim) {
+      F.T[d][c] = 0.0;
+      continue;
+    }
+    const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+    const long long flo = face_index(P.n, d, q[0], q[1], q[2]);
+    const long long fhi = face_index(P.n, d, q[0] + di, q[1] + dj, q[2] + dk);
+    F.T[d][c] = (q[d] + 1 < P.n[d]) ? A2 / F.aP[d][fhi] : 0.0;
+    const bool lo_bnd = q[d] == 0, hi_bnd = q[d] + 1 == P.n[d];
+    if (lo_bnd && P.bc[2 * d] == kOutlet) Dd += 2.0 * A2 / F.aP[d][flo];
+    if (hi_bnd && P.bc[2 * d + 1] == kOutlet) Dd += 2.0 * A2 / F.aP[d][fhi];
+    const bool lo_fixed = lo_bnd && P.bc[2 * d] != kOutlet;
+    const bool hi_fixed = hi_bnd && P.bc[2 * d + 1] != kOutlet;
+    const double ulo = lo_fixed ? F.u[d][flo] : F.hbya[d][flo];
+    const double uhi = hi_fixed ? F.u[d][fhi] : F.hbya[d][fhi];
+    div += A * uhi - A * ulo;
+  }
+  F.Dd[c] = Dd;
+  F.b[c] = -div;
+}
+
+template <typename R>
+__device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], long long c) {
+  if (q[d] == 0) return R(0);
+  long long o = d == 0 ? 1 : (d == 1 ? (long long)L.n[0] : (long long)L.n[0] * L.n[1]);
+  return L.T[d][c - o];
+}
+
+template <typename R>
+__global__ void k_diag(Level<R> L) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= L.cells) return;
+  int q[3];
+  decode3(L.n, c, q[0], q[1], q[2]);
+  R dg = R(0);
+  for (int d = 0; d < 3; d++) {
+    dg += L.T[d][c];
+    if (q[d] > 0) dg += coef_lo(L, d, q, c);
+  }
+  L.diag[c] = dg + L.Dd[c];
+}
+
+__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) b[c] = (float)a[c];
+}
+
+// coarse transmissibilities: fine rows across a coarse face in parallel, along a
+// row half of each coarse cell's interior link and the crossing link in series
+template <typename R>
+__global__ void k_coarsen(Level<R> Fi, Level<R> Co) {
+  long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (ci >= Co.cells) return;
+  int Q[3];
+  decode3(Co.n, ci, Q[0], Q[1], Q[2]);
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; a++) {
+    lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
+    hi[a] = Co.cz[a] ? (2 * Q[a] + 1 < Fi.n[a] ? 2 * Q[a] + 1 : 2 * Q[a]) : Q[a];
+  }
+  for (int d = 0; d < 3; d++) {
+    if (Q[d] + 1 >= Co.n[d]) {
+      Co.T[d][ci] = R(0);
+      continue;
+    }
+    const R* Tf = Fi.T[d];
+    int rl[3] = {lo[0], lo[1], lo[2]}, rh[3] = {hi[0], hi[1], hi[2]};
+    rl[d] = rh[d] = 0;
+    R sum = R(0);
+    for (int z = rl[2]; z <= rh[2]; z++)
+      for (int y = rl[1]; y <= rh[1]; y++)
+        for (int x = rl[0]; x <= rh[0]; x++) {
+          int fc[3] = {x, y, z};
+          R inv;
+          if (Co.cz[d]) {
+            fc[d] = 2 * Q[d] + 1;
+            const R tface = Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+            fc[d] = 2 * Q[d];
+            const R tin_l = Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+            inv = R(1) / tface + R(1) / (R(2) * tin_l);
+            if (2 * Q[d] + 3 < Fi.n[d]) {
+              fc[d] = 2 * Q[d] + 2;
+              inv += R(1) / (R(2) * Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])]);
+            }
+          } else {
+            fc[d] = Q[d];
+            inv = R(1) / Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+          }
+          sum += R(1) / inv;
+        }
+    Co.T[d][ci] = sum;
+  }
+  R dd = R(0);
+  for (int z = lo[2]; z <= hi[2]; z++)
+    for (int y = lo[1]; y <= hi[1]; y++)
+      for (int x = lo[0]; x <= hi[0]; x++) dd += R(0.5) * Fi.Dd[cell_index(Fi.n, x, y, z)];
+  Co.Dd[ci] = dd;
+}
+
+// sum_nb T x_nb at cell c of level L (order x-, x+, y-, y+, z-, z+)
+template <typename R>
+__device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restrict__ x, const int q[3],
+                                           long long c) {
+  R v = R(0);
+  long long o = 1;
+  for (int d = 0; d < 3; d++) {
+    if (q[d] > 0) v += L.T[d][c - o] * x[c - o];
+    if (q[d] + 1 < L.n[d]) v += L.T[d][c] * x[c + o];
+    o *= L.n[d];
+  }
+  return v;
+}
+
+// red-black Gauss-Seidel half sweep of colour col; zero: x is taken as 0
+template <typename R>
+__global__ void k_smooth(Level<R> L, int col, int zero) {
+  const int half = (L.n[0] + 1) >> 1;
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  long long rows = (long long)L.n[1] * L.n[2];
+  if (t >= rows * half) return;
+  const int ti = (int)(t % half);
+  const long long row = t / half;
+  const int j = (int)(row % L.n[1]), k = (int)(row / L.n[1]);
+  const int i = ((j + k + col) & 1) + 2 * ti;
+  if (i >= L.n[0]) return;
+  const long long c = i + (long long)L.n[0] * row;
+  if (zero) {
+    L.x[c] = L.b[c] / L.diag[c];
+    return;
+  }
+  const int q[3] = {i, j, k};
+  R v = L.b[c] + neighbour_sum(L, L.x, q, c);
+  L.x[c] = v / L.diag[c];
+}
+
+template <typename R>
+__global__ void k_zero(R* x, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) x[c] = R(0);
+}
+
+// coarse b = sum of the fine residuals b - A x over the covered fine cells
+template <typename R>
+__global__ void k_resid_restrict(Level<R> Fi, Level<R> Co) {
+  long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (ci >= Co.cells) return;
+  int Q[3];
+  decode3(Co.n, ci, Q[0], Q[1], Q[2]);
+  int lo[3], hi[3];
+  for (int a = 0; a < 3; a++) {
+    lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
+    hi[a] = Co.cz[a] ? (2 * Q[a] + 1 < Fi.n[a] ? 2 * Q[a] + 1 : 2 * Q[a]) : Q[a];
+  }
+  R s = R(0);
+  for (int z = lo[2]; z <= hi[2]; z++)
+    for (int y = lo[1]; y <= hi[1]; y++)
+      for (int x = lo[0]; x <= hi[0]; x++) {
+        const int q[3] = {x, y, z};
+        const long long c = cell_index(Fi.n, x, y, z);
+        const R ax = Fi.diag[c] * Fi.x[c] - neighbour_sum(Fi, Fi.x, q, c);
+        s += Fi.b[c] - ax;
+      }
+  Co.b[ci] = s;
+}
+
+template <typename R>
+__global__ void k_prolong(Level<R> Fi, Level<R> Co) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= Fi.cells) return;
+  int q[3];
+  decode3(Fi.n, c, q[0], q[1], q[2]);
+  int Q[3];
+  for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
+  Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
+}
+
+// ------------------------------------------------------------------ CG kernels (FP64)
+__device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const double* __restrict__ x, long long c,
+                                           const int q[3]) {
+  double v = F.diag[c] * x[c];
+  long long o = 1;
+  for (int d = 0; d < 3; d++) {
+    if (q[d] > 0) v -= F.T[d][c - o] * x[c - o];
+    if (q[d] + 1 < P.n[d]) v -= F.T[d][c] * x[c + o];
+    o *= P.n[d];
+  }
+  return v;
+}
+
+// r = b - A x; partial sums of r.r and b.b
+__global__ void k_resid0(Prm P, Fld F, const double* __restrict__ x, double* __restrict__ r,
+                         double* __restrict__ partials, int nb) {
+  double rr = 0.0, bb = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    int q[3];
+    decode3(P.n, c, q[0], q[1], q[2]);
+    const double bc = F.b[c];
+    const double rc = bc - apply_A0(F, P, x, c, q);
+    r[c] = rc;
+    rr += rc * rc;
+    bb += bc * bc;
+  }
+  rr = block_sum(rr);
+  if (threadIdx.x == 0) partials[blockIdx.x] = rr;
+  bb = block_sum(bb);
+  if (threadIdx.x == 0) partials[nb + blockIdx.x] = bb;
+}
+
+// q = A d; partial d.q
+__global__ void k_spmv_dot(Prm P, Fld F, const double* __restrict__ dv, double* __restrict__ q,
+                           double* __restrict__ partials) {
+  double s = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    int qq[3];
+    decode3(P.n, c, qq[0], qq[1], qq[2]);
+    const double v = apply_A0(F, P, dv, c, qq);
+    q[c] = v;
+    s += dv[c] * v;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// x += alpha d; r -= alpha q; partial r.r   (alpha = scal[5])
+__global__ void k_update_xr(long long n, const double* __restrict__ scal, double* __restrict__ x,
+                            double* __restrict__ r, const double* __restrict__ dv, const double* __restrict__ q,
+                            double* __restrict__ partials) {
+  const double al = scal[5];
+  double s = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    x[c] += al * dv[c];
+    const double rc = r[c] - al * q[c];
+    r[c] = rc;
+    s += rc * rc;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// partial r.z and z.q
+__global__ void k_dots_rz(long long n, const double* __restrict__ r, const double* __restrict__ z,
+                          const double* __restrict__ q, double* __restrict__ partials, int nb, int with_zq) {
+  double rz = 0.0, zq = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x) {
+    rz += r[c] * z[c];
+    if (with_zq) zq += z[c] * q[c];
+  }
+  rz = block_sum(rz);
+  if (threadIdx.x == 0) partials[blockIdx.x] = rz;
+  if (with_zq) {
+    zq = block_sum(zq);
+    if (threadIdx.x == 0) partials[nb + blockIdx.x] = zq;
+  }
+}
+
+// d = z + beta d, beta from the scalars (first: d = z)
+__global__ void k_update_d(long long n, const double* __restrict__ scal, const double* __restrict__ z,
+                           double* __restrict__ dv, int first, int flexible) {
+  double be = 0.0;
+  if (!first) be = flexible ? -scal[5] * scal[4] / scal[7] : scal[2] / scal[7];
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    dv[c] = first ? z[c] : z[c] + be * dv[c];
+}
+
+// scalar finalizers (one block, fixed summation order)
+// mode 0: scal[0] = bb, scal[1] = rr  (two channels)
+// mode 1: scal[3] = dq, scal[5] = scal[2] / dq
+// mode 2: scal[1] = rr
+// mode 3: scal[7] = scal[2]; scal[2] = rz; scal[4] = zq (second channel when present)
+__global__ void k_finalize(const double* __restrict__ partials, int nb, double* scal, int mode, int two) {
+  double a = 0.0, b = 0.0;
+  for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+    a += partials[i];
+    if (two) b += partials[nb + i];
+  }
+  a = block_sum(a);
+  if (two) b = block_sum(b);
+  if (threadIdx.x != 0) return;
+  if (mode == 0) {
+    scal[1] = a;
+    scal[0] = b;
+  } else if (mode == 1) {
+    scal[3] = a;
+    scal[5] = scal[2] / a;
+  } else if (mode == 2) {
+    scal[1] = a;
+  } else {
+    scal[7] = scal[2];
+    scal[2] = a;
+    scal[4] = two ? b : 0.0;
+  }
+}
+
+__global__ void k_copy_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) b[c] = (float)a[c];
+}
+__global__ void k_copy_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) b[c] = (double)a[c];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ solver object
+struct PressureSolver {
+  int precision;
+  int nlev;
+  Level<double> ld[kMaxLevels];  // FP64 hierarchy (level 0 arrays are borrowed)
+  Level<float> lf[kMaxLevels];   // FP32 hierarchy (mixed precision)
+  double *r, *z, *dv, *q;
+  double* partials;
+  double* scal;
+  double* host_scal;  // pinned
+  void* block;        // single device allocation
+};
+
+static int plan_levels(const int n0[3], int dims[kMaxLevels][3], int cz[kMaxLevels][3]) {
+  int nlev = 1;
+  for (int a = 0; a < 3; a++) {
+    dims[0][a] = n0[a];
+    cz[0][a] = 0;
+  }
+  while (nlev < kMaxLevels) {
+    int changed = 0;
+    for (int a = 0; a < 3; a++) {
+      if (dims[nlev - 1][a] > 4) {
+        dims[nlev][a] = (dims[nlev - 1][a] + 1) / 2;
+        cz[nlev][a] = 1;
+        changed = 1;
+      } else {
+        dims[nlev][a] = dims[nlev - 1][a];
+        cz[nlev][a] = 0;
+      }
+    }
+    if (!changed) break;
+    nlev++;
+  }
+  return nlev;
+}
+
+static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, char* base) {
+  int dims[kMaxLevels][3], cz[kMaxLevels][3];
+  const int nlev = plan_levels(n, dims, cz);
+  size_t off = 0;
+  auto take = [&](size_t bytes) -> char* {
+    char* p = base ? base + off : nullptr;
+    off += align256(bytes);
+    return p;
+  };
+  const long long n0 = (long long)n[0] * n[1] * n[2];
+  if (ps) ps->nlev = nlev;
+  double* r = (double*)take(n0 * 8);
+  double* z = (double*)take(n0 * 8);
+  double* dv = (double*)take(n0 * 8);
+  double* q = (double*)take(n0 * 8);
+  double* partials = (double*)take(2 * kMaxPartials * 8);
+  double* scal = (double*)take(16 * 8);
+  if (ps) {
+    ps->r = r;
+    ps->z = z;
+    ps->dv = dv;
+    ps->q = q;
+    ps->partials = partials;
+    ps->scal = scal;
+  }
+  for (int l = 0; l < nlev; l++) {
+    const long long nc = (long long)dims[l][0] * dims[l][1] * dims[l][2];
+    if (precision == 0) {
+      Level<double> L{};
+      for (int a = 0; a < 3; a++) {
+        L.n[a] = dims[l][a];
+        L.cz[a] = cz[l][a];
+      }
+      L.cells = nc;
+      if (l > 0) {
+        for (int a = 0; a < 3; a++) L.T[a] = (double*)take(nc * 8);
+        L.Dd = (double*)take(nc * 8);
+        L.diag = (double*)take(nc * 8);
+        L.x = (double*)take(nc * 8);
+        L.b = (double*)take(nc * 8);
+      }
+      if (ps) ps->ld[l] = L;
+    } else {
+      Level<float> L{};
+      for (int a = 0; a < 3; a++) {
+        L.n[a] = dims[l][a];
+        L.cz[a] = cz[l][a];
+      }
+      L.cells = nc;
+      for (int a = 0; a < 3; a++) L.T[a] = (float*)take(nc * 4);
+      L.Dd = (float*)take(nc * 4);
+      L.diag = (float*)take(nc * 4);
+      L.x = (float*)take(nc * 4);
+      L.b = (float*)take(nc * 4);
+      if (ps) ps->lf[l] = L;
+    }
+  }
+  return off;
+}
+
+size_t pressure_bytes(const int n[3], int precision) { return solver_layout(n, precision, nullptr, nullptr); }
+
+PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
+  PressureSolver* ps = new (std::nothrow) PressureSolver();
+  if (!ps) {
+    *err = cudaErrorMemoryAllocation;
+    return nullptr;
+  }
+  ps->precision = precision == 0 ? 0 : 1;
+  size_t bytes = solver_layout(P.n, ps->precision, nullptr, nullptr);
+  *err = cudaMalloc(&ps->block, bytes);
+  if (*err != cudaSuccess) {
+    delete ps;
+    return nullptr;
+  }
+  *err = cudaMallocHost(&ps->host_scal, 16 * sizeof(double));
+  if (*err != cudaSuccess) {
+    cudaFree(ps->block);
+    delete ps;
+    return nullptr;
+  }
+  solver_layout(P.n, ps->precision, ps, (char*)ps->block);
+  return ps;
+}
+
+void pressure_destroy(PressureSolver* ps) {
+  if (!ps) return;
+  cudaFree(ps->block);
+  cudaFreeHost(ps->host_scal);
+  delete ps;
+}
+
+void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s) {
+  MDBS_LAUNCH(K_ASSEMBLE, grid_for(P.cells), kBlock, s, k_assemble, P, F);
+  Level<double> L0{};
+  for (int a = 0; a < 3; a++) {
+    L0.n[a] = P.n[a];
+    L0.T[a] = F.T[a];
+  }
+  L0.cells = P.cells;
+  L0.Dd = F.Dd;
+  L0.diag = F.diag;
+  MDBS_LAUNCH(K_DIAG, grid_for(P.cells), kBlock, s, k_diag<double>, L0);
+}
+
+template <typename R>
+static void build_hierarchy(Level<R>* lv, int nlev, cudaStream_t s) {
+  for (int l = 1; l < nlev; l++) {
+    MDBS_LAUNCH(K_COARSEN, grid_for(lv[l].cells), kBlock, s, k_coarsen<R>, lv[l - 1], lv[l]);
+    MDBS_LAUNCH(K_DIAG, grid_for(lv[l].cells), kBlock, s, k_diag<R>, lv[l]);
+  }
+}
+
+template <typename R>
+static void smooth_pair(const Level<R>& L, int first_col, bool zero_first, bool finest, cudaStream_t s) {
+  const int id = finest ? K_SMOOTH0 : K_SMOOTHC;
+  const long long threads = (long long)((L.n[0] + 1) >> 1) * L.n[1] * L.n[2];
+  MDBS_LAUNCH(id, grid_for(threads), kBlock, s, k_smooth<R>, L, first_col, zero_first ? 1 : 0);
+  MDBS_LAUNCH(id, grid_for(threads), kBlock, s, k_smooth<R>, L, 1 - first_col, 0);
+}
+
+// symmetric V-cycle, x of level 0 receives M b of level 0
+template <typename R>
+static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, cudaStream_t s) {
+  for (int l = 0; l < nlev - 1; l++) {
+    if (nu1 == 0) MDBS_LAUNCH(K_ZERO, grid_for(lv[l].cells), kBlock, s, k_zero<R>, lv[l].x, lv[l].cells);
+    for (int it = 0; it < nu1; it++) smooth_pair(lv[l], 0, it == 0, l == 0, s);
+    MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_for(lv[l + 1].cells), kBlock, s, k_resid_restrict<R>, lv[l], lv[l + 1]);
+  }
+  Level<R>& C = lv[nlev - 1];
+  if (cs == 0) MDBS_LAUNCH(K_ZERO, grid_for(C.cells), kBlock, s, k_zero<R>, C.x, C.cells);
+  for (int it = 0; it < cs; it++) smooth_pair(C, 0, it == 0, nlev == 1, s);
+  for (int it = 0; it < cs; it++) smooth_pair(C, 1, false, nlev == 1, s);
+  for (int l = nlev - 2; l >= 0; l--) {
+    MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_for(lv[l].cells), kBlock, s, k_prolong<R>, lv[l], lv[l + 1]);
+    for (int it = 0; it < nu2; it++) smooth_pair(lv[l], 1, false, l == 0, s);
+  }
+}
+
+int pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1, int nu2,
+                   int cs, double* resid, cudaStream_t s) {
+  const long long n = P.cells;
+  const int nb = grid_for(n, kMaxPartials);
+  const int flexible = ps->precision != 0;
+  double* x = F.p;
+  // hierarchy for this assembly
+  if (!flexible) {
+    Level<double>& L0 = ps->ld[0];
+    for (int a = 0; a < 3; a++) L0.T[a] = F.T[a];
+    L0.Dd = F.Dd;
+    L0.diag = F.diag;
+    L0.b = ps->r;
+    L0.x = ps->z;
+    build_hierarchy(ps->ld, ps->nlev, s);
+  } else {
+    Level<float>& L0 = ps->lf[0];
+    const int g = grid_for(n);
+    for (int a = 0; a < 3; a++) MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.T[a], L0.T[a], n);
+    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.Dd, L0.Dd, n);
+    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.diag, L0.diag, n);
+    build_hierarchy(ps->lf, ps->nlev, s);
+  }
+  auto precondition = [&]() {
+    if (!flexible) {
+      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, s);
+    } else {
+      const int g = grid_for(n);
+      MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_copy_d2f, ps->r, ps->lf[0].b, n);
+      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, s);
+      MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_copy_f2d, ps->lf[0].x, ps->z, n);
+    }
+  };
+  auto read_scalars = [&]() -> bool {
+    if (cudaMemcpyAsync(ps->host_scal, ps->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+      return false;
+    return cudaStreamSynchronize(s) == cudaSuccess;
+  };
+  MDBS_LAUNCH(K_RESID0, nb, kBlock, s, k_resid0, P, F, x, ps->r, ps->partials, nb);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 0, 1);
+  if (!read_scalars()) return -1;
+  const double bn = sqrt(ps->host_scal[0]);
+  double rn = sqrt(ps->host_scal[1]);
+  if (bn == 0.0) {
+    cudaMemsetAsync(x, 0, n * sizeof(double), s);
+    *resid = 0.0;
+    return 0;
+  }
+  if (rn <= tol * bn) {
+    *resid = rn / bn;
+    return 0;
+  }
+  precondition();
+  MDBS_LAUNCH(K_DOTS, nb, kBlock, s, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, 0);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 3, 0);
+  MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, s, k_update_d, n, ps->scal, ps->z, ps->dv, 1, flexible);
+  int it = 0;
+  while (it < max_it) {
+    it++;
+    MDBS_LAUNCH(K_SPMV_DOT, nb, kBlock, s, k_spmv_dot, P, F, ps->dv, ps->q, ps->partials);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 1, 0);
+    MDBS_LAUNCH(K_UPDATE_XR, nb, kBlock, s, k_update_xr, n, ps->scal, x, ps->r, ps->dv, ps->q, ps->partials);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 2, 0);
+    if (!read_scalars()) return -1;
+    rn = sqrt(ps->host_scal[1]);
+    if (!(rn == rn)) break;
+    if (rn <= tol * bn) break;
+    precondition();
+    MDBS_LAUNCH(K_DOTS, nb, kBlock, s, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, flexible);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 3, flexible);
+    MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, s, k_update_d, n, ps->scal, ps->z, ps->dv, 0, flexible);
+  }
+  *resid = rn / bn;
+  return cudaGetLastError() == cudaSuccess ? it : -1;
+}
+
+}  // namespace mdbs

@@ -1,0 +1,688 @@
+// step_kernels.cu -- CUDA kernels of the micro-continuum DBS-VOF time step
+// (saturation update, closures, interface geometry, momentum predictor,
+// velocity correction) for sm_103a.  One thread per cell or per face; the
+// arrays are x-fastest so consecutive threads touch consecutive addresses.
+// Paper references: Carrillo, Bourg & Soulaine, arXiv 2003.08374.
+#include <math.h>
+
+#include "mdbs_internal.cuh"
+
+namespace mdbs {
+
+namespace {
+
+// Flat face numbering: all x faces, then y faces, then z faces.
+__device__ __forceinline__ bool decode_face(const Prm& P, long long t, int& d, int& i, int& j, int& k,
+                                            long long& f) {
+  if (t < P.nf[0]) {
+    d = 0;
+    f = t;
+  } else if (t < P.nf[0] + P.nf[1]) {
+    d = 1;
+    f = t - P.nf[0];
+  } else if (P.dim == 3 && t < P.nf[0] + P.nf[1] + P.nf[2]) {
+    d = 2;
+    f = t - P.nf[0] - P.nf[1];
+  } else {
+    return false;
+  }
+  long long fx = P.n[0] + (d == 0), fy = P.n[1] + (d == 1);
+  i = (int)(f % fx);
+  long long r = f / fx;
+  j = (int)(r % fy);
+  k = (int)(r / fy);
+  return true;
+}
+
+__device__ __forceinline__ long long total_faces(const Prm& P) {
+  return P.nf[0] + P.nf[1] + (P.dim == 3 ? P.nf[2] : 0);
+}
+
+__device__ __forceinline__ void decode_cell(const Prm& P, long long c, int& i, int& j, int& k) {
+  i = (int)(c % P.n[0]);
+  long long r = c / P.n[0];
+  j = (int)(r % P.n[1]);
+  k = (int)(r / P.n[1]);
+}
+
+// central difference of a cell field along e at (i,j,k), zero-gradient ghosts
+__device__ __forceinline__ double cgrad(const double* __restrict__ a, const Prm& P, int e, int i, int j,
+                                        int k) {
+  int di = (e == 0), dj = (e == 1), dk = (e == 2);
+  return (ghost_read(a, P.n, i + di, j + dj, k + dk) - ghost_read(a, P.n, i - di, j - dj, k - dk)) /
+         (2.0 * P.h);
+}
+
+// 0 = interior face, 1 = fixed (wall / inlet) face, 2 = outlet face
+__device__ __forceinline__ int face_kind(const Prm& P, int d, int cd) {
+  if (cd > 0 && cd < P.n[d]) return 0;
+  int side = 2 * d + (cd == 0 ? 0 : 1);
+  return P.bc[side] == kOutlet ? 2 : 1;
+}
+
+__device__ __forceinline__ double warp_reduce_max(double v) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+int grid_for(long long n, int cap = 1 << 30) {
+  long long b = (n + kBlock - 1) / kBlock;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (int)b;
+}
+
+// ------------------------------------------------------------------ saturation
+// Face fluxes of the saturation equation (Eq. 15): upwind (low-order) flux,
+// Van Leer high-order flux (section 3.1) plus the relative-velocity flux --
+// compression in solid-free faces (Eq. 22 oriented as Eq. 41) or the porous
+// phase-flux difference (Eq. 34 times a_l a_g).  AF = high - low order.
+__global__ void k_alpha_flux(Prm P, Fld F, double* __restrict__ partials) {
+  double inflow = 0.0;
+  const long long total = total_faces(P);
+  const double inv_h = 1.0 / P.h;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int d, i, j, k;
+    long long f;
+    decode_face(P, t, d, i, j, k, f);
+    const double uf = F.u[d][f];
+    const double Q = P.A * uf;
+    const int cd = d == 0 ? i : (d == 1 ? j : k);
+    const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+    if (cd > 0 && cd < P.n[d]) {
+      const long long l = cell_index(P.n, i - di, j - dj, k - dk);
+      const long long r = cell_index(P.n, i, j, k);
+      const double al = F.alpha[l], ar = F.alpha[r];
+      double aU, aD, aUU;
+      if (Q >= 0.0) {
+        aU = al;
+        aD = ar;
+        aUU = ghost_read(F.alpha, P.n, i - 2 * di, j - 2 * dj, k - 2 * dk);
+      } else {
+        aU = ar;
+        aD = al;
+        aUU = ghost_read(F.alpha, P.n, i + di, j + dj, k + dk);
+      }
+      const double flo = Q * aU;
+      // Van Leer: aU + (1/2) psi(r) (aD - aU), psi(r) = (r+|r|)/(1+|r|), r = (aU-aUU)/(aD-aU),
+      // evaluated without the ratio: aU + ab/(a+b) when ab > 0.
+      const double ga = aU - aUU, gb = aD - aU;
+      const double avl = (ga * gb > 0.0) ? aU + ga * gb / (ga + gb) : aU;
+      double rel = 0.0;
+      const bool fl = F.is_free[l], fr = F.is_free[r];
+      if (fl && fr) {
+        double gf[3] = {0.0, 0.0, 0.0};
+        for (int e = 0; e < P.dim; e++)
+          gf[e] = 0.5 * (cgrad(F.alpha, P, e, i - di, j - dj, k - dk) + cgrad(F.alpha, P, e, i, j, k));
+        const double mag = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
+        const double nfc = gf[d] / (mag + 1e-8 * inv_h);
+        const double w = P.c_alpha * fabs(uf) * nfc * P.A;
+        rel = (w >= 0.0) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
+      } else if (!fl && !fr) {
+        const double af = 0.5 * (al + ar), agf = 1.0 - af;
+        const double Mlf = 0.5 * (F.Ml[l] + F.Ml[r]), Mgf = 0.5 * (F.Mg[l] + F.Mg[r]);
+        const double pcl = F.pc[l], pcr = F.pc[r];
+        const double pcf = 0.5 * (pcl + pcr);
+        const double dp = (F.p[r] - F.p[l]) * inv_h;
+        const double dpc = (pcr - pcl) * inv_h;
+        const double da = (ar - al) * inv_h;
+        const double cm = agf * Mlf - af * Mgf;
+        rel = P.A * (-cm * dp + (agf * P.rho_l * Mlf - af * P.rho_g * Mgf) * P.g[d] +
+                     (Mlf * agf * agf + Mgf * af * af) * dpc - cm * pcf * da);
+      }
+      F.FLO[d][f] = flo;
+      F.AF[d][f] = (Q * avl + rel) - flo;
+    } else {
+      const bool high = cd != 0;
+      const int side = 2 * d + (high ? 1 : 0);
+      const long long c = high ? cell_index(P.n, i - di, j - dj, k - dk) : cell_index(P.n, i, j, k);
+      double flo = 0.0;
+      if (P.bc[side] == kInlet) {
+        const bool entering = high ? (Q < 0.0) : (Q > 0.0);
+        flo = Q * (entering ? P.inlet_alpha : F.alpha[c]);
+      } else if (P.bc[side] == kOutlet) {
+        flo = Q * F.alpha[c];
+      }
+      F.FLO[d][f] = flo;
+      F.AF[d][f] = 0.0;
+      inflow += high ? -flo : flo;
+    }
+  }
+  double s = block_sum(inflow);
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+// low-order (upwind) update
+__global__ void k_alpha_lo(Prm P, Fld F, double dt) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  double div = 0.0;
+  for (int d = 0; d < P.dim; d++) {
+    long long flo = face_index(P.n, d, i, j, k);
+    long long fhi = face_index(P.n, d, i + (d == 0), j + (d == 1), k + (d == 2));
+    div += F.FLO[d][fhi] - F.FLO[d][flo];
+  }
+  F.aL[c] = F.alpha[c] - dt / (F.phi[c] * P.V) * div;
+}
+
+// Zalesak limiter coefficients R+ / R-.  Bounds: local extrema of the old and
+// low-order solutions over the cell and its face neighbours (within [0, 1]) in
+// solid-free cells; [0, 1] in porous cells, where the relative flux is the
+// physical Darcy phase flux of Eq. 34.
+__global__ void k_alpha_limit(Prm P, Fld F, double dt) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  const double a0 = F.alpha[c], aLc = F.aL[c];
+  double amax = fmax(a0, aLc), amin = fmin(a0, aLc);
+  double Pp = 0.0, Pm = 0.0;
+  for (int d = 0; d < P.dim; d++) {
+    const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+    const int cd = d == 0 ? i : (d == 1 ? j : k);
+    if (cd > 0) {
+      long long b = cell_index(P.n, i - di, j - dj, k - dk);
+      amax = fmax(amax, fmax(F.alpha[b], F.aL[b]));
+      amin = fmin(amin, fmin(F.alpha[b], F.aL[b]));
+    }
+    if (cd + 1 < P.n[d]) {
+      long long b = cell_index(P.n, i + di, j + dj, k + dk);
+      amax = fmax(amax, fmax(F.alpha[b], F.aL[b]));
+      amin = fmin(amin, fmin(F.alpha[b], F.aL[b]));
+    }
+    const double alo = F.AF[d][face_index(P.n, d, i, j, k)];
+    const double ahi = F.AF[d][face_index(P.n, d, i + di, j + dj, k + dk)];
+    Pp += fmax(0.0, alo) + fmax(0.0, -ahi);
+    Pm += fmax(0.0, -alo) + fmax(0.0, ahi);
+  }
+  amax = fmin(1.0, amax);
+  amin = fmax(0.0, amin);
+  if (!F.is_free[c]) {
+    amax = 1.0;
+    amin = 0.0;
+  }
+  const double fac = F.phi[c] * P.V / dt;
+  const double Qp = fmax(0.0, amax - aLc) * fac;
+  const double Qm = fmax(0.0, aLc - amin) * fac;
+  F.Rp[c] = Pp > 0.0 ? fmin(1.0, Qp / Pp) : 1.0;
+  F.Rm[c] = Pm > 0.0 ? fmin(1.0, Qm / Pm) : 1.0;
+}
+
+__device__ __forceinline__ double limited_af(const Prm& P, const Fld& F, int d, int i, int j, int k) {
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (cd == 0 || cd == P.n[d]) return 0.0;
+  const long long l = cell_index(P.n, i - (d == 0), j - (d == 1), k - (d == 2));
+  const long long r = cell_index(P.n, i, j, k);
+  const double a = F.AF[d][face_index(P.n, d, i, j, k)];
+  const double lam = a >= 0.0 ? fmin(F.Rm[l], F.Rp[r]) : fmin(F.Rp[l], F.Rm[r]);
+  return lam * a;
+}
+
+__global__ void k_alpha_update(Prm P, Fld F, double dt) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  double corr = 0.0;
+  for (int d = 0; d < P.dim; d++) {
+    const double lo = limited_af(P, F, d, i, j, k);
+    const double hi = limited_af(P, F, d, i + (d == 0), j + (d == 1), k + (d == 2));
+    corr += hi - lo;
+  }
+  F.alpha[c] = F.aL[c] - dt / (F.phi[c] * P.V) * corr;
+}
+
+// deterministic final sum of nb partials: scal[slot] += scale * sum (or = when !accumulate)
+__global__ void k_finalize_sum(const double* __restrict__ partials, int nb, double* scal, int slot,
+                               double scale, int accumulate) {
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[b];
+  v = block_sum(v);
+  if (threadIdx.x == 0) scal[slot] = (accumulate ? scal[slot] : 0.0) + scale * v;
+}
+
+// ------------------------------------------------------------------ closures
+// Appendix A closures, Eqs. 42 and 45 densities / drag, Eq. 38 coefficient.
+__global__ void k_properties(Prm P, Fld F) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  const double a = F.alpha[c];
+  F.mu[c] = a * P.mu_l + (1.0 - a) * P.mu_g;
+  if (F.is_free[c]) {
+    F.Ml[c] = 0.0;
+    F.Mg[c] = 0.0;
+    F.drag[c] = 0.0;
+    F.pc[c] = 0.0;
+    F.cf[c] = 0.0;
+    F.rho[c] = a * P.rho_l + (1.0 - a) * P.rho_g;
+    return;
+  }
+  double ae = (a - P.a_l_irr) / (1.0 - P.a_g_irr - P.a_l_irr);
+  ae = fmin(fmax(ae, 0.0), 1.0);
+  double krl, krg;
+  if (P.kr_model == 0) {
+    krl = pow(ae, P.kr_m);
+    krg = pow(1.0 - ae, P.kr_m);
+  } else {
+    const double s1m = pow(ae, 1.0 / P.kr_m);
+    krg = sqrt(1.0 - ae) * pow(1.0 - s1m, 2.0 * P.kr_m);
+    const double t = 1.0 - pow(1.0 - s1m, P.kr_m);
+    krl = sqrt(ae) * t * t;
+  }
+  const double k0 = F.k0[c];
+  const double Ml = k0 * krl / P.mu_l, Mg = k0 * krg / P.mu_g, M = Ml + Mg;
+  double s = (a - P.a_pc_irr) / (P.a_pc_max - P.a_pc_irr);
+  s = fmin(fmax(s, P.pc_eps), 1.0 - P.pc_eps);
+  const double pc = P.pc_model == 0 ? P.pc0 * pow(s, -P.pc_beta)
+                                    : P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
+  F.Ml[c] = Ml;
+  F.Mg[c] = Mg;
+  F.drag[c] = 1.0 / M;
+  F.rho[c] = (P.rho_l * Ml + P.rho_g * Mg) / M;
+  F.pc[c] = pc;
+  F.cf[c] = (Ml * (1.0 - a) - Mg * a) / M;
+}
+
+// interface normal toward the liquid (Eq. 24 with the orientation of Eq. 41)
+// and the contact-angle normal of Eq. 40 in free cells next to porous cells
+__global__ void k_normals(Prm P, Fld F) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  double g[3] = {0.0, 0.0, 0.0};
+  for (int e = 0; e < P.dim; e++) g[e] = cgrad(F.alpha, P, e, i, j, k);
+  const double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+  const double den = mag + 1e-8 / P.h;
+  double m[3] = {g[0] / den, g[1] / den, g[2] / den};
+  const double nw[3] = {F.nw[0][c], F.nw[1][c], F.nw[2][c]};
+  if (nw[0] != 0.0 || nw[1] != 0.0 || nw[2] != 0.0) {
+    const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
+    const double mn = m[0] * nw[0] + m[1] * nw[1] + m[2] * nw[2];
+    double t[3], tn = 0.0;
+    for (int e = 0; e < 3; e++) {
+      t[e] = m[e] - mn * nw[e];
+      tn += t[e] * t[e];
+    }
+    tn = sqrt(tn);
+    for (int e = 0; e < 3; e++) m[e] = mm * (P.cos_t * nw[e] + P.sin_t * (tn > 0.0 ? t[e] / tn : 0.0));
+  }
+  F.m[0][c] = m[0];
+  F.m[1][c] = m[1];
+  F.m[2][c] = m[2];
+}
+
+// curvature kappa = -div(m) (Eq. 27 / 43)
+__global__ void k_curvature(Prm P, Fld F) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  double kap = 0.0;
+  for (int e = 0; e < P.dim; e++) kap -= cgrad(F.m[e], P, e, i, j, k);
+  F.kappa[c] = kap;
+}
+
+// ------------------------------------------------------------------ momentum
+// Staggered momentum equation of a face (Eqs. 46-48): diagonal a_P, neighbour
+// coefficients (implicit upwind convection of rho u u / phi^2 and viscous
+// diffusion), and rhs0 = Euler source + explicit transpose viscous stress +
+// body force (gravity rho g and capillary force F_c, Eqs. 38, 43, 45).
+__global__ void k_momentum_assemble(Prm P, Fld F, double dt) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const long long nf = P.nf[d];
+  const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  const int kind = face_kind(P, d, cd);
+  for (int s = 0; s < 6; s++) F.anb[d][s * nf + f] = 0.0;
+  if (kind == 1) {
+    F.aP[d][f] = 1.0;
+    F.rhs0[d][f] = 0.0;
+    F.B[d][f] = 0.0;
+    return;
+  }
+  const int li = i - di, lj = j - dj, lk = k - dk;  // low cell (may be a ghost at an outlet)
+  const double h = P.h, A = P.A, V = P.V;
+  const double phif = 0.5 * (ghost_read(F.phi, P.n, li, lj, lk) + ghost_read(F.phi, P.n, i, j, k));
+  const double rhof = 0.5 * (ghost_read(F.rho, P.n, li, lj, lk) + ghost_read(F.rho, P.n, i, j, k));
+  const double rhoo = 0.5 * (ghost_read(F.rho_old, P.n, li, lj, lk) + ghost_read(F.rho_old, P.n, i, j, k));
+  const double Df = 0.5 * (ghost_read(F.drag, P.n, li, lj, lk) + ghost_read(F.drag, P.n, i, j, k));
+  const double muL = ghost_read(F.mu, P.n, li, lj, lk), muR = ghost_read(F.mu, P.n, i, j, k);
+  double Bf = rhof * P.g[d];
+  if (kind == 0) {
+    const long long l = cell_index(P.n, li, lj, lk), r = cell_index(P.n, i, j, k);
+    const bool fl = F.is_free[l], fr = F.is_free[r];
+    if (fl && fr) {
+      Bf += P.sigma * 0.5 * (F.kappa[l] + F.kappa[r]) * (F.alpha[r] - F.alpha[l]) / h;
+    } else if (!fl && !fr) {
+      Bf += (0.5 * (F.cf[l] + F.cf[r]) * (F.pc[r] - F.pc[l]) -
+             0.5 * (F.pc[l] + F.pc[r]) * (F.alpha[r] - F.alpha[l])) /
+            h;
+    }
+  }
+  F.B[d][f] = Bf;
+  const double uf = F.u[d][f];
+  const double at = V * rhof / (phif * dt);
+  const double S = V * rhoo * uf / (phif * dt);
+  const double cconv = V * rhof / (phif * phif * h);
+  double ap = at + V * Df;
+  double tt = 0.0;
+  for (int e = 0; e < P.dim; e++) {
+    const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
+    // e-velocities on the low / high e-faces of the (clamped) low and high cells
+    double vLlo = 0.0, vLhi = 0.0, vRlo = 0.0, vRhi = 0.0;
+    if (e != d) {
+      const int ci = clampi(li, 0, P.n[0] - 1), cj = clampi(lj, 0, P.n[1] - 1), ck = clampi(lk, 0, P.n[2] - 1);
+      const int ri = clampi(i, 0, P.n[0] - 1), rj = clampi(j, 0, P.n[1] - 1), rk = clampi(k, 0, P.n[2] - 1);
+      vLlo = F.u[e][face_index(P.n, e, ci, cj, ck)];
+      vLhi = F.u[e][face_index(P.n, e, ci + ei, cj + ej, ck + ek)];
+      vRlo = F.u[e][face_index(P.n, e, ri, rj, rk)];
+      vRhi = F.u[e][face_index(P.n, e, ri + ei, rj + ej, rk + ek)];
+    }
+    const double w = (e == d) ? uf : 0.25 * (vLlo + vLhi + vRlo + vRhi);
+    for (int sg = -1; sg <= 1; sg += 2) {
+      const int slot = 2 * e + (sg > 0);
+      const int ce = (e == 0 ? i : (e == 1 ? j : k)) + sg;
+      int status;  // 0 exists, 1 mirror (no-slip ghost), 2 copy (zero-gradient ghost)
+      if (e == d)
+        status = (ce >= 0 && ce <= P.n[d]) ? 0 : 2;
+      else if (ce >= 0 && ce < P.n[e])
+        status = 0;
+      else
+        status = P.bc[2 * e + (sg > 0)] == kOutlet ? 2 : 1;
+      const double cup = cconv * (sg < 0 ? fmax(w, 0.0) : fmax(-w, 0.0));
+      double mus;
+      if (e == d) {
+        mus = sg < 0 ? muL : muR;
+      } else {
+        mus = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
+                      ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
+      }
+      const double a = cup + mus * A / h;
+      if (status == 0) {
+        F.anb[d][slot * nf + f] = a;
+        ap += a;
+      } else if (status == 1) {
+        ap += 2.0 * a;
+      }
+    }
+    // explicit div(mu grad(u)^T), component d
+    if (e == d) {
+      const double dR = (cd + 1 <= P.n[d]) ? (F.u[d][face_index(P.n, d, i + di, j + dj, k + dk)] - uf) / h : 0.0;
+      const double dL = (cd - 1 >= 0) ? (uf - F.u[d][face_index(P.n, d, li, lj, lk)]) / h : 0.0;
+      tt += (muR * dR - muL * dL) / h;
+    } else {
+      double ts = 0.0;
+      for (int sg = -1; sg <= 1; sg += 2) {
+        const double muE = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
+                                   ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
+        const double der = sg > 0 ? (vRhi - vLhi) / h : (vRlo - vLlo) / h;
+        ts += sg > 0 ? muE * der : -muE * der;
+      }
+      tt += ts / h;
+    }
+  }
+  F.aP[d][f] = ap;
+  F.rhs0[d][f] = S + V * (tt + Bf);
+}
+
+// H(u) = sum_nb a_nb u_nb + rhs0 of an unknown face
+__device__ __forceinline__ double face_H(const Prm& P, const Fld& F, const double* const* u, int d, int i, int j,
+                                         int k, long long f) {
+  const long long nf = P.nf[d];
+  double hs = 0.0;
+  for (int e = 0; e < P.dim; e++) {
+    const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
+    const double am = F.anb[d][(2 * e) * nf + f];
+    const double ap = F.anb[d][(2 * e + 1) * nf + f];
+    if (am != 0.0) hs += am * u[d][face_index(P.n, d, i - ei, j - ej, k - ek)];
+    if (ap != 0.0) hs += ap * u[d][face_index(P.n, d, i + ei, j + ej, k + ek)];
+  }
+  return hs + F.rhs0[d][f];
+}
+
+// p_R - p_L across a face; the outlet ghost holds -p (p = 0 on the face)
+__device__ __forceinline__ double face_dp(const Prm& P, const double* __restrict__ p, int d, int i, int j,
+                                          int k) {
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+  const double pl = cd > 0 ? p[cell_index(P.n, i - di, j - dj, k - dk)] : -p[cell_index(P.n, i, j, k)];
+  const double pr = cd < P.n[d] ? p[cell_index(P.n, i, j, k)] : -p[cell_index(P.n, i - di, j - dj, k - dk)];
+  return pr - pl;
+}
+
+// one Jacobi sweep of the momentum predictor (Eq. 50): utmp = (H(u) - V grad p^k)/a_P
+__global__ void k_jacobi(Prm P, Fld F) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (face_kind(P, d, cd) == 1) {
+    F.utmp[d][f] = F.u[d][f];
+    return;
+  }
+  const double* u[3] = {F.u[0], F.u[1], F.u[2]};
+  const double hs = face_H(P, F, u, d, i, j, k, f);
+  F.utmp[d][f] = (hs - P.V * face_dp(P, F.p, d, i, j, k) / P.h) / F.aP[d][f];
+}
+
+// HbyA = H(u)/a_P (Eq. 51 without the pressure gradient)
+__global__ void k_hbya(Prm P, Fld F) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (face_kind(P, d, cd) == 1) {
+    F.hbya[d][f] = 0.0;
+    return;
+  }
+  const double* u[3] = {F.u[0], F.u[1], F.u[2]};
+  F.hbya[d][f] = face_H(P, F, u, d, i, j, k, f) / F.aP[d][f];
+}
+
+// corrected velocity, Eq. 51
+__global__ void k_correct(Prm P, Fld F) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (face_kind(P, d, cd) == 1) return;
+  F.u[d][f] = F.hbya[d][f] - (P.A / F.aP[d][f]) * face_dp(P, F.p, d, i, j, k);
+}
+
+__global__ void k_boundary_velocities(Prm P, Fld F) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const int cd = d == 0 ? i : (d == 1 ? j : k);
+  if (face_kind(P, d, cd) != 1) return;
+  const int side = 2 * d + (cd == 0 ? 0 : 1);
+  double v = 0.0;
+  if (P.bc[side] == kInlet) v = (side & 1) ? -P.inlet_u : P.inlet_u;
+  F.u[d][f] = v;
+}
+
+// mass, alpha min / max and a non-finite sentinel over the cells
+__global__ void k_field_stats(Prm P, Fld F, double* __restrict__ partials, int nb) {
+  double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
+       c += (long long)gridDim.x * blockDim.x) {
+    const double a = F.alpha[c];
+    mass += F.phi[c] * a * P.V;
+    amin = fmin(amin, a);
+    amax = fmax(amax, a);
+    if (!isfinite(a) || !isfinite(F.p[c])) bad += 1.0;
+  }
+  mass = block_sum(mass);
+  if (threadIdx.x == 0) partials[blockIdx.x] = mass;
+  __syncthreads();
+  bad = block_sum(bad);
+  if (threadIdx.x == 0) partials[3 * nb + blockIdx.x] = bad;
+  // min / max through the max reduction
+  __shared__ double smx[32], smn[32];
+  double vmx = warp_reduce_max(amax), vmn = -warp_reduce_max(-amin);
+  if ((threadIdx.x & 31) == 0) {
+    smx[threadIdx.x >> 5] = vmx;
+    smn[threadIdx.x >> 5] = vmn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = -INFINITY, b = INFINITY;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
+      a = fmax(a, smx[w]);
+      b = fmin(b, smn[w]);
+    }
+    partials[nb + blockIdx.x] = b;
+    partials[2 * nb + blockIdx.x] = a;
+  }
+}
+
+__global__ void k_finalize_stats(const double* __restrict__ partials, int nb, double* scal) {
+  if (threadIdx.x != 0) return;
+  double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
+  for (int b = 0; b < nb; b++) {
+    mass += partials[b];
+    amin = fmin(amin, partials[nb + b]);
+    amax = fmax(amax, partials[2 * nb + b]);
+    bad += partials[3 * nb + b];
+  }
+  scal[0] = mass;
+  scal[1] = amin;
+  scal[2] = amax;
+  scal[3] = bad;
+}
+
+// max over faces of |u_f| / phi_f (CFL time step, section 3.2)
+__global__ void k_cfl(Prm P, Fld F, double* __restrict__ partials) {
+  double vmax = 0.0;
+  const long long total = total_faces(P);
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    int d, i, j, k;
+    long long f;
+    decode_face(P, t, d, i, j, k, f);
+    const double phif = 0.5 * (ghost_read(F.phi, P.n, i - (d == 0), j - (d == 1), k - (d == 2)) +
+                               ghost_read(F.phi, P.n, i, j, k));
+    vmax = fmax(vmax, fabs(F.u[d][f]) / phif);
+  }
+  __shared__ double sm[32];
+  vmax = warp_reduce_max(vmax);
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = vmax;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); w++) a = fmax(a, sm[w]);
+    partials[blockIdx.x] = a;
+  }
+}
+
+__global__ void k_finalize_max(const double* __restrict__ partials, int nb, double* scal, int slot) {
+  if (threadIdx.x != 0) return;
+  double a = 0.0;
+  for (int b = 0; b < nb; b++) a = fmax(a, partials[b]);
+  scal[slot] = a;
+}
+
+// static geometry: solid-free flag (porosity exactly 1) and, in free cells with a
+// porous face neighbour, the wall normal n_w = -grad(phi)/|grad(phi)| pointing
+// into the porous side (used by the contact-angle normal of Eq. 40)
+__global__ void k_static_geometry(Prm P, const double* __restrict__ phi, uint8_t* __restrict__ is_free,
+                                  double* __restrict__ nwx, double* __restrict__ nwy, double* __restrict__ nwz) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= P.cells) return;
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  const bool fr = phi[c] == 1.0;
+  is_free[c] = fr ? 1 : 0;
+  double n[3] = {0.0, 0.0, 0.0};
+  if (fr) {
+    bool touch = false;
+    for (int d = 0; d < P.dim; d++) {
+      const int di = (d == 0), dj = (d == 1), dk = (d == 2);
+      const int cd = d == 0 ? i : (d == 1 ? j : k);
+      if (cd > 0 && phi[cell_index(P.n, i - di, j - dj, k - dk)] != 1.0) touch = true;
+      if (cd + 1 < P.n[d] && phi[cell_index(P.n, i + di, j + dj, k + dk)] != 1.0) touch = true;
+    }
+    if (touch) {
+      double g[3] = {0.0, 0.0, 0.0};
+      for (int e = 0; e < P.dim; e++) g[e] = cgrad(phi, P, e, i, j, k);
+      const double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
+      if (mag > 0.0)
+        for (int e = 0; e < 3; e++) n[e] = -g[e] / mag;
+    }
+  }
+  nwx[c] = n[0];
+  nwy[c] = n[1];
+  nwz[c] = n[2];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s) {
+  MDBS_LAUNCH(K_STATIC, grid_for(P.cells), kBlock, s, k_static_geometry, P, phi, is_free, nw[0], nw[1], nw[2]);
+}
+
+static long long faces_total_host(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P.nf[2] : 0); }
+
+void launch_alpha_step(const Prm& P, const Fld& F, double dt, double* partials, double* scal, int slot,
+                       cudaStream_t s) {
+  const int gf = grid_for(faces_total_host(P), kMaxPartials);
+  MDBS_LAUNCH(K_ALPHA_FLUX, gf, kBlock, s, k_alpha_flux, P, F, partials);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize_sum, partials, gf, scal, slot, dt, 1);
+  const int gc = grid_for(P.cells);
+  MDBS_LAUNCH(K_ALPHA_LO, gc, kBlock, s, k_alpha_lo, P, F, dt);
+  MDBS_LAUNCH(K_ALPHA_LIMIT, gc, kBlock, s, k_alpha_limit, P, F, dt);
+  MDBS_LAUNCH(K_ALPHA_UPDATE, gc, kBlock, s, k_alpha_update, P, F, dt);
+}
+
+void launch_properties(const Prm& P, const Fld& F, cudaStream_t s) {
+  const int gc = grid_for(P.cells);
+  MDBS_LAUNCH(K_PROPERTIES, gc, kBlock, s, k_properties, P, F);
+  MDBS_LAUNCH(K_NORMALS, gc, kBlock, s, k_normals, P, F);
+  MDBS_LAUNCH(K_CURVATURE, gc, kBlock, s, k_curvature, P, F);
+}
+
+void launch_momentum_assemble(const Prm& P, const Fld& F, double dt, cudaStream_t s) {
+  MDBS_LAUNCH(K_MOM_ASSEMBLE, grid_for(faces_total_host(P)), kBlock, s, k_momentum_assemble, P, F, dt);
+}
+
+void launch_jacobi_sweep(const Prm& P, const Fld& F, cudaStream_t s) {
+  MDBS_LAUNCH(K_JACOBI, grid_for(faces_total_host(P)), kBlock, s, k_jacobi, P, F);
+}
+
+void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s) {
+  MDBS_LAUNCH(K_HBYA, grid_for(faces_total_host(P)), kBlock, s, k_hbya, P, F);
+}
+
+void launch_correct(const Prm& P, const Fld& F, cudaStream_t s) {
+  MDBS_LAUNCH(K_CORRECT, grid_for(faces_total_host(P)), kBlock, s, k_correct, P, F);
+}
+
+void launch_set_boundary_velocities(const Prm& P, const Fld& F, cudaStream_t s) {
+  MDBS_LAUNCH(K_BOUNDARY, grid_for(faces_total_host(P)), kBlock, s, k_boundary_velocities, P, F);
+}
+
+void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
+  const int nb = grid_for(P.cells, 512);
+  MDBS_LAUNCH(K_STATS, nb, kBlock, s, k_field_stats, P, F, partials, nb);
+  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_stats, partials, nb, scal);
+}
+
+void launch_cfl(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
+  const int nb = grid_for(faces_total_host(P), 512);
+  MDBS_LAUNCH(K_CFL, nb, kBlock, s, k_cfl, P, F, partials);
+  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_max, partials, nb, scal, 4);
+}
+
+}  // namespace mdbs

@@ -1,0 +1,209 @@
+"""Thin ctypes binding of libmdbs.so (include/mdbs.h): argument marshalling only.
+
+Every numerical step runs in the library's CUDA kernels.  Loading fails loudly
+when the library has not been built: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmdbs.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_DIVERGED, ERR_NOT_CONVERGED = 0, -1, -2, -3, -4, -5
+
+
+class Grid(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("h", C.c_double)]
+
+
+class Fluids(C.Structure):
+    _fields_ = [("rho_l", C.c_double), ("mu_l", C.c_double), ("rho_g", C.c_double), ("mu_g", C.c_double),
+                ("sigma", C.c_double), ("g", C.c_double * 3)]
+
+
+class Closures(C.Structure):
+    _fields_ = [("kr_model", C.c_int32), ("pc_model", C.c_int32), ("kr_m", C.c_double),
+                ("a_l_irr", C.c_double), ("a_g_irr", C.c_double), ("pc0", C.c_double),
+                ("pc_beta", C.c_double), ("pc_m", C.c_double), ("a_pc_irr", C.c_double),
+                ("a_pc_max", C.c_double), ("pc_eps", C.c_double)]
+
+
+class Options(C.Structure):
+    _fields_ = [("dt", C.c_double), ("cfl", C.c_double), ("dt_max", C.c_double), ("c_alpha", C.c_double),
+                ("p_tol", C.c_double), ("n_corr", C.c_int32), ("mom_sweeps", C.c_int32),
+                ("max_cg", C.c_int32), ("mg_nu1", C.c_int32), ("mg_nu2", C.c_int32),
+                ("mg_coarse_sweeps", C.c_int32), ("precision", C.c_int32), ("bc", C.c_int32 * 6),
+                ("inlet_u", C.c_double), ("inlet_alpha", C.c_double)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("time", C.c_double), ("dt", C.c_double),
+                ("cg_iters", C.c_int32 * 8), ("cg_resid", C.c_double * 8), ("cg_iters_total", C.c_int64),
+                ("not_converged", C.c_int32), ("mass", C.c_double), ("boundary_in", C.c_double),
+                ("alpha_min", C.c_double), ("alpha_max", C.c_double), ("kernel_launches", C.c_int64)]
+
+
+_D = C.POINTER(C.c_double)
+_lib = None
+
+
+class MdbsError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("mdbs error %d: %s" % (code, msg))
+        self.code = code
+
+
+def lib():
+    """Loads libmdbs.so; raises if it is missing (build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libmdbs.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = C.CDLL(LIB_PATH)
+        L.mdbs_create.argtypes = [C.POINTER(Grid), _D, _D, C.POINTER(Fluids), C.c_double, C.POINTER(Closures),
+                                  C.POINTER(Options), C.POINTER(C.c_void_p)]
+        L.mdbs_set_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
+        L.mdbs_step.argtypes = [C.c_void_p, C.c_int32]
+        L.mdbs_get_fields.argtypes = [C.c_void_p, _D, _D, _D, _D, _D]
+        L.mdbs_destroy.argtypes = [C.c_void_p]
+        L.mdbs_get_stats.argtypes = [C.c_void_p, C.POINTER(Stats)]
+        L.mdbs_last_error.argtypes = [C.c_void_p]
+        L.mdbs_last_error.restype = C.c_char_p
+        L.mdbs_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.mdbs_bytes_required.argtypes = [C.POINTER(Grid), C.c_int32]
+        L.mdbs_bytes_required.restype = C.c_size_t
+        L.mdbs_profile_enable.argtypes = [C.c_void_p, C.c_int32, C.c_int32]
+        L.mdbs_profile_count.restype = C.c_int32
+        L.mdbs_profile_read.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), _D,
+                                        C.POINTER(C.c_int64)]
+        L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
+        L.mdbs_debug_array.restype = C.c_int64
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(_D) if a is not None else None
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def structs_from_case(case):
+    grid = Grid(case.nx, case.ny, case.nz, case.h)
+    fl = Fluids(case.rho_l, case.mu_l, case.rho_g, case.mu_g, case.sigma, (C.c_double * 3)(*case.g))
+    cl = Closures(case.kr_model, case.pc_model, case.kr_m, case.a_l_irr, case.a_g_irr, case.pc0, case.pc_beta,
+                  case.pc_m, case.a_pc_irr, case.a_pc_max, case.pc_eps)
+    op = Options(case.dt, case.cfl, case.dt_max, case.c_alpha, case.p_tol, case.n_corr, case.mom_sweeps,
+                 case.max_cg, case.mg_nu1, case.mg_nu2, case.mg_coarse_sweeps, case.precision,
+                 (C.c_int32 * 6)(*case.bc), case.inlet_u, case.inlet_alpha)
+    return grid, fl, cl, op
+
+
+def bytes_required(case, precision=None):
+    g = Grid(case.nx, case.ny, case.nz, case.h)
+    return int(lib().mdbs_bytes_required(C.byref(g), case.precision if precision is None else precision))
+
+
+def kernel_names():
+    out = []
+    for i in range(lib().mdbs_profile_count()):
+        nm = C.c_char_p()
+        lib().mdbs_profile_read(None, i, C.byref(nm), None, None)
+        out.append(nm.value.decode() if nm.value else "")
+    return out
+
+
+class Simulation:
+    """One device-resident simulation (mdbs_create ... mdbs_destroy)."""
+
+    def __init__(self, case, set_fields=True):
+        self.case = case
+        self.n = (case.nx, case.ny, case.nz)
+        grid, fl, cl, op = structs_from_case(case)
+        phi, k = _f64(case.porosity.ravel()), _f64(case.permeability.ravel())
+        h = C.c_void_p()
+        rc = lib().mdbs_create(C.byref(grid), _ptr(phi), _ptr(k), C.byref(fl), case.theta_deg, C.byref(cl),
+                               C.byref(op), C.byref(h))
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_last_error(None).decode())
+        self.h = h
+        if set_fields:
+            self.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_last_error(self.h).decode())
+
+    def set_fields(self, alpha, ux, uy, uz, p):
+        a, x, y, pp = (_f64(v.ravel()) for v in (alpha, ux, uy, p))
+        z = _f64(uz.ravel()) if uz is not None and self.n[2] > 1 else None
+        self._check(lib().mdbs_set_fields(self.h, _ptr(a), _ptr(x), _ptr(y), _ptr(z), _ptr(pp)))
+
+    def step(self, n=1):
+        self._check(lib().mdbs_step(self.h, int(n)))
+
+    def fields(self):
+        nx, ny, nz = self.n
+        out = {"alpha": np.zeros(nx * ny * nz), "p": np.zeros(nx * ny * nz),
+               "ux": np.zeros((nx + 1) * ny * nz), "uy": np.zeros(nx * (ny + 1) * nz),
+               "uz": np.zeros(nx * ny * (nz + 1)) if nz > 1 else np.zeros(0)}
+        self._check(lib().mdbs_get_fields(self.h, _ptr(out["alpha"]), _ptr(out["ux"]), _ptr(out["uy"]),
+                                          _ptr(out["uz"]) if nz > 1 else None, _ptr(out["p"])))
+        return out
+
+    def stats(self):
+        st = Stats()
+        self._check(lib().mdbs_get_stats(self.h, C.byref(st)))
+        return {"steps": st.steps, "time": st.time, "dt": st.dt,
+                "cg_iters": list(st.cg_iters)[: self.case.n_corr],
+                "cg_resid": list(st.cg_resid)[: self.case.n_corr],
+                "cg_iters_total": st.cg_iters_total, "not_converged": st.not_converged,
+                "mass": st.mass, "boundary_in": st.boundary_in,
+                "alpha_min": st.alpha_min, "alpha_max": st.alpha_max,
+                "kernel_launches": st.kernel_launches}
+
+    def profile(self, enable=True, only=None):
+        """Enables per-kernel event timing (of kernel name `only`, or of every kernel)."""
+        only_id = -1
+        if only is not None:
+            names = kernel_names()
+            only_id = names.index(only)
+        self._check(lib().mdbs_profile_enable(self.h, 1 if enable else 0, only_id))
+
+    def profile_read(self):
+        """{kernel name: (total device ms, timed launches)} since profiling was enabled."""
+        out = {}
+        for i in range(lib().mdbs_profile_count()):
+            nm, ms, cnt = C.c_char_p(), C.c_double(), C.c_int64()
+            self._check(lib().mdbs_profile_read(self.h, i, C.byref(nm), C.byref(ms), C.byref(cnt)))
+            if cnt.value:
+                out[nm.value.decode()] = (ms.value, cnt.value)
+        return out
+
+    def array(self, name):
+        n = lib().mdbs_debug_array(self.h, name.encode(), None, 0)
+        if n < 0:
+            raise KeyError(name)
+        out = np.zeros(n)
+        lib().mdbs_debug_array(self.h, name.encode(), _ptr(out), n)
+        return out
+
+    def set_stream(self, stream_handle: int):
+        self._check(lib().mdbs_set_stream(self.h, C.c_void_p(stream_handle)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mdbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,69 @@
+"""CPU checks of the C-ABI boundary: the library loads, exports every entry
+point that include/mdbs.h declares, and its ctypes binding agrees with the
+header's struct layouts.  No CUDA call is made."""
+import ctypes as C
+import os
+import re
+import subprocess
+import tempfile
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mdbs.h")
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2003_08374_gb300.build import build_library
+    return build_library()
+
+
+def declared_functions():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(mdbs_[a-z_]+)\s*\(", src)))
+
+
+def test_library_exports_every_declared_function(built):
+    names = declared_functions()
+    assert "mdbs_step" in names and len(names) >= 10
+    out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True).stdout
+    exported = set(re.findall(r" T (mdbs_\w+)", out))
+    missing = [n for n in names if n not in exported]
+    assert not missing, missing
+    lib = C.CDLL(built)
+    for n in names:
+        getattr(lib, n)
+
+
+def test_binding_struct_layouts_match_header(built):
+    from paper_2003_08374_gb300 import mdbs
+    structs = {"mdbs_grid": mdbs.Grid, "mdbs_fluids": mdbs.Fluids, "mdbs_closures": mdbs.Closures,
+               "mdbs_options": mdbs.Options, "mdbs_stats": mdbs.Stats}
+    prog = '#include <stdio.h>\n#include <stddef.h>\n#include "mdbs.h"\nint main(void){\n'
+    for s, cls in structs.items():
+        prog += 'printf("%s %%zu\\n", sizeof(%s));\n' % (s, s)
+        for f, _ in cls._fields_:
+            prog += 'printf("%s.%s %%zu\\n", offsetof(%s, %s));\n' % (s, f, s, f)
+    prog += "return 0;}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "t.c")
+        exe = os.path.join(d, "t")
+        open(c, "w").write(prog)
+        subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout
+    got = dict(l.split() for l in out.strip().splitlines())
+    for s, cls in structs.items():
+        assert int(got[s]) == C.sizeof(cls), s
+        for f, _ in cls._fields_:
+            assert int(got["%s.%s" % (s, f)]) == getattr(cls, f).offset, (s, f)
+
+
+def test_bytes_required_is_host_only_and_monotone(built):
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    a = mdbs.bytes_required(W.Case(name="a", nx=32, ny=32, nz=32, h=1e-5))
+    b = mdbs.bytes_required(W.Case(name="b", nx=64, ny=64, nz=64, h=1e-5))
+    assert 0 < a < b
+    assert b / (64 ** 3) < 1200  # device bytes per cell

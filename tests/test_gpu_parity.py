@@ -1,0 +1,150 @@
+"""Parity of the CUDA path (through the C-ABI) with the FP64 oracle on identical
+seeded inputs.  FP64: relative L2 <= 1e-9 on alpha, p and every velocity
+component; mixed precision: <= 1e-6."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOLMIX = 1e-6
+# Both sides solve the pressure equation to a relative residual of 1e-15, which
+# the GMG-PCG reaches: velocities are differences of HbyA and the pressure
+# gradient, so a looser stopping tolerance (1e-12) alone leaves ~1e-8 relative
+# differences in u between any two correct solvers.
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_08374_gb300.build import build_library
+    from oracle.build import build_oracle
+    build_library()
+    build_oracle()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    if nb == 0.0:
+        return float(np.linalg.norm(a))
+    return float(np.linalg.norm(a - b) / nb)
+
+
+def run_both(case, steps):
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    g = mdbs.Simulation(case)
+    o = OracleSim(case)
+    g.step(steps)
+    o.step(steps)
+    return g, o
+
+
+def check_fields(g, o, tol, names=("alpha", "p", "ux", "uy", "uz")):
+    fg, fo = g.fields(), o.fields()
+    errs = {n: rel(fg[n], fo[n]) for n in names if fo[n].size}
+    bad = {n: e for n, e in errs.items() if not e <= tol}
+    assert not bad, errs
+    return errs
+
+
+def test_stage_arrays_after_one_step():
+    """Every intermediate array of one step (fluxes, limiter, closures, momentum
+    coefficients, pressure system) against the oracle's."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.fracture_2d(nx=24, ny=16, p_tol=1e-15, max_cg=500)
+    g, o = run_both(case, 1)
+    for name in ["FLOx", "FLOy", "AFx", "AFy", "aL", "Rp", "Rm", "rho", "rho_old", "mu", "drag", "pc", "cf",
+                 "Ml", "Mg", "mx", "my", "kappa", "aPx", "aPy", "rhs0x", "rhs0y", "Bx", "By", "Tx", "Ty",
+                 "Dd", "b", "hbyax", "hbyay", "nwx", "nwy"]:
+        a, b = g.array(name), o.array(name)
+        assert a.shape == b.shape, name
+        assert rel(a, b) <= 1e-11, (name, rel(a, b))
+    check_fields(g, o, 1e-10)
+
+
+def test_fracture_2d_64_100_steps():
+    """The 2-D 64x64 fracture workload (dx 10 um, dt 1e-6 s, 100 steps), FP64."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.fracture_2d(nx=64, ny=64, p_tol=1e-15, max_cg=500)
+    g, o = run_both(case, 100)
+    check_fields(g, o, TOL64)
+    sg, so = g.stats(), o.stats()
+    assert abs(sg["mass"] - so["mass"]) <= 1e-12 * so["mass"]
+
+
+@pytest.mark.parametrize("shape", [(20, 18, 16), (13, 9, 11), (33, 8, 5)])
+def test_grf_3d_ragged(shape):
+    """3-D log-normal porous block with a fracture, gravity, water into oil; ragged sizes that
+    leave odd cells at every multigrid level."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=shape, seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500)
+    g, o = run_both(case, 10)
+    check_fields(g, o, TOL64)
+
+
+def test_wave_tank_small_cfl():
+    """Small wave tank: Van Genuchten closures, porous barrier, open top, adaptive CFL time step."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.wave_tank(nx=32, ny=6, nz=20, h=5e-3, depth=10, x0=8, barrier=(20, 26, 8), p_tol=1e-15,
+                       max_cg=500, precision=W.FP64, dt=1e-4)
+    g, o = run_both(case, 10)
+    check_fields(g, o, TOL64)
+    assert g.stats()["dt"] == pytest.approx(o.stats()["dt"], rel=1e-9)
+
+
+def test_darcy_domain_and_2d_shapes():
+    from paper_2003_08374_gb300 import workloads as W
+    for shape in [(17, 23, 1), (9, 7, 6)]:
+        case = W.darcy_domain(shape, seed=3, p_tol=1e-15, max_cg=500)
+        g, o = run_both(case, 5)
+        check_fields(g, o, TOL64)
+
+
+@pytest.mark.parametrize("shape", [(1, 1, 1), (3, 2, 1), (1, 5, 1), (2, 2, 2), (5, 1, 3)])
+def test_degenerate_grids(shape):
+    """Single cell, single row / column, 2x2x2: no multigrid coarsening, boundary-only faces."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.darcy_domain(shape, seed=1, p_tol=1e-15, max_cg=200, sat=0.4)
+    g, o = run_both(case, 3)
+    check_fields(g, o, TOL64)
+
+
+def test_mixed_precision_matches_fp64_oracle():
+    """FP32 V-cycle inside FP64 flexible CG, solved to 1e-14: within 1e-6 of the FP64 oracle."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(24, 20, 16), seed=5, corr_len=4.0, frac_w=4, p_tol=1e-14, max_cg=500,
+                    precision=W.MIXED)
+    g, o = run_both(case, 10)
+    check_fields(g, o, TOLMIX)
+
+
+def test_deterministic_rerun():
+    """Fixed reduction order: the same inputs give bit-identical fields."""
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(16, 16, 16), seed=2, corr_len=4.0, frac_w=2, p_tol=1e-10)
+    a = mdbs.Simulation(case)
+    a.step(5)
+    b = mdbs.Simulation(case)
+    b.step(5)
+    fa, fb = a.fields(), b.fields()
+    for n in fa:
+        assert np.array_equal(fa[n], fb[n]), n
+
+
+def test_set_fields_rejects_bad_alpha_and_invalid_create():
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.fracture_2d(nx=8, ny=8)
+    s = mdbs.Simulation(case)
+    bad = case.alpha.copy()
+    bad[3] = 1.5
+    with pytest.raises(mdbs.MdbsError) as e:
+        s.set_fields(bad, case.ux, case.uy, case.uz, case.p)
+    assert e.value.code == mdbs.ERR_ARG
+    c2 = case.replace(bc=(W.WALL,) * 6)
+    with pytest.raises(mdbs.MdbsError):
+        mdbs.Simulation(c2)
+    c3 = case.replace(porosity=np.zeros(64))
+    with pytest.raises(mdbs.MdbsError):
+        mdbs.Simulation(c3)
