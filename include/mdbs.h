@@ -138,7 +138,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
  * Sets the state (saturation alpha_l in [0, 1], Eq. 8; face velocities, Eq. 10;
  * pressure, Eq. 9) from host arrays laid out as above; uz may be NULL in 2-D.
  * Wall and inlet face velocities are overwritten by their boundary values.
- * Resets the statistics.  MDBS_ERR_ARG if alpha is outside [0, 1] or not finite.
+ * Resets the statistics.  MDBS_ERR_ARG if alpha is not finite or lies more than
+ * 1e-9 outside [0, 1] (round-off excursions of a previous step are accepted).
  */
 int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const double* uy,
                     const double* uz, const double* p);

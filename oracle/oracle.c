@@ -1087,7 +1087,7 @@ int orc_set_fields(orc_state* s, const double* alpha, const double* ux, const do
                    const double* uz, const double* p) {
   const double* src[3] = {ux, uy, uz};
   for (long c = 0; c < s->cells; c++) {
-    if (!(alpha[c] >= 0.0 && alpha[c] <= 1.0)) return -1;
+    if (!(alpha[c] >= -1e-9 && alpha[c] <= 1.0 + 1e-9)) return -1; /* round-off of a previous step */
   }
   memcpy(s->alpha, alpha, s->cells * sizeof(double));
   memcpy(s->p, p, s->cells * sizeof(double));

@@ -85,6 +85,8 @@ void prof_begin(int id, cudaStream_t s) {
   p->open_ev = p->event(s);
 }
 
+long long launch_count() { return g_active ? g_active->launches : 0; }
+
 void prof_end(int id, cudaStream_t s) {
   Profiler* p = g_active;
   if (!p || !p->on || p->open_id != id || p->open_ev == (size_t)-1) return;
@@ -106,12 +108,16 @@ struct mdbs_sim {
   size_t arena_bytes;
   PressureSolver* ps;
   double* partials;   // kMaxPartials * 4
-  double* scal;       // step scalars: 0 mass, 1 amin, 2 amax, 3 bad, 4 umax, 5 boundary_in
-  double* host_scal;  // pinned
-  double dt, time;
+  double* scal;       // device step scalars (kSlot* in mdbs_internal.cuh)
+  double* host_scal;  // pinned copy of scal
   mdbs_stats st;
   bool fields_set;
   std::string err;
+  // the whole step captured as one CUDA graph (CG loops as conditional WHILE nodes)
+  cudaStream_t cap_stream;
+  cudaGraphExec_t step_exec;
+  long long graph_static_launches;  // kernels outside the CG loops per step
+  long long graph_body_launches;    // kernels per CG iteration
 };
 
 static thread_local std::string g_create_error;
@@ -192,7 +198,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
     F.utmp[d] = fd();
   }
   double* partials = (double*)take(4 * kMaxPartials * 8);
-  double* scal = (double*)take(16 * 8);
+  double* scal = (double*)take(kNumSlots * 8);
   if (s) {
     s->F = F;
     s->partials = partials;
@@ -219,68 +225,84 @@ int cuda_fail(mdbs_sim* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
   } while (0)
 
+// copies the device scalars and the statistics they hold; checks health
 int refresh_stats(mdbs_sim* s) {
-  launch_field_stats(s->P, s->F, s->partials, s->scal, s->stream);
-  CK(cudaMemcpyAsync(s->host_scal, s->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaMemcpyAsync(s->host_scal, s->scal, kNumSlots * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
   CK(cudaStreamSynchronize(s->stream));
+  const double* h = s->host_scal;
+  s->st.mass = h[kSlotMass];
+  s->st.alpha_min = h[kSlotAmin];
+  s->st.alpha_max = h[kSlotAmax];
+  s->st.boundary_in = h[kSlotInflow];
+  s->st.dt = h[kSlotDt];
+  s->st.time = h[kSlotTime];
+  for (int c = 0; c < s->opt.n_corr && c < 8; c++) {
+    s->st.cg_iters[c] = (int32_t)h[kSlotIters + c];
+    s->st.cg_resid[c] = h[kSlotResid + c];
+  }
+  s->st.cg_iters_total = (int64_t)h[kSlotItersTotal];
+  s->st.not_converged = (int32_t)h[kSlotNotConverged];
   s->st.kernel_launches = s->prof.launches;
-  s->st.mass = s->host_scal[0];
-  s->st.alpha_min = s->host_scal[1];
-  s->st.alpha_max = s->host_scal[2];
-  s->st.boundary_in = s->host_scal[5];
-  if (s->host_scal[3] != 0.0) return fail(s, MDBS_ERR_DIVERGED, "non-finite alpha or pressure");
+  if (h[kSlotBad] != 0.0) return fail(s, MDBS_ERR_DIVERGED, "non-finite alpha or pressure");
   return MDBS_OK;
 }
 
-int one_step(mdbs_sim* s) {
+// Enqueues one time step (section 3.2) on st.  capture: st is capturing a graph.
+int record_step(mdbs_sim* s, cudaStream_t st, bool capture) {
   Prm& P = s->P;
   Fld& F = s->F;
-  cudaStream_t st = s->stream;
-  const double dt = s->dt;
   // 1. saturation (Eq. 15) by flux-corrected transport
-  launch_alpha_step(P, F, dt, s->partials, s->scal, 5, st);
-  // 3. properties at alpha^{k+1}; the old density stays for the Euler source (Eq. 46)
-  std::swap(F.rho, F.rho_old);
+  launch_alpha_step(P, F, s->partials, s->scal, st);
+  // 3. properties at alpha^{k+1} (the old density is kept for the Euler source of Eq. 46)
   launch_properties(P, F, st);
   // 4. momentum predictor (Eq. 50) from u^k and p^k
-  launch_momentum_assemble(P, F, dt, st);
-  for (int it = 0; it < s->opt.mom_sweeps; it++) {
-    launch_jacobi_sweep(P, F, st);
-    for (int d = 0; d < 3; d++) std::swap(F.u[d], F.utmp[d]);
-  }
+  launch_momentum_assemble(P, F, s->scal, st);
+  launch_jacobi_sweeps(P, F, s->opt.mom_sweeps, st);
   // 5. PISO correctors (Eqs. 51-53)
   for (int c = 0; c < s->opt.n_corr; c++) {
     launch_hbya(P, F, st);
     launch_pressure_assemble(P, F, st);
-    double res = 0.0;
-    int it = pressure_solve(s->ps, P, F, s->opt.p_tol, s->opt.max_cg, s->opt.mg_nu1, s->opt.mg_nu2,
-                            s->opt.mg_coarse_sweeps, &res, st);
-    if (it < 0) return cuda_fail(s, cudaGetLastError(), "pressure_solve");
-    if (c < 8) {
-      s->st.cg_iters[c] = it;
-      s->st.cg_resid[c] = res;
-    }
-    s->st.cg_iters_total += it;
-    if (!(res <= s->opt.p_tol)) s->st.not_converged++;
+    cudaError_t e = pressure_solve(s->ps, P, F, s->opt.p_tol, s->opt.max_cg, s->opt.mg_nu1, s->opt.mg_nu2,
+                                   s->opt.mg_coarse_sweeps, s->scal, c, capture, st);
+    if (e != cudaSuccess) return cuda_fail(s, e, "pressure_solve");
     launch_correct(P, F, st);
   }
+  // 6. time and next time step; statistics and health sentinel
+  launch_time_advance(P, F, s->opt.cfl, s->opt.dt_max, s->partials, s->scal, st);
+  launch_field_stats(P, F, s->partials, s->scal, st);
   CK(cudaGetLastError());
-  // 6. time step
-  s->time += dt;
-  s->st.steps++;
-  if (s->opt.cfl > 0.0) {
-    launch_cfl(P, F, s->partials, s->scal, st);
-    CK(cudaMemcpyAsync(s->host_scal + 4, s->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
-    const double umax = s->host_scal[4];
-    double dtn = umax > 0.0 ? s->opt.cfl * P.h / umax : s->opt.dt_max;
-    dtn = fmin(dtn, 1.2 * dt);
-    dtn = fmin(dtn, s->opt.dt_max);
-    s->dt = dtn;
+  return MDBS_OK;
+}
+
+// captures the step graph once (lazily) and counts its kernels
+int ensure_graph(mdbs_sim* s) {
+  if (s->step_exec) return MDBS_OK;
+  if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
+  long long before = s->prof.launches;
+  bool was_on = s->prof.on;
+  s->prof.on = false;
+  CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
+  int rc = record_step(s, s->cap_stream, true);
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
+  s->prof.on = was_on;
+  long long captured = s->prof.launches - before;
+  s->prof.launches = before;
+  if (rc != MDBS_OK) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
   }
-  s->st.time = s->time;
-  s->st.dt = s->dt;
-  return refresh_stats(s);
+  if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&s->step_exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    s->step_exec = nullptr;
+    return cuda_fail(s, e, "cudaGraphInstantiate");
+  }
+  // kernels per CG iteration: count one body recording without launching it
+  s->graph_body_launches = s->ps ? pressure_body_launches(s->ps) : 0;
+  s->graph_static_launches = captured - s->opt.n_corr * s->graph_body_launches;
+  return MDBS_OK;
 }
 
 }  // namespace
@@ -362,7 +384,6 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.c_alpha = op->c_alpha;
   s->opt = *op;
   s->precision = op->precision;
-  s->dt = op->dt;
   s->stream = nullptr;
 
   s->arena_bytes = carve(nullptr, L, nullptr);
@@ -376,7 +397,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   }
   cudaMemset(s->arena, 0, s->arena_bytes);
   carve(s, L, (char*)s->arena);
-  e = cudaMallocHost(&s->host_scal, 16 * sizeof(double));
+  e = cudaMallocHost(&s->host_scal, kNumSlots * sizeof(double));
   if (e == cudaSuccess) s->ps = pressure_create(P, s->precision, &e);
   if (e != cudaSuccess) {
     int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
@@ -410,8 +431,11 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   if (!s) return MDBS_ERR_ARG;
   if (!alpha || !ux || !uy || !p || (s->P.dim == 3 && !uz)) return fail(s, MDBS_ERR_ARG, "NULL field");
   Activate act(s);
+  // round-off excursions of the flux-corrected update (|.| ~ 1e-30) must survive a
+  // get_fields / set_fields round trip, so the check allows 1e-9 outside [0, 1]
   for (long long c = 0; c < s->P.cells; c++)
-    if (!(alpha[c] >= 0.0 && alpha[c] <= 1.0)) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1]");
+    if (!(alpha[c] >= -1e-9 && alpha[c] <= 1.0 + 1e-9))
+      return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-9)");
   const double* src[3] = {ux, uy, uz};
   CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(s->F.p, p, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
@@ -419,13 +443,13 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
     CK(cudaMemcpyAsync(s->F.u[d], src[d], s->P.nf[d] * 8, cudaMemcpyHostToDevice, s->stream));
   launch_set_boundary_velocities(s->P, s->F, s->stream);
   launch_properties(s->P, s->F, s->stream);
-  CK(cudaMemsetAsync(s->scal, 0, 16 * sizeof(double), s->stream));
+  for (int i = 0; i < kNumSlots; i++) s->host_scal[i] = 0.0;
+  s->host_scal[kSlotDt] = s->opt.dt;
+  CK(cudaMemcpyAsync(s->scal, s->host_scal, kNumSlots * sizeof(double), cudaMemcpyHostToDevice, s->stream));
+  launch_field_stats(s->P, s->F, s->partials, s->scal, s->stream);
   CK(cudaGetLastError());
   memset(&s->st, 0, sizeof(s->st));
   s->prof.launches = 0;
-  s->dt = s->opt.dt;
-  s->time = 0.0;
-  s->st.dt = s->dt;
   s->fields_set = true;
   return refresh_stats(s);
 }
@@ -435,11 +459,26 @@ int mdbs_step(mdbs_sim* s, int32_t n) {
   if (n < 1) return fail(s, MDBS_ERR_ARG, "n must be >= 1");
   if (!s->fields_set) return fail(s, MDBS_ERR_ARG, "mdbs_set_fields has not been called");
   Activate act(s);
-  for (int i = 0; i < n; i++) {
-    int rc = one_step(s);
-    if (rc != MDBS_OK) return rc;
+  if (s->prof.on) {
+    // per-kernel event timing needs individual launches: host-driven step
+    for (int i = 0; i < n; i++) {
+      int rc = record_step(s, s->stream, false);
+      if (rc != MDBS_OK) return rc;
+      s->st.steps++;
+    }
+    return refresh_stats(s);
   }
-  return MDBS_OK;
+  int rc = ensure_graph(s);
+  if (rc != MDBS_OK) return rc;
+  const double it0 = s->host_scal[kSlotItersTotal];
+  for (int i = 0; i < n; i++) CK(cudaGraphLaunch(s->step_exec, s->stream));
+  s->st.steps += n;
+  rc = refresh_stats(s);
+  // kernels launched by the graphs: the fixed part of every step plus the CG bodies run
+  s->prof.launches += (long long)n * s->graph_static_launches +
+                      (long long)(s->host_scal[kSlotItersTotal] - it0) * s->graph_body_launches;
+  s->st.kernel_launches = s->prof.launches;
+  return rc;
 }
 
 int mdbs_get_fields(const mdbs_sim* cs, double* alpha, double* ux, double* uy, double* uz, double* p) {
@@ -457,6 +496,11 @@ int mdbs_get_fields(const mdbs_sim* cs, double* alpha, double* ux, double* uy, d
 void mdbs_destroy(mdbs_sim* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
+  if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
+  if (s->cap_stream) {
+    cudaStreamSynchronize(s->cap_stream);
+    cudaStreamDestroy(s->cap_stream);
+  }
   pressure_destroy(s->ps);
   if (s->host_scal) cudaFreeHost(s->host_scal);
   cudaFree(s->arena);

@@ -11,6 +11,11 @@ constexpr int kMaxLevels = 16;
 constexpr int kBlock = 256;
 constexpr int kMaxPartials = 2048;  // blocks per deterministic reduction
 
+// slots of the per-simulation device scalar array
+constexpr int kSlotMass = 0, kSlotAmin = 1, kSlotAmax = 2, kSlotBad = 3, kSlotUmax = 4, kSlotInflow = 5,
+              kSlotDt = 6, kSlotTime = 7, kSlotIters = 8 /* 8 correctors */, kSlotResid = 16 /* 8 */,
+              kSlotItersTotal = 24, kSlotNotConverged = 25, kNumSlots = 32;
+
 // Geometry and physical parameters, passed by value to every kernel.
 struct Prm {
   int n[3];      // cells per axis
@@ -111,6 +116,7 @@ enum KernelId {
 extern const char* const kKernelNames[K_COUNT];
 void prof_begin(int id, cudaStream_t s);
 void prof_end(int id, cudaStream_t s);
+long long launch_count();  // kernels launched so far by the active simulation
 
 #define MDBS_LAUNCH(ID, GRID, BLOCK, STREAM, KERNEL, ...)   \
   do {                                                     \
@@ -121,16 +127,17 @@ void prof_end(int id, cudaStream_t s);
 
 // ---------------------------------------------------------------- launchers
 // step_kernels.cu
-void launch_alpha_step(const Prm& P, const Fld& F, double dt, double* partials, double* scal, int slot,
-                       cudaStream_t s);
+// (dt, time and the statistics live in the device scalar array, see kSlot*)
+void launch_alpha_step(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
 void launch_properties(const Prm& P, const Fld& F, cudaStream_t s);
-void launch_momentum_assemble(const Prm& P, const Fld& F, double dt, cudaStream_t s);
-void launch_jacobi_sweep(const Prm& P, const Fld& F, cudaStream_t s);  // u -> utmp
+void launch_momentum_assemble(const Prm& P, const Fld& F, const double* scal, cudaStream_t s);
+void launch_jacobi_sweeps(const Prm& P, const Fld& F, int sweeps, cudaStream_t s);  // result in F.u
 void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s);
 void launch_correct(const Prm& P, const Fld& F, cudaStream_t s);
 void launch_set_boundary_velocities(const Prm& P, const Fld& F, cudaStream_t s);
 void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
-void launch_cfl(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
+void launch_time_advance(const Prm& P, const Fld& F, double cfl, double dt_max, double* partials, double* scal,
+                         cudaStream_t s);
 void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s);
 
 // pressure.cu
@@ -139,9 +146,16 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err);
 void pressure_destroy(PressureSolver* ps);
 size_t pressure_bytes(const int n[3], int precision);
 void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s);
-// solves A p = b (level-0 arrays of F) by GMG-preconditioned CG; returns iterations,
-// writes the final relative residual; negative on a CUDA error
-int pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1, int nu2,
-                   int coarse_sweeps, double* resid, cudaStream_t s);
+// Enqueues the solve of A p = b (level-0 arrays of F) by GMG-preconditioned CG on s.
+// Iterations and the final relative residual of corrector `corr` go to
+// step_scal[kSlotIters + corr] / [kSlotResid + corr] (totals accumulate).
+// capture == false: the CG loop is driven from the host (one sync per iteration);
+// capture == true: s is capturing a graph and the loop becomes a conditional
+// WHILE node evaluated on the device.  Returns a CUDA error code.
+cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1,
+                           int nu2, int coarse_sweeps, double* step_scal, int corr, bool capture,
+                           cudaStream_t s);
+// kernels in one CG iteration, as counted during the last capture
+long long pressure_body_launches(const PressureSolver* ps);
 
 }  // namespace mdbs

@@ -299,22 +299,29 @@ __global__ void k_dots_rz(long long n, const double* __restrict__ r, const doubl
   }
 }
 
-// d = z + beta d, beta from the scalars (first: d = z)
+// CG scalars on the device
+constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6, kRZold = 7, kIt = 8;
+
+// d = z + beta d; the first iteration (counter 0) takes d = z
 __global__ void k_update_d(long long n, const double* __restrict__ scal, const double* __restrict__ z,
-                           double* __restrict__ dv, int first, int flexible) {
+                           double* __restrict__ dv, int flexible) {
+  const bool first = scal[kIt] == 0.0;
   double be = 0.0;
-  if (!first) be = flexible ? -scal[5] * scal[4] / scal[7] : scal[2] / scal[7];
+  if (!first) be = flexible ? -scal[kAlpha] * scal[kZQ] / scal[kRZold] : scal[kRZ] / scal[kRZold];
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
        c += (long long)gridDim.x * blockDim.x)
     dv[c] = first ? z[c] : z[c] + be * dv[c];
 }
 
-// scalar finalizers (one block, fixed summation order)
-// mode 0: scal[0] = bb, scal[1] = rr  (two channels)
-// mode 1: scal[3] = dq, scal[5] = scal[2] / dq
-// mode 2: scal[1] = rr
-// mode 3: scal[7] = scal[2]; scal[2] = rz; scal[4] = zq (second channel when present)
-__global__ void k_finalize(const double* __restrict__ partials, int nb, double* scal, int mode, int two) {
+// Scalar finalizers (one block, fixed summation order).  The loop condition
+// "not converged, below max_it, finite" is written to scal[kCond] and, inside a
+// captured graph, to the WHILE node's conditional handle.
+// mode 0: rr, bb after the initial residual; iteration counter = 0
+// mode 1: dq, alpha = rz / dq
+// mode 2: rr after the update; counter += 1
+// mode 3: rz_old = rz; rz (and zq when two channels)
+__global__ void k_finalize(const double* __restrict__ partials, int nb, double* scal, int mode, int two,
+                           double tol, int max_it, cudaGraphConditionalHandle handle, int use_handle) {
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
     a += partials[i];
@@ -323,19 +330,50 @@ __global__ void k_finalize(const double* __restrict__ partials, int nb, double* 
   a = block_sum(a);
   if (two) b = block_sum(b);
   if (threadIdx.x != 0) return;
-  if (mode == 0) {
-    scal[1] = a;
-    scal[0] = b;
-  } else if (mode == 1) {
-    scal[3] = a;
-    scal[5] = scal[2] / a;
-  } else if (mode == 2) {
-    scal[1] = a;
-  } else {
-    scal[7] = scal[2];
-    scal[2] = a;
-    scal[4] = two ? b : 0.0;
+  if (mode == 1) {
+    scal[kDQ] = a;
+    scal[kAlpha] = scal[kRZ] / a;
+    return;
   }
+  if (mode == 3) {
+    scal[kRZold] = scal[kRZ];
+    scal[kRZ] = a;
+    scal[kZQ] = two ? b : 0.0;
+    return;
+  }
+  double it;
+  if (mode == 0) {
+    scal[kRR] = a;
+    scal[kBB] = b;
+    it = 0.0;
+  } else {
+    scal[kRR] = a;
+    it = scal[kIt] + 1.0;
+  }
+  scal[kIt] = it;
+  const double bb = scal[kBB];
+  const bool done = bb == 0.0 || sqrt(a) <= tol * sqrt(bb) || it >= (double)max_it || !(a == a);
+  scal[kCond] = done ? 0.0 : 1.0;
+  if (use_handle) cudaGraphSetConditional(handle, done ? 0u : 1u);
+}
+
+// b = 0 has the solution p = 0 whatever the initial guess
+__global__ void k_zero_if_b0(long long n, const double* __restrict__ scal, double* __restrict__ x) {
+  if (scal[kBB] != 0.0) return;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+       c += (long long)gridDim.x * blockDim.x)
+    x[c] = 0.0;
+}
+
+// iterations and relative residual of corrector corr into the step scalars
+__global__ void k_record(const double* __restrict__ scal, double* step, int corr, double tol) {
+  if (threadIdx.x != 0) return;
+  const double bb = scal[kBB];
+  const double res = bb == 0.0 ? 0.0 : sqrt(scal[kRR] / bb);
+  step[kSlotIters + corr] = scal[kIt];
+  step[kSlotResid + corr] = res;
+  step[kSlotItersTotal] += scal[kIt];
+  if (!(res <= tol)) step[kSlotNotConverged] += 1.0;
 }
 
 __global__ void k_copy_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
@@ -360,7 +398,11 @@ struct PressureSolver {
   double* scal;
   double* host_scal;  // pinned
   void* block;        // single device allocation
+  cudaStream_t body_stream;  // captures the body of the CG WHILE node
+  long long body_launches;   // kernels per CG iteration (counted while capturing)
 };
+
+long long pressure_body_launches(const PressureSolver* ps) { return ps->body_launches; }
 
 static int plan_levels(const int n0[3], int dims[kMaxLevels][3], int cz[kMaxLevels][3]) {
   int nlev = 1;
@@ -469,12 +511,20 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
     delete ps;
     return nullptr;
   }
+  *err = cudaStreamCreateWithFlags(&ps->body_stream, cudaStreamNonBlocking);
+  if (*err != cudaSuccess) {
+    cudaFreeHost(ps->host_scal);
+    cudaFree(ps->block);
+    delete ps;
+    return nullptr;
+  }
   solver_layout(P.n, ps->precision, ps, (char*)ps->block);
   return ps;
 }
 
 void pressure_destroy(PressureSolver* ps) {
   if (!ps) return;
+  cudaStreamDestroy(ps->body_stream);
   cudaFree(ps->block);
   cudaFreeHost(ps->host_scal);
   delete ps;
@@ -527,8 +577,8 @@ static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, cudaStream_
   }
 }
 
-int pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1, int nu2,
-                   int cs, double* resid, cudaStream_t s) {
+cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1,
+                           int nu2, int cs, double* step_scal, int corr, bool capture, cudaStream_t s) {
   const long long n = P.cells;
   const int nb = grid_for(n, kMaxPartials);
   const int flexible = ps->precision != 0;
@@ -550,57 +600,79 @@ int pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, i
     MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.diag, L0.diag, n);
     build_hierarchy(ps->lf, ps->nlev, s);
   }
-  auto precondition = [&]() {
+  cudaGraphConditionalHandle handle = 0;
+  cudaGraph_t graph = nullptr;
+  if (capture) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    if (st != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    e = cudaGraphConditionalHandleCreate(&handle, graph, 0, 0);
+    if (e != cudaSuccess) return e;
+  }
+  const int use = capture ? 1 : 0;
+  // initial residual and loop condition
+  MDBS_LAUNCH(K_RESID0, nb, kBlock, s, k_resid0, P, F, x, ps->r, ps->partials, nb);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 0, 1, tol, max_it, handle, use);
+  MDBS_LAUNCH(K_ZERO, nb, kBlock, s, k_zero_if_b0, n, ps->scal, x);
+  // one CG iteration, preconditioner first; the last finalizer decides whether to continue
+  auto body = [&](cudaStream_t bs) {
     if (!flexible) {
-      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, s);
+      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, bs);
     } else {
       const int g = grid_for(n);
-      MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_copy_d2f, ps->r, ps->lf[0].b, n);
-      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, s);
-      MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_copy_f2d, ps->lf[0].x, ps->z, n);
+      MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_d2f, ps->r, ps->lf[0].b, n);
+      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, bs);
+      MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_f2d, ps->lf[0].x, ps->z, n);
     }
+    MDBS_LAUNCH(K_DOTS, nb, kBlock, bs, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, flexible);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 3, flexible, tol, max_it,
+                handle, use);
+    MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, bs, k_update_d, n, ps->scal, ps->z, ps->dv, flexible);
+    MDBS_LAUNCH(K_SPMV_DOT, nb, kBlock, bs, k_spmv_dot, P, F, ps->dv, ps->q, ps->partials);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 1, 0, tol, max_it, handle, use);
+    MDBS_LAUNCH(K_UPDATE_XR, nb, kBlock, bs, k_update_xr, n, ps->scal, x, ps->r, ps->dv, ps->q, ps->partials);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 2, 0, tol, max_it, handle, use);
   };
-  auto read_scalars = [&]() -> bool {
-    if (cudaMemcpyAsync(ps->host_scal, ps->scal, 8 * sizeof(double), cudaMemcpyDeviceToHost, s) != cudaSuccess)
-      return false;
-    return cudaStreamSynchronize(s) == cudaSuccess;
-  };
-  MDBS_LAUNCH(K_RESID0, nb, kBlock, s, k_resid0, P, F, x, ps->r, ps->partials, nb);
-  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 0, 1);
-  if (!read_scalars()) return -1;
-  const double bn = sqrt(ps->host_scal[0]);
-  double rn = sqrt(ps->host_scal[1]);
-  if (bn == 0.0) {
-    cudaMemsetAsync(x, 0, n * sizeof(double), s);
-    *resid = 0.0;
-    return 0;
+  if (capture) {
+    cudaStreamCaptureStatus st;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &st, nullptr, &graph, &deps, nullptr, &ndeps);
+    if (e != cudaSuccess) return e;
+    cudaGraphNodeParams prm = {};
+    prm.type = cudaGraphNodeTypeConditional;
+    prm.conditional.handle = handle;
+    prm.conditional.type = cudaGraphCondTypeWhile;
+    prm.conditional.size = 1;
+    cudaGraphNode_t node;
+    e = cudaGraphAddNode(&node, graph, deps, nullptr, ndeps, &prm);
+    if (e != cudaSuccess) return e;
+    cudaGraph_t body_graph = prm.conditional.phGraph_out[0];
+    e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
+    if (e != cudaSuccess) return e;
+    e = cudaStreamBeginCaptureToGraph(ps->body_stream, body_graph, nullptr, nullptr, 0,
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    const long long c0 = launch_count();
+    body(ps->body_stream);
+    ps->body_launches = launch_count() - c0;
+    cudaGraph_t out = nullptr;
+    e = cudaStreamEndCapture(ps->body_stream, &out);
+    if (e != cudaSuccess) return e;
+  } else {
+    for (;;) {
+      cudaError_t e = cudaMemcpyAsync(ps->host_scal, ps->scal + kCond, sizeof(double), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) return e;
+      if (ps->host_scal[0] == 0.0) break;
+      body(s);
+    }
   }
-  if (rn <= tol * bn) {
-    *resid = rn / bn;
-    return 0;
-  }
-  precondition();
-  MDBS_LAUNCH(K_DOTS, nb, kBlock, s, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, 0);
-  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 3, 0);
-  MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, s, k_update_d, n, ps->scal, ps->z, ps->dv, 1, flexible);
-  int it = 0;
-  while (it < max_it) {
-    it++;
-    MDBS_LAUNCH(K_SPMV_DOT, nb, kBlock, s, k_spmv_dot, P, F, ps->dv, ps->q, ps->partials);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 1, 0);
-    MDBS_LAUNCH(K_UPDATE_XR, nb, kBlock, s, k_update_xr, n, ps->scal, x, ps->r, ps->dv, ps->q, ps->partials);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 2, 0);
-    if (!read_scalars()) return -1;
-    rn = sqrt(ps->host_scal[1]);
-    if (!(rn == rn)) break;
-    if (rn <= tol * bn) break;
-    precondition();
-    MDBS_LAUNCH(K_DOTS, nb, kBlock, s, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, flexible);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 3, flexible);
-    MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, s, k_update_d, n, ps->scal, ps->z, ps->dv, 0, flexible);
-  }
-  *resid = rn / bn;
-  return cudaGetLastError() == cudaSuccess ? it : -1;
+  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_record, ps->scal, step_scal, corr, tol);
+  return cudaGetLastError();
 }
 
 }  // namespace mdbs

@@ -154,9 +154,10 @@ __global__ void k_alpha_flux(Prm P, Fld F, double* __restrict__ partials) {
 }
 
 // low-order (upwind) update
-__global__ void k_alpha_lo(Prm P, Fld F, double dt) {
+__global__ void k_alpha_lo(Prm P, Fld F, const double* __restrict__ dtp) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.cells) return;
+  const double dt = *dtp;
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double div = 0.0;
@@ -172,9 +173,10 @@ __global__ void k_alpha_lo(Prm P, Fld F, double dt) {
 // low-order solutions over the cell and its face neighbours (within [0, 1]) in
 // solid-free cells; [0, 1] in porous cells, where the relative flux is the
 // physical Darcy phase flux of Eq. 34.
-__global__ void k_alpha_limit(Prm P, Fld F, double dt) {
+__global__ void k_alpha_limit(Prm P, Fld F, const double* __restrict__ dtp) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.cells) return;
+  const double dt = *dtp;
   int i, j, k;
   decode_cell(P, c, i, j, k);
   const double a0 = F.alpha[c], aLc = F.aL[c];
@@ -221,9 +223,10 @@ __device__ __forceinline__ double limited_af(const Prm& P, const Fld& F, int d, 
   return lam * a;
 }
 
-__global__ void k_alpha_update(Prm P, Fld F, double dt) {
+__global__ void k_alpha_update(Prm P, Fld F, const double* __restrict__ dtp) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.cells) return;
+  const double dt = *dtp;
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double corr = 0.0;
@@ -235,13 +238,13 @@ __global__ void k_alpha_update(Prm P, Fld F, double dt) {
   F.alpha[c] = F.aL[c] - dt / (F.phi[c] * P.V) * corr;
 }
 
-// deterministic final sum of nb partials: scal[slot] += scale * sum (or = when !accumulate)
+// deterministic final sum of nb partials: scal[slot] += dt * sum
 __global__ void k_finalize_sum(const double* __restrict__ partials, int nb, double* scal, int slot,
-                               double scale, int accumulate) {
+                               const double* __restrict__ dtp) {
   double v = 0.0;
   for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[b];
   v = block_sum(v);
-  if (threadIdx.x == 0) scal[slot] = (accumulate ? scal[slot] : 0.0) + scale * v;
+  if (threadIdx.x == 0) scal[slot] += *dtp * v;
 }
 
 // ------------------------------------------------------------------ closures
@@ -249,6 +252,7 @@ __global__ void k_finalize_sum(const double* __restrict__ partials, int nb, doub
 __global__ void k_properties(Prm P, Fld F) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= P.cells) return;
+  F.rho_old[c] = F.rho[c];  // the density of the previous step feeds the Euler source (Eq. 46)
   const double a = F.alpha[c];
   F.mu[c] = a * P.mu_l + (1.0 - a) * P.mu_g;
   if (F.is_free[c]) {
@@ -331,7 +335,7 @@ __global__ void k_curvature(Prm P, Fld F) {
 // coefficients (implicit upwind convection of rho u u / phi^2 and viscous
 // diffusion), and rhs0 = Euler source + explicit transpose viscous stress +
 // body force (gravity rho g and capillary force F_c, Eqs. 38, 43, 45).
-__global__ void k_momentum_assemble(Prm P, Fld F, double dt) {
+__global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int d, i, j, k;
   long long f;
@@ -368,6 +372,7 @@ __global__ void k_momentum_assemble(Prm P, Fld F, double dt) {
   }
   F.B[d][f] = Bf;
   const double uf = F.u[d][f];
+  const double dt = *dtp;
   const double at = V * rhof / (phif * dt);
   const double S = V * rhoo * uf / (phif * dt);
   const double cconv = V * rhof / (phif * phif * h);
@@ -457,20 +462,32 @@ __device__ __forceinline__ double face_dp(const Prm& P, const double* __restrict
   return pr - pl;
 }
 
-// one Jacobi sweep of the momentum predictor (Eq. 50): utmp = (H(u) - V grad p^k)/a_P
-__global__ void k_jacobi(Prm P, Fld F) {
+struct Faces3 {
+  double* a[3];
+};
+
+// one Jacobi sweep of the momentum predictor (Eq. 50): out = (H(in) - V grad p^k)/a_P
+__global__ void k_jacobi(Prm P, Fld F, Faces3 in, Faces3 out) {
   long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
   const int cd = d == 0 ? i : (d == 1 ? j : k);
   if (face_kind(P, d, cd) == 1) {
-    F.utmp[d][f] = F.u[d][f];
+    out.a[d][f] = in.a[d][f];
     return;
   }
-  const double* u[3] = {F.u[0], F.u[1], F.u[2]};
+  const double* u[3] = {in.a[0], in.a[1], in.a[2]};
   const double hs = face_H(P, F, u, d, i, j, k, f);
-  F.utmp[d][f] = (hs - P.V * face_dp(P, F.p, d, i, j, k) / P.h) / F.aP[d][f];
+  out.a[d][f] = (hs - P.V * face_dp(P, F.p, d, i, j, k) / P.h) / F.aP[d][f];
+}
+
+__global__ void k_copy_faces(Prm P, Faces3 src, Faces3 dst) {
+  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  dst.a[d][f] = src.a[d][f];
 }
 
 // HbyA = H(u)/a_P (Eq. 51 without the pressure gradient)
@@ -586,11 +603,23 @@ __global__ void k_cfl(Prm P, Fld F, double* __restrict__ partials) {
   }
 }
 
-__global__ void k_finalize_max(const double* __restrict__ partials, int nb, double* scal, int slot) {
+// CFL time step (section 3.2): time += dt; dt = min(cfl h / max|u/phi|, 1.2 dt, dt_max)
+__global__ void k_finalize_cfl(const double* __restrict__ partials, int nb, double* scal, double cfl, double h,
+                               double dt_max) {
   if (threadIdx.x != 0) return;
   double a = 0.0;
   for (int b = 0; b < nb; b++) a = fmax(a, partials[b]);
-  scal[slot] = a;
+  const double dt = scal[kSlotDt];
+  scal[kSlotUmax] = a;
+  scal[kSlotTime] += dt;
+  double dtn = a > 0.0 ? cfl * h / a : dt_max;
+  dtn = fmin(dtn, 1.2 * dt);
+  dtn = fmin(dtn, dt_max);
+  scal[kSlotDt] = dtn;
+}
+
+__global__ void k_advance_time(double* scal) {
+  if (threadIdx.x == 0) scal[kSlotTime] += scal[kSlotDt];
 }
 
 // static geometry: solid-free flag (porosity exactly 1) and, in free cells with a
@@ -629,21 +658,17 @@ __global__ void k_static_geometry(Prm P, const double* __restrict__ phi, uint8_t
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s) {
-  MDBS_LAUNCH(K_STATIC, grid_for(P.cells), kBlock, s, k_static_geometry, P, phi, is_free, nw[0], nw[1], nw[2]);
-}
-
 static long long faces_total_host(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P.nf[2] : 0); }
 
-void launch_alpha_step(const Prm& P, const Fld& F, double dt, double* partials, double* scal, int slot,
-                       cudaStream_t s) {
+void launch_alpha_step(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
+  const double* dtp = scal + kSlotDt;
   const int gf = grid_for(faces_total_host(P), kMaxPartials);
   MDBS_LAUNCH(K_ALPHA_FLUX, gf, kBlock, s, k_alpha_flux, P, F, partials);
-  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize_sum, partials, gf, scal, slot, dt, 1);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize_sum, partials, gf, scal, kSlotInflow, dtp);
   const int gc = grid_for(P.cells);
-  MDBS_LAUNCH(K_ALPHA_LO, gc, kBlock, s, k_alpha_lo, P, F, dt);
-  MDBS_LAUNCH(K_ALPHA_LIMIT, gc, kBlock, s, k_alpha_limit, P, F, dt);
-  MDBS_LAUNCH(K_ALPHA_UPDATE, gc, kBlock, s, k_alpha_update, P, F, dt);
+  MDBS_LAUNCH(K_ALPHA_LO, gc, kBlock, s, k_alpha_lo, P, F, dtp);
+  MDBS_LAUNCH(K_ALPHA_LIMIT, gc, kBlock, s, k_alpha_limit, P, F, dtp);
+  MDBS_LAUNCH(K_ALPHA_UPDATE, gc, kBlock, s, k_alpha_update, P, F, dtp);
 }
 
 void launch_properties(const Prm& P, const Fld& F, cudaStream_t s) {
@@ -653,12 +678,22 @@ void launch_properties(const Prm& P, const Fld& F, cudaStream_t s) {
   MDBS_LAUNCH(K_CURVATURE, gc, kBlock, s, k_curvature, P, F);
 }
 
-void launch_momentum_assemble(const Prm& P, const Fld& F, double dt, cudaStream_t s) {
-  MDBS_LAUNCH(K_MOM_ASSEMBLE, grid_for(faces_total_host(P)), kBlock, s, k_momentum_assemble, P, F, dt);
+void launch_momentum_assemble(const Prm& P, const Fld& F, const double* scal, cudaStream_t s) {
+  MDBS_LAUNCH(K_MOM_ASSEMBLE, grid_for(faces_total_host(P)), kBlock, s, k_momentum_assemble, P, F,
+              scal + kSlotDt);
 }
 
-void launch_jacobi_sweep(const Prm& P, const Fld& F, cudaStream_t s) {
-  MDBS_LAUNCH(K_JACOBI, grid_for(faces_total_host(P)), kBlock, s, k_jacobi, P, F);
+void launch_jacobi_sweeps(const Prm& P, const Fld& F, int sweeps, cudaStream_t s) {
+  Faces3 a{{F.u[0], F.u[1], F.u[2]}}, b{{F.utmp[0], F.utmp[1], F.utmp[2]}};
+  const int g = grid_for(faces_total_host(P));
+  for (int it = 0; it < sweeps; it++) {
+    MDBS_LAUNCH(K_JACOBI, g, kBlock, s, k_jacobi, P, F, a, b);
+    Faces3 t = a;
+    a = b;
+    b = t;
+  }
+  // an odd sweep count leaves the result in the scratch buffers
+  if (sweeps & 1) MDBS_LAUNCH(K_JACOBI, g, kBlock, s, k_copy_faces, P, a, b);
 }
 
 void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s) {
@@ -679,10 +714,19 @@ void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* sc
   MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_stats, partials, nb, scal);
 }
 
-void launch_cfl(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
-  const int nb = grid_for(faces_total_host(P), 512);
-  MDBS_LAUNCH(K_CFL, nb, kBlock, s, k_cfl, P, F, partials);
-  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_max, partials, nb, scal, 4);
+void launch_time_advance(const Prm& P, const Fld& F, double cfl, double dt_max, double* partials, double* scal,
+                         cudaStream_t s) {
+  if (cfl > 0.0) {
+    const int nb = grid_for(faces_total_host(P), 512);
+    MDBS_LAUNCH(K_CFL, nb, kBlock, s, k_cfl, P, F, partials);
+    MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_cfl, partials, nb, scal, cfl, P.h, dt_max);
+  } else {
+    MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_advance_time, scal);
+  }
+}
+
+void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s) {
+  MDBS_LAUNCH(K_STATIC, grid_for(P.cells), kBlock, s, k_static_geometry, P, phi, is_free, nw[0], nw[1], nw[2]);
 }
 
 }  // namespace mdbs
