@@ -22,7 +22,7 @@ const char* const kKernelNames[K_COUNT] = {
     "curvature", "momentum_assemble", "jacobi", "hbya", "correct", "boundary", "field_stats", "cfl",
     "static_geometry", "pressure_assemble", "diag", "convert", "coarsen", "smooth_fine", "smooth_coarse",
     "zero", "restrict_fine", "restrict_coarse", "prolong_fine", "prolong_coarse", "cg_resid0",
-    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d"};
+    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d", "tail_vcycle"};
 
 // Per-simulation launch counter and optional event timer.
 struct Profiler {

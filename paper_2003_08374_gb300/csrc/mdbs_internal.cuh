@@ -111,7 +111,7 @@ enum KernelId {
   K_ALPHA_FLUX, K_ALPHA_LO, K_ALPHA_LIMIT, K_ALPHA_UPDATE, K_FINALIZE, K_PROPERTIES, K_NORMALS,
   K_CURVATURE, K_MOM_ASSEMBLE, K_JACOBI, K_HBYA, K_CORRECT, K_BOUNDARY, K_STATS, K_CFL, K_STATIC,
   K_ASSEMBLE, K_DIAG, K_CONVERT, K_COARSEN, K_SMOOTH0, K_SMOOTHC, K_ZERO, K_RESTRICT0, K_RESTRICTC,
-  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_COUNT
+  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_TAIL, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 void prof_begin(int id, cudaStream_t s);

@@ -216,6 +216,111 @@ __global__ void k_prolong(Level<R> Fi, Level<R> Co) {
   Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
 }
 
+// ------------------------------------------------------------------ tail V-cycle
+// The small levels (and the coarsest solve) of a V-cycle in one CTA: the same
+// per-cell arithmetic, in the same order, as the per-level kernels above, with
+// __syncthreads() between phases instead of kernel boundaries.
+constexpr int kTailCells = 4096;
+constexpr int kTailThreads = 1024;
+
+template <typename R>
+struct Tail {
+  Level<R> lv[kMaxLevels];
+  int first, nlev, nu1, nu2, cs;
+};
+
+template <typename R>
+__device__ void tail_smooth(const Level<R>& L, int col, int zero) {
+  const unsigned half = (L.n[0] + 1) >> 1;
+  const unsigned total = half * (unsigned)L.n[1] * (unsigned)L.n[2];
+  for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
+    const unsigned ti = t % half, row = t / half;
+    const int j = (int)(row % (unsigned)L.n[1]), k = (int)(row / (unsigned)L.n[1]);
+    const int i = ((j + k + col) & 1) + 2 * (int)ti;
+    if (i >= L.n[0]) continue;
+    const long long c = i + (long long)L.n[0] * row;
+    if (zero) {
+      L.x[c] = L.b[c] / L.diag[c];
+    } else {
+      const int q[3] = {i, j, k};
+      R v = L.b[c] + neighbour_sum(L, L.x, q, c);
+      L.x[c] = v / L.diag[c];
+    }
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__device__ void tail_pair(const Level<R>& L, int first_col, bool zero_first) {
+  tail_smooth(L, first_col, zero_first ? 1 : 0);
+  tail_smooth(L, 1 - first_col, 0);
+}
+
+template <typename R>
+__device__ void tail_zero(const Level<R>& L) {
+  for (unsigned c = threadIdx.x; c < (unsigned)L.cells; c += blockDim.x) L.x[c] = R(0);
+  __syncthreads();
+}
+
+template <typename R>
+__device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co) {
+  for (unsigned ci = threadIdx.x; ci < (unsigned)Co.cells; ci += blockDim.x) {
+    int Q[3];
+    Q[0] = (int)(ci % (unsigned)Co.n[0]);
+    const unsigned r = ci / (unsigned)Co.n[0];
+    Q[1] = (int)(r % (unsigned)Co.n[1]);
+    Q[2] = (int)(r / (unsigned)Co.n[1]);
+    int lo[3], hi[3];
+    for (int a = 0; a < 3; a++) {
+      lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
+      hi[a] = Co.cz[a] ? (2 * Q[a] + 1 < Fi.n[a] ? 2 * Q[a] + 1 : 2 * Q[a]) : Q[a];
+    }
+    R s = R(0);
+    for (int z = lo[2]; z <= hi[2]; z++)
+      for (int y = lo[1]; y <= hi[1]; y++)
+        for (int x = lo[0]; x <= hi[0]; x++) {
+          const int q[3] = {x, y, z};
+          const long long c = cell_index(Fi.n, x, y, z);
+          const R ax = Fi.diag[c] * Fi.x[c] - neighbour_sum(Fi, Fi.x, q, c);
+          s += Fi.b[c] - ax;
+        }
+    Co.b[ci] = s;
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co) {
+  for (unsigned c = threadIdx.x; c < (unsigned)Fi.cells; c += blockDim.x) {
+    int q[3];
+    q[0] = (int)(c % (unsigned)Fi.n[0]);
+    const unsigned r = c / (unsigned)Fi.n[0];
+    q[1] = (int)(r % (unsigned)Fi.n[1]);
+    q[2] = (int)(r / (unsigned)Fi.n[1]);
+    int Q[3];
+    for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
+    Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
+  }
+  __syncthreads();
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(Tail<R> t) {
+  for (int l = t.first; l < t.nlev - 1; l++) {
+    if (t.nu1 == 0) tail_zero(t.lv[l]);
+    for (int it = 0; it < t.nu1; it++) tail_pair(t.lv[l], 0, it == 0);
+    tail_restrict(t.lv[l], t.lv[l + 1]);
+  }
+  const Level<R>& C = t.lv[t.nlev - 1];
+  if (t.cs == 0) tail_zero(C);
+  for (int it = 0; it < t.cs; it++) tail_pair(C, 0, it == 0);
+  for (int it = 0; it < t.cs; it++) tail_pair(C, 1, false);
+  for (int l = t.nlev - 2; l >= t.first; l--) {
+    tail_prolong(t.lv[l], t.lv[l + 1]);
+    for (int it = 0; it < t.nu2; it++) tail_pair(t.lv[l], 1, false);
+  }
+}
+
 // ------------------------------------------------------------------ CG kernels (FP64)
 __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const double* __restrict__ x, long long c,
                                            const int q[3]) {
@@ -559,19 +664,26 @@ static void smooth_pair(const Level<R>& L, int first_col, bool zero_first, bool 
   MDBS_LAUNCH(id, grid_for(threads), kBlock, s, k_smooth<R>, L, 1 - first_col, 0);
 }
 
-// symmetric V-cycle, x of level 0 receives M b of level 0
+// symmetric V-cycle, x of level 0 receives M b of level 0; the levels from the
+// first one with at most kTailCells cells run in the single-CTA tail kernel
 template <typename R>
 static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, cudaStream_t s) {
-  for (int l = 0; l < nlev - 1; l++) {
+  int first = nlev - 1;
+  while (first > 0 && lv[first - 1].cells <= kTailCells) first--;
+  for (int l = 0; l < first; l++) {
     if (nu1 == 0) MDBS_LAUNCH(K_ZERO, grid_for(lv[l].cells), kBlock, s, k_zero<R>, lv[l].x, lv[l].cells);
     for (int it = 0; it < nu1; it++) smooth_pair(lv[l], 0, it == 0, l == 0, s);
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_for(lv[l + 1].cells), kBlock, s, k_resid_restrict<R>, lv[l], lv[l + 1]);
   }
-  Level<R>& C = lv[nlev - 1];
-  if (cs == 0) MDBS_LAUNCH(K_ZERO, grid_for(C.cells), kBlock, s, k_zero<R>, C.x, C.cells);
-  for (int it = 0; it < cs; it++) smooth_pair(C, 0, it == 0, nlev == 1, s);
-  for (int it = 0; it < cs; it++) smooth_pair(C, 1, false, nlev == 1, s);
-  for (int l = nlev - 2; l >= 0; l--) {
+  Tail<R> t;
+  for (int l = 0; l < nlev; l++) t.lv[l] = lv[l];
+  t.first = first;
+  t.nlev = nlev;
+  t.nu1 = nu1;
+  t.nu2 = nu2;
+  t.cs = cs;
+  MDBS_LAUNCH(K_TAIL, 1, kTailThreads, s, k_tail_vcycle<R>, t);
+  for (int l = first - 1; l >= 0; l--) {
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_for(lv[l].cells), kBlock, s, k_prolong<R>, lv[l], lv[l + 1]);
     for (int it = 0; it < nu2; it++) smooth_pair(lv[l], 1, false, l == 0, s);
   }
