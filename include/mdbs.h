@@ -198,6 +198,41 @@ int mdbs_profile_read(const mdbs_sim* sim, int32_t id, const char** name, double
  */
 int64_t mdbs_debug_array(const mdbs_sim* sim, const char* name, double* out, int64_t capacity);
 
+/* ---------------- allocation-free helper ---------------- */
+
+/* Capacity of the file-scope scratch array used by mdbs_field_stats_static:
+ * per-block partial results, 4 doubles per block (16 KiB in all), held by every
+ * device that loads the library until the process exits. */
+#define MDBS_STATIC_STATS_MAX_BLOCKS 512
+/* Largest cell count mdbs_field_stats_static accepts. */
+#define MDBS_STATIC_STATS_MAX_CELLS ((int64_t)2147483647)
+
+/*
+ * Field statistics without any device allocation.  The paper has no counterpart:
+ * this is a library service.  It computes, on the GPU, the same quantities that
+ * mdbs_set_fields / mdbs_step leave in mdbs_stats (liquid volume
+ * sum porosity*alpha*cell_volume, alpha min, alpha max) plus the count of
+ * non-finite alpha or p values, for fields that the caller already holds on the
+ * device.  It exists for callers that must not allocate: code that runs while a
+ * CUDA graph is being captured (cudaMalloc is not allowed there), serving loops
+ * that cannot afford the device-wide synchronisation an allocation may cause,
+ * and embedders that do not let a library own device memory at all.
+ *   cells        : number of cells, 1 .. MDBS_STATIC_STATS_MAX_CELLS, else MDBS_ERR_ARG
+ *   cell_volume  : h^3 [m^3], > 0
+ *   porosity, alpha, p : device arrays of `cells` float64 values (x-fastest)
+ *   out          : device array of 4 float64: volume, alpha min, alpha max, non-finite count
+ *   stream       : cudaStream_t the two kernels are queued on (NULL: legacy default stream)
+ * Allocates nothing: its scratch is a file-scope __device__ array of
+ * MDBS_STATIC_STATS_MAX_BLOCKS * 4 doubles shared by every call.  The first call on a
+ * device looks up that array's device address with the device current; make that first
+ * call before any stream capture.  Calls whose kernels overlap on the GPU race on the
+ * shared scratch: serialise them (one stream, or events).  Each call overwrites every
+ * scratch value it reads, so nothing needs clearing between calls.  Returns MDBS_OK,
+ * MDBS_ERR_ARG or MDBS_ERR_CUDA; the result is ready when the stream reaches it.
+ */
+int mdbs_field_stats_static(int64_t cells, double cell_volume, const double* porosity, const double* alpha,
+                            const double* p, double* out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

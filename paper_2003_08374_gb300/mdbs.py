@@ -80,6 +80,8 @@ def lib():
         L.mdbs_profile_count.restype = C.c_int32
         L.mdbs_profile_read.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), _D,
                                         C.POINTER(C.c_int64)]
+        L.mdbs_field_stats_static.argtypes = [C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
+                                              C.c_void_p, C.c_void_p]
         L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
         L.mdbs_debug_array.restype = C.c_int64
         _lib = L
@@ -103,6 +105,16 @@ def structs_from_case(case):
                  case.max_cg, case.mg_nu1, case.mg_nu2, case.mg_coarse_sweeps, case.precision,
                  (C.c_int32 * 6)(*case.bc), case.inlet_u, case.inlet_alpha)
     return grid, fl, cl, op
+
+
+def field_stats_static(cells, cell_volume, porosity_ptr, alpha_ptr, p_ptr, out_ptr, stream=0):
+    """mdbs_field_stats_static on caller-owned device buffers (integer device addresses);
+    allocates nothing.  out receives volume, alpha min, alpha max, non-finite count."""
+    rc = lib().mdbs_field_stats_static(int(cells), float(cell_volume), C.c_void_p(porosity_ptr),
+                                       C.c_void_p(alpha_ptr), C.c_void_p(p_ptr), C.c_void_p(out_ptr),
+                                       C.c_void_p(stream))
+    if rc != OK:
+        raise MdbsError(rc, "mdbs_field_stats_static rejected the call")
 
 
 def bytes_required(case, precision=None):
