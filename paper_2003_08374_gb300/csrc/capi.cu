@@ -325,6 +325,9 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   if (!grid || !porosity || !permeability || !fl || !cl || !op) return fail(s, MDBS_ERR_ARG, "NULL argument");
   if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1 || !(grid->h > 0.0))
     return fail(s, MDBS_ERR_ARG, "grid sizes must be >= 1 and h > 0");
+  // kernels decode indices in 32 bits: every face array must stay below 2^31 entries
+  if ((long long)(grid->nx + 1) * (grid->ny + 1) * (long long)(grid->nz + 1) >= (1ll << 31))
+    return fail(s, MDBS_ERR_ARG, "grid too large (more than 2^31 faces per direction)");
   const long long cells = (long long)grid->nx * grid->ny * grid->nz;
   for (long long c = 0; c < cells; c++) {
     const double ph = porosity[c];
@@ -382,6 +385,9 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.cos_t = cos(th);
   P.sin_t = sin(th);
   P.c_alpha = op->c_alpha;
+  P.inv_h = 1.0 / grid->h;
+  P.half_inv_h = 0.5 / grid->h;
+  P.kr_m_int = (cl->kr_m >= 1.0 && cl->kr_m <= 8.0 && cl->kr_m == floor(cl->kr_m)) ? (int)cl->kr_m : 0;
   s->opt = *op;
   s->precision = op->precision;
   s->stream = nullptr;

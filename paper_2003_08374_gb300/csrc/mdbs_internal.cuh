@@ -30,6 +30,8 @@ struct Prm {
   double kr_m, a_l_irr, a_g_irr, pc0, pc_beta, pc_m, a_pc_irr, a_pc_max, pc_eps;
   double cos_t, sin_t;  // contact angle
   double c_alpha;
+  double inv_h, half_inv_h;  // 1/h and 1/(2h)
+  int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
 };
 
 // Device arrays of one simulation.

@@ -22,10 +22,11 @@ int grid_for(long long n, int cap = 1 << 30) {
 }
 
 __device__ __forceinline__ void decode3(const int n[3], long long c, int& i, int& j, int& k) {
-  i = (int)(c % n[0]);
-  long long r = c / n[0];
-  j = (int)(r % n[1]);
-  k = (int)(r / n[1]);
+  const unsigned uc = (unsigned)c;  // arrays stay below 2^31 entries
+  i = (int)(uc % (unsigned)n[0]);
+  const unsigned r = uc / (unsigned)n[0];
+  j = (int)(r % (unsigned)n[1]);
+  k = (int)(r / (unsigned)n[1]);
 }
 
 // ------------------------------------------------------------------ assembly
@@ -156,13 +157,13 @@ __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restric
 // red-black Gauss-Seidel half sweep of colour col; zero: x is taken as 0
 template <typename R>
 __global__ void k_smooth(Level<R> L, int col, int zero) {
-  const int half = (L.n[0] + 1) >> 1;
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  long long rows = (long long)L.n[1] * L.n[2];
+  const unsigned half = (L.n[0] + 1) >> 1;
+  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
+  const unsigned rows = (unsigned)L.n[1] * (unsigned)L.n[2];
   if (t >= rows * half) return;
   const int ti = (int)(t % half);
-  const long long row = t / half;
-  const int j = (int)(row % L.n[1]), k = (int)(row / L.n[1]);
+  const unsigned row = t / half;
+  const int j = (int)(row % (unsigned)L.n[1]), k = (int)(row / (unsigned)L.n[1]);
   const int i = ((j + k + col) & 1) + 2 * ti;
   if (i >= L.n[0]) return;
   const long long c = i + (long long)L.n[0] * row;

@@ -26,9 +26,11 @@ __device__ __forceinline__ bool decode_face(const Prm& P, long long t, int& d, i
   } else {
     return false;
   }
-  long long fx = P.n[0] + (d == 0), fy = P.n[1] + (d == 1);
-  i = (int)(f % fx);
-  long long r = f / fx;
+  // 32-bit decode: mdbs_create limits every array to fewer than 2^31 entries
+  const unsigned fx = P.n[0] + (d == 0), fy = P.n[1] + (d == 1);
+  const unsigned uf = (unsigned)f;
+  i = (int)(uf % fx);
+  const unsigned r = uf / fx;
   j = (int)(r % fy);
   k = (int)(r / fy);
   return true;
@@ -39,18 +41,18 @@ __device__ __forceinline__ long long total_faces(const Prm& P) {
 }
 
 __device__ __forceinline__ void decode_cell(const Prm& P, long long c, int& i, int& j, int& k) {
-  i = (int)(c % P.n[0]);
-  long long r = c / P.n[0];
-  j = (int)(r % P.n[1]);
-  k = (int)(r / P.n[1]);
+  const unsigned uc = (unsigned)c;
+  i = (int)(uc % (unsigned)P.n[0]);
+  const unsigned r = uc / (unsigned)P.n[0];
+  j = (int)(r % (unsigned)P.n[1]);
+  k = (int)(r / (unsigned)P.n[1]);
 }
 
 // central difference of a cell field along e at (i,j,k), zero-gradient ghosts
 __device__ __forceinline__ double cgrad(const double* __restrict__ a, const Prm& P, int e, int i, int j,
                                         int k) {
   int di = (e == 0), dj = (e == 1), dk = (e == 2);
-  return (ghost_read(a, P.n, i + di, j + dj, k + dk) - ghost_read(a, P.n, i - di, j - dj, k - dk)) /
-         (2.0 * P.h);
+  return (ghost_read(a, P.n, i + di, j + dj, k + dk) - ghost_read(a, P.n, i - di, j - dj, k - dk)) * P.half_inv_h;
 }
 
 // 0 = interior face, 1 = fixed (wall / inlet) face, 2 = outlet face
@@ -268,8 +270,18 @@ __global__ void k_properties(Prm P, Fld F) {
   ae = fmin(fmax(ae, 0.0), 1.0);
   double krl, krg;
   if (P.kr_model == 0) {
-    krl = pow(ae, P.kr_m);
-    krg = pow(1.0 - ae, P.kr_m);
+    if (P.kr_m_int > 0) {  // integer exponent: repeated products instead of FP64 pow
+      krl = ae;
+      krg = 1.0 - ae;
+      const double bl = krl, bg = krg;
+      for (int q = 1; q < P.kr_m_int; q++) {
+        krl *= bl;
+        krg *= bg;
+      }
+    } else {
+      krl = pow(ae, P.kr_m);
+      krg = pow(1.0 - ae, P.kr_m);
+    }
   } else {
     const double s1m = pow(ae, 1.0 / P.kr_m);
     krg = sqrt(1.0 - ae) * pow(1.0 - s1m, 2.0 * P.kr_m);
@@ -280,14 +292,18 @@ __global__ void k_properties(Prm P, Fld F) {
   const double Ml = k0 * krl / P.mu_l, Mg = k0 * krg / P.mu_g, M = Ml + Mg;
   double s = (a - P.a_pc_irr) / (P.a_pc_max - P.a_pc_irr);
   s = fmin(fmax(s, P.pc_eps), 1.0 - P.pc_eps);
-  const double pc = P.pc_model == 0 ? P.pc0 * pow(s, -P.pc_beta)
-                                    : P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
+  double pc;
+  if (P.pc_model == 0)
+    pc = P.pc_beta == 0.5 ? P.pc0 / sqrt(s) : P.pc0 * pow(s, -P.pc_beta);
+  else
+    pc = P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
   F.Ml[c] = Ml;
   F.Mg[c] = Mg;
-  F.drag[c] = 1.0 / M;
-  F.rho[c] = (P.rho_l * Ml + P.rho_g * Mg) / M;
+  const double inv_M = 1.0 / M;
+  F.drag[c] = inv_M;
+  F.rho[c] = (P.rho_l * Ml + P.rho_g * Mg) * inv_M;
   F.pc[c] = pc;
-  F.cf[c] = (Ml * (1.0 - a) - Mg * a) / M;
+  F.cf[c] = (Ml * (1.0 - a) - Mg * a) * inv_M;
 }
 
 // interface normal toward the liquid (Eq. 24 with the orientation of Eq. 41)
@@ -363,19 +379,21 @@ __global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp
     const long long l = cell_index(P.n, li, lj, lk), r = cell_index(P.n, i, j, k);
     const bool fl = F.is_free[l], fr = F.is_free[r];
     if (fl && fr) {
-      Bf += P.sigma * 0.5 * (F.kappa[l] + F.kappa[r]) * (F.alpha[r] - F.alpha[l]) / h;
+      Bf += P.sigma * 0.5 * (F.kappa[l] + F.kappa[r]) * (F.alpha[r] - F.alpha[l]) * P.inv_h;
     } else if (!fl && !fr) {
       Bf += (0.5 * (F.cf[l] + F.cf[r]) * (F.pc[r] - F.pc[l]) -
-             0.5 * (F.pc[l] + F.pc[r]) * (F.alpha[r] - F.alpha[l])) /
-            h;
+             0.5 * (F.pc[l] + F.pc[r]) * (F.alpha[r] - F.alpha[l])) *
+            P.inv_h;
     }
   }
   F.B[d][f] = Bf;
   const double uf = F.u[d][f];
-  const double dt = *dtp;
-  const double at = V * rhof / (phif * dt);
-  const double S = V * rhoo * uf / (phif * dt);
-  const double cconv = V * rhof / (phif * phif * h);
+  const double inv_phidt = 1.0 / (phif * *dtp);
+  const double inv_phi = 1.0 / phif;
+  const double inv_h = P.inv_h;
+  const double at = V * rhof * inv_phidt;
+  const double S = V * rhoo * uf * inv_phidt;
+  const double cconv = V * rhof * inv_phi * inv_phi * inv_h;
   double ap = at + V * Df;
   double tt = 0.0;
   for (int e = 0; e < P.dim; e++) {
@@ -409,7 +427,7 @@ __global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp
         mus = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
                       ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
       }
-      const double a = cup + mus * A / h;
+      const double a = cup + mus * h;  // mu A / h with A = h^2
       if (status == 0) {
         F.anb[d][slot * nf + f] = a;
         ap += a;
@@ -419,18 +437,18 @@ __global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp
     }
     // explicit div(mu grad(u)^T), component d
     if (e == d) {
-      const double dR = (cd + 1 <= P.n[d]) ? (F.u[d][face_index(P.n, d, i + di, j + dj, k + dk)] - uf) / h : 0.0;
-      const double dL = (cd - 1 >= 0) ? (uf - F.u[d][face_index(P.n, d, li, lj, lk)]) / h : 0.0;
-      tt += (muR * dR - muL * dL) / h;
+      const double dR = (cd + 1 <= P.n[d]) ? (F.u[d][face_index(P.n, d, i + di, j + dj, k + dk)] - uf) * inv_h : 0.0;
+      const double dL = (cd - 1 >= 0) ? (uf - F.u[d][face_index(P.n, d, li, lj, lk)]) * inv_h : 0.0;
+      tt += (muR * dR - muL * dL) * inv_h;
     } else {
       double ts = 0.0;
       for (int sg = -1; sg <= 1; sg += 2) {
         const double muE = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
                                    ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
-        const double der = sg > 0 ? (vRhi - vLhi) / h : (vRlo - vLlo) / h;
+        const double der = sg > 0 ? (vRhi - vLhi) * inv_h : (vRlo - vLlo) * inv_h;
         ts += sg > 0 ? muE * der : -muE * der;
       }
-      tt += ts / h;
+      tt += ts * inv_h;
     }
   }
   F.aP[d][f] = ap;
@@ -479,7 +497,7 @@ __global__ void k_jacobi(Prm P, Fld F, Faces3 in, Faces3 out) {
   }
   const double* u[3] = {in.a[0], in.a[1], in.a[2]};
   const double hs = face_H(P, F, u, d, i, j, k, f);
-  out.a[d][f] = (hs - P.V * face_dp(P, F.p, d, i, j, k) / P.h) / F.aP[d][f];
+  out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) / F.aP[d][f];  // V/h = A
 }
 
 __global__ void k_copy_faces(Prm P, Faces3 src, Faces3 dst) {
