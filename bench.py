@@ -197,6 +197,45 @@ def measured_traffic(kernel, precision_tag, cells):
     return per_cell * cells
 
 
+FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM clock (GB300: 1.26)
+
+
+def roofline(prof, cells, word, fp64):
+    """Roofline of the finest-level red-black half sweep.  Per V-cycle the finest level runs
+    8 half sweeps (nu1 = nu2 = 2): 1 from a zero guess (b, 1/diag, x written on half the cells:
+    3 words per updated cell) and 7 full ones (b, 1/diag, x written and the other colour's x read
+    on half the cells, the three face-coefficient arrays in full: 5 words per cell).  Flops per
+    updated cell: 6 fused multiply-adds and one multiply (13), 1 for the zero-guess sweep."""
+    if DOMINANT not in prof:
+        return None
+    tot_ms, cnt = prof[DOMINANT]
+    avg_s = tot_ms / cnt / 1e3
+    alg_bytes = (7 * 5 * word + 1 * 1.5 * word) / 8 * cells
+    flops = (7 * 13 + 1 * 1) / 8 * cells / 2
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    gbs = alg_bytes / avg_s / 1e9
+    tfl = flops / avg_s / 1e12
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak,
+           "traffic": measured_traffic(DOMINANT, "fp64_grf128" if fp64 else "fp32_grf128", cells),
+           "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6800 GB/s"}
+    out = dict(hbm)
+    if fp64:
+        alu = {"bound": "alu", "achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+               "frac": tfl / FP64_PEAK_TFLOPS, "traffic": hbm["traffic"],
+               "peak_source": "FP64 pipe: 152 SMs x 4 flop/clk x 2.07 GHz (nominal 1.25 TFLOP/s)"}
+        if alu["frac"] > hbm["frac"]:
+            out = dict(alu)
+            out["hbm"] = {"achieved": gbs, "peak": hbm_peak, "unit": "GB/s", "frac": gbs / hbm_peak}
+        else:
+            out["alu"] = {"achieved": tfl, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                          "frac": tfl / FP64_PEAK_TFLOPS}
+    out.update({"kernel": DOMINANT + ("_fp64" if fp64 else "_fp32"), "launches": cnt, "avg_us": avg_s * 1e6,
+                "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+                "timing": "CUDA events around every kernel launch in an eager pass of the same K steps"})
+    return out
+
+
 def gpu_arm(args):
     import torch
     rank, world, local = dist_info()
@@ -259,23 +298,7 @@ def gpu_arm(args):
     _, prof, _, _, _ = timed(sim, args.steps, args.warmup, "*")
     breakdown = {k: round(v[0] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
-    # roofline of the dominant kernel: finest-level RBGS half sweep, FP64.
-    # algorithmic bytes per launch: b, diag, own x written and neighbour x read on half the
-    # cells (4 x 8 B / 2) plus the three face-coefficient arrays read in full (3 x 8 B).
-    alg_bytes = (4 * 8 / 2 + 3 * 8) * case.cells
-    pk = peaks()
-    roof = None
-    if DOMINANT in prof:
-        tot_ms, cnt = prof[DOMINANT]
-        avg_s = tot_ms / cnt / 1e3
-        achieved = alg_bytes / avg_s / 1e9
-        peak = pk["hbm_gbs"] if pk else 6800.0
-        traffic = measured_traffic(DOMINANT, "fp64_grf128", case.cells)
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": DOMINANT, "launches": cnt, "avg_us": avg_s * 1e6,
-                "alg_bytes_per_launch": alg_bytes,
-                "timing": "CUDA events around every kernel launch in an eager pass of the same K steps",
-                "peak_source": "measured (MEASURED_PEAKS.json hbm_gbs)" if pk else "fallback 6800 GB/s"}
+    roof = roofline(prof, case.cells, 8, fp64=True)
 
     mixed = None
     if not args.no_mixed:
@@ -285,8 +308,10 @@ def gpu_arm(args):
         mms, _, _, _, mst = timed(msim, args.steps, args.warmup)
         mms = max_over_ranks(mms)
         mval = case.cells * args.steps * world / (mms / 1e3)
+        msim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
+        _, mprof, _, _, _ = timed(msim, args.steps, args.warmup, DOMINANT)
         mixed = {"value": mval, "ms_per_step": mms / args.steps, "speedup_vs_fp64": mval / value,
-                 "cg_iters_last_step": mst["cg_iters"]}
+                 "cg_iters_last_step": mst["cg_iters"], "roofline": roofline(mprof, case.cells, 4, fp64=False)}
         msim.close()
 
     # end to end through the public API with host buffers: each step copies the state in

@@ -174,7 +174,7 @@ def apply_A(n, Tx, Ty, Tz, Dd, x):
     return y
 
 
-def vcycle(n, Tx, Ty, Tz, Dd, r, nu1=2, nu2=2, coarse=8):
+def vcycle(n, Tx, Ty, Tz, Dd, r, nu1=2, nu2=2, coarse=0):
     Tx, Ty, Tz, Dd = _coef((Tx, Ty, Tz, Dd))
     r = _f64(r.ravel())
     z = np.zeros_like(r)
@@ -182,7 +182,7 @@ def vcycle(n, Tx, Ty, Tz, Dd, r, nu1=2, nu2=2, coarse=8):
     return z
 
 
-def pcg(n, Tx, Ty, Tz, Dd, b, x0=None, tol=1e-12, max_it=500, nu1=2, nu2=2, coarse=8):
+def pcg(n, Tx, Ty, Tz, Dd, b, x0=None, tol=1e-12, max_it=500, nu1=2, nu2=2, coarse=0):
     Tx, Ty, Tz, Dd = _coef((Tx, Ty, Tz, Dd))
     b = _f64(b.ravel())
     x = np.zeros_like(b) if x0 is None else _f64(x0.ravel()).copy()

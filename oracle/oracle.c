@@ -778,13 +778,62 @@ static void smooth_color(level_t* L, int col) {
   }
 }
 
+/* Exact solve of the coarsest level (at most 4 x 4 x 4 cells): dense matrix of
+ * the operator, Cholesky factorisation, forward and back substitution. */
+static void coarsest_direct(level_t* L) {
+  long n = L->cells;
+  double* M = calloc(n * n, sizeof(double));
+  for (long c = 0; c < n; c++) {
+    int q[3];
+    coords_of(L->n, c, q);
+    M[c * n + c] = L->diag[c];
+    for (int d = 0; d < 3; d++) {
+      if (q[d] + 1 < L->n[d]) {
+        int p[3];
+        cpy3(p, q);
+        p[d] += 1;
+        long o = cid3(L->n, p);
+        M[c * n + o] -= lev_T(L, d)[c];
+        M[o * n + c] -= lev_T(L, d)[c];
+      }
+    }
+  }
+  /* Cholesky M = G G^T, G lower, stored in M */
+  for (long j = 0; j < n; j++) {
+    double dj = M[j * n + j];
+    for (long k = 0; k < j; k++) dj -= M[j * n + k] * M[j * n + k];
+    dj = sqrt(dj);
+    M[j * n + j] = dj;
+    for (long i = j + 1; i < n; i++) {
+      double v = M[i * n + j];
+      for (long k = 0; k < j; k++) v -= M[i * n + k] * M[j * n + k];
+      M[i * n + j] = v / dj;
+    }
+  }
+  for (long i = 0; i < n; i++) { /* G y = b */
+    double v = L->b[i];
+    for (long k = 0; k < i; k++) v -= M[i * n + k] * L->x[k];
+    L->x[i] = v / M[i * n + i];
+  }
+  for (long i = n - 1; i >= 0; i--) { /* G^T x = y */
+    double v = L->x[i];
+    for (long k = i + 1; k < n; k++) v -= M[k * n + i] * L->x[k];
+    L->x[i] = v / M[i * n + i];
+  }
+  free(M);
+}
+
 /* symmetric V-cycle from a zero initial guess: (red, black) x nu1 before the
- * coarse correction, (black, red) x nu2 after it; the coarsest level runs
- * coarse_sweeps forward then coarse_sweeps backward pairs. */
+ * coarse correction, (black, red) x nu2 after it; the coarsest level is solved
+ * exactly (cs == 0) or by cs forward then cs backward sweep pairs. */
 static void vcycle_rec(level_t* lev, int l, int nlev, int nu1, int nu2, int cs) {
   level_t* L = &lev[l];
   memset(L->x, 0, L->cells * sizeof(double));
   if (l == nlev - 1) {
+    if (cs == 0) {
+      coarsest_direct(L);
+      return;
+    }
     for (int i = 0; i < cs; i++) {
       smooth_color(L, 0);
       smooth_color(L, 1);

@@ -40,7 +40,7 @@ typedef struct {
   /* time stepping and solver */
   double dt, cfl, dt_max, c_alpha, p_tol;
   int n_corr, mom_sweeps, max_cg;
-  int mg_nu1, mg_nu2, mg_coarse_sweeps;
+  int mg_nu1, mg_nu2, mg_coarse_sweeps; /* 0: exact solve of the coarsest level */
   int bc[6];
   double inlet_u, inlet_alpha;
 } orc_params;

@@ -183,6 +183,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   for (int e = 0; e < 3; e++) F.T[e] = cd();
   F.Dd = cd();
   F.diag = cd();
+  F.dinv = cd();
   F.b = cd();
   for (int d = 0; d < 3; d++) {
     const long long nf = (d < L.dim) ? L.nf[d] : 1;
@@ -583,6 +584,9 @@ int64_t mdbs_debug_array(const mdbs_sim* cs, const char* name, double* out, int6
         cudaError_t er = cudaMemcpyAsync(out, e.a, m * 8, cudaMemcpyDeviceToHost, s->stream);
         if (er == cudaSuccess) er = cudaStreamSynchronize(s->stream);
         if (er != cudaSuccess) return cuda_fail(s, er, "debug copy");
+        // the a_P arrays hold reciprocals on the device (fixed faces hold 1)
+        if (name[0] == 'a' && name[1] == 'P')
+          for (long long i = 0; i < m; i++) out[i] = 1.0 / out[i];
       }
     }
     return n;

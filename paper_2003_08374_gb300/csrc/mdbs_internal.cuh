@@ -50,9 +50,9 @@ struct Fld {
   // saturation step
   double *FLO[3], *AF[3], *aL, *Rp, *Rm;
   // momentum
-  double *aP[3], *anb[3], *rhs0[3], *B[3], *hbya[3], *utmp[3];
+  double *aP[3], *anb[3], *rhs0[3], *B[3], *hbya[3], *utmp[3];  // aP holds 1 / a_P
   // pressure system (level 0)
-  double *T[3], *Dd, *diag, *b;
+  double *T[3], *Dd, *diag, *dinv, *b;
 };
 
 // One multigrid level (T is stored per cell for the face towards +axis).
@@ -64,6 +64,7 @@ struct Level {
   R* T[3];
   R* Dd;
   R* diag;
+  R* dinv;  // 1 / diag (multiplied in the smoothers instead of dividing)
   R* x;
   R* b;
 };

@@ -48,10 +48,10 @@ __global__ void k_assemble(Prm P, Fld F) {
     const int di = (d == 0), dj = (d == 1), dk = (d == 2);
     const long long flo = face_index(P.n, d, q[0], q[1], q[2]);
     const long long fhi = face_index(P.n, d, q[0] + di, q[1] + dj, q[2] + dk);
-    F.T[d][c] = (q[d] + 1 < P.n[d]) ? A2 / F.aP[d][fhi] : 0.0;
+    F.T[d][c] = (q[d] + 1 < P.n[d]) ? A2 * F.aP[d][fhi] : 0.0;  // aP holds 1 / a_P
     const bool lo_bnd = q[d] == 0, hi_bnd = q[d] + 1 == P.n[d];
-    if (lo_bnd && P.bc[2 * d] == kOutlet) Dd += 2.0 * A2 / F.aP[d][flo];
-    if (hi_bnd && P.bc[2 * d + 1] == kOutlet) Dd += 2.0 * A2 / F.aP[d][fhi];
+    if (lo_bnd && P.bc[2 * d] == kOutlet) Dd += 2.0 * A2 * F.aP[d][flo];
+    if (hi_bnd && P.bc[2 * d + 1] == kOutlet) Dd += 2.0 * A2 * F.aP[d][fhi];
     const bool lo_fixed = lo_bnd && P.bc[2 * d] != kOutlet;
     const bool hi_fixed = hi_bnd && P.bc[2 * d + 1] != kOutlet;
     const double ulo = lo_fixed ? F.u[d][flo] : F.hbya[d][flo];
@@ -80,12 +80,19 @@ __global__ void k_diag(Level<R> L) {
     dg += L.T[d][c];
     if (q[d] > 0) dg += coef_lo(L, d, q, c);
   }
-  L.diag[c] = dg + L.Dd[c];
+  const R dgt = dg + L.Dd[c];
+  L.diag[c] = dgt;
+  L.dinv[c] = R(1) / dgt;
 }
 
 __global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
   long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c < n) b[c] = (float)a[c];
+}
+
+__global__ void k_reciprocal_f(const float* __restrict__ a, float* __restrict__ b, long long n) {
+  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c < n) b[c] = 1.0f / a[c];
 }
 
 // coarse transmissibilities: fine rows across a coarse face in parallel, along a
@@ -168,12 +175,12 @@ __global__ void k_smooth(Level<R> L, int col, int zero) {
   if (i >= L.n[0]) return;
   const long long c = i + (long long)L.n[0] * row;
   if (zero) {
-    L.x[c] = L.b[c] / L.diag[c];
+    L.x[c] = L.b[c] * L.dinv[c];
     return;
   }
   const int q[3] = {i, j, k};
   R v = L.b[c] + neighbour_sum(L, L.x, q, c);
-  L.x[c] = v / L.diag[c];
+  L.x[c] = v * L.dinv[c];
 }
 
 template <typename R>
@@ -217,6 +224,57 @@ __global__ void k_prolong(Level<R> Fi, Level<R> Co) {
   Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
 }
 
+// ------------------------------------------------------------------ coarsest level
+// The coarsest level has at most 4 x 4 x 4 cells.  Once per assembly its dense
+// operator is inverted in one CTA (Gauss-Jordan in shared memory, no pivoting:
+// the matrix is symmetric positive definite) and symmetrised; the V-cycle then
+// solves it exactly with one dense product.
+constexpr int kCoarseMax = 64;
+
+template <typename R>
+__global__ void k_coarse_inverse(Level<R> C, R* __restrict__ inv) {
+  __shared__ R M[kCoarseMax * kCoarseMax];
+  const int n = (int)C.cells;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = R(0);
+  __syncthreads();
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+    int q[3];
+    q[0] = c % C.n[0];
+    q[1] = (c / C.n[0]) % C.n[1];
+    q[2] = c / (C.n[0] * C.n[1]);
+    M[c * n + c] = C.diag[c];
+    int o = 1;
+    for (int d = 0; d < 3; d++) {
+      if (q[d] + 1 < C.n[d]) {
+        M[c * n + c + o] = -C.T[d][c];
+        M[(c + o) * n + c] = -C.T[d][c];
+      }
+      o *= C.n[d];
+    }
+  }
+  __syncthreads();
+  for (int k = 0; k < n; k++) {
+    const R pinv = R(1) / M[k * n + k];
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x)
+      if (j != k) M[k * n + j] *= pinv;
+    __syncthreads();
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+      const int i = e / n, j = e % n;
+      if (i != k && j != k) M[e] -= M[i * n + k] * M[k * n + j];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+      if (i != k) M[i * n + k] = -M[i * n + k] * pinv;
+    if (threadIdx.x == 0) M[k * n + k] = pinv;
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e / n, j = e % n;
+    inv[e] = R(0.5) * (M[i * n + j] + M[j * n + i]);
+  }
+}
+
 // ------------------------------------------------------------------ tail V-cycle
 // The small levels (and the coarsest solve) of a V-cycle in one CTA: the same
 // per-cell arithmetic, in the same order, as the per-level kernels above, with
@@ -228,6 +286,7 @@ template <typename R>
 struct Tail {
   Level<R> lv[kMaxLevels];
   int first, nlev, nu1, nu2, cs;
+  const R* cinv;  // inverse of the coarsest operator (used when cs == 0)
 };
 
 template <typename R>
@@ -241,11 +300,11 @@ __device__ void tail_smooth(const Level<R>& L, int col, int zero) {
     if (i >= L.n[0]) continue;
     const long long c = i + (long long)L.n[0] * row;
     if (zero) {
-      L.x[c] = L.b[c] / L.diag[c];
+      L.x[c] = L.b[c] * L.dinv[c];
     } else {
       const int q[3] = {i, j, k};
       R v = L.b[c] + neighbour_sum(L, L.x, q, c);
-      L.x[c] = v / L.diag[c];
+      L.x[c] = v * L.dinv[c];
     }
   }
   __syncthreads();
@@ -313,7 +372,15 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(Tail<R> t) {
     tail_restrict(t.lv[l], t.lv[l + 1]);
   }
   const Level<R>& C = t.lv[t.nlev - 1];
-  if (t.cs == 0) tail_zero(C);
+  if (t.cs == 0) {
+    const int n = (int)C.cells;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      R v = R(0);
+      for (int j = 0; j < n; j++) v += t.cinv[i * n + j] * C.b[j];
+      C.x[i] = v;
+    }
+    __syncthreads();
+  }
   for (int it = 0; it < t.cs; it++) tail_pair(C, 0, it == 0);
   for (int it = 0; it < t.cs; it++) tail_pair(C, 1, false);
   for (int l = t.nlev - 2; l >= t.first; l--) {
@@ -503,6 +570,8 @@ struct PressureSolver {
   double* partials;
   double* scal;
   double* host_scal;  // pinned
+  double* cinv_d;     // inverse of the coarsest operator (FP64 hierarchy)
+  float* cinv_f;      // (FP32 hierarchy)
   void* block;        // single device allocation
   cudaStream_t body_stream;  // captures the body of the CG WHILE node
   long long body_launches;   // kernels per CG iteration (counted while capturing)
@@ -553,6 +622,8 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
   double* q = (double*)take(n0 * 8);
   double* partials = (double*)take(2 * kMaxPartials * 8);
   double* scal = (double*)take(16 * 8);
+  double* cinv_d = (double*)take(kCoarseMax * kCoarseMax * 8);
+  float* cinv_f = (float*)take(kCoarseMax * kCoarseMax * 4);
   if (ps) {
     ps->r = r;
     ps->z = z;
@@ -560,6 +631,8 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     ps->q = q;
     ps->partials = partials;
     ps->scal = scal;
+    ps->cinv_d = cinv_d;
+    ps->cinv_f = cinv_f;
   }
   for (int l = 0; l < nlev; l++) {
     const long long nc = (long long)dims[l][0] * dims[l][1] * dims[l][2];
@@ -574,6 +647,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
         for (int a = 0; a < 3; a++) L.T[a] = (double*)take(nc * 8);
         L.Dd = (double*)take(nc * 8);
         L.diag = (double*)take(nc * 8);
+        L.dinv = (double*)take(nc * 8);
         L.x = (double*)take(nc * 8);
         L.b = (double*)take(nc * 8);
       }
@@ -588,6 +662,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
       for (int a = 0; a < 3; a++) L.T[a] = (float*)take(nc * 4);
       L.Dd = (float*)take(nc * 4);
       L.diag = (float*)take(nc * 4);
+      L.dinv = (float*)take(nc * 4);
       L.x = (float*)take(nc * 4);
       L.b = (float*)take(nc * 4);
       if (ps) ps->lf[l] = L;
@@ -605,6 +680,15 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
     return nullptr;
   }
   ps->precision = precision == 0 ? 0 : 1;
+  {
+    int dims[kMaxLevels][3], cz[kMaxLevels][3];
+    const int nl = plan_levels(P.n, dims, cz);
+    if ((long long)dims[nl - 1][0] * dims[nl - 1][1] * dims[nl - 1][2] > kCoarseMax) {
+      *err = cudaErrorInvalidValue;  // coarsest level larger than the dense solver handles
+      delete ps;
+      return nullptr;
+    }
+  }
   size_t bytes = solver_layout(P.n, ps->precision, nullptr, nullptr);
   *err = cudaMalloc(&ps->block, bytes);
   if (*err != cudaSuccess) {
@@ -646,15 +730,17 @@ void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s) {
   L0.cells = P.cells;
   L0.Dd = F.Dd;
   L0.diag = F.diag;
+  L0.dinv = F.dinv;
   MDBS_LAUNCH(K_DIAG, grid_for(P.cells), kBlock, s, k_diag<double>, L0);
 }
 
 template <typename R>
-static void build_hierarchy(Level<R>* lv, int nlev, cudaStream_t s) {
+static void build_hierarchy(Level<R>* lv, int nlev, R* cinv, bool direct, cudaStream_t s) {
   for (int l = 1; l < nlev; l++) {
     MDBS_LAUNCH(K_COARSEN, grid_for(lv[l].cells), kBlock, s, k_coarsen<R>, lv[l - 1], lv[l]);
     MDBS_LAUNCH(K_DIAG, grid_for(lv[l].cells), kBlock, s, k_diag<R>, lv[l]);
   }
+  if (direct) MDBS_LAUNCH(K_COARSEN, 1, 256, s, k_coarse_inverse<R>, lv[nlev - 1], cinv);
 }
 
 template <typename R>
@@ -668,7 +754,7 @@ static void smooth_pair(const Level<R>& L, int first_col, bool zero_first, bool 
 // symmetric V-cycle, x of level 0 receives M b of level 0; the levels from the
 // first one with at most kTailCells cells run in the single-CTA tail kernel
 template <typename R>
-static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, cudaStream_t s) {
+static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, const R* cinv, cudaStream_t s) {
   int first = nlev - 1;
   while (first > 0 && lv[first - 1].cells <= kTailCells) first--;
   for (int l = 0; l < first; l++) {
@@ -683,6 +769,7 @@ static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, cudaStream_
   t.nu1 = nu1;
   t.nu2 = nu2;
   t.cs = cs;
+  t.cinv = cinv;
   MDBS_LAUNCH(K_TAIL, 1, kTailThreads, s, k_tail_vcycle<R>, t);
   for (int l = first - 1; l >= 0; l--) {
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_for(lv[l].cells), kBlock, s, k_prolong<R>, lv[l], lv[l + 1]);
@@ -702,16 +789,18 @@ cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, doubl
     for (int a = 0; a < 3; a++) L0.T[a] = F.T[a];
     L0.Dd = F.Dd;
     L0.diag = F.diag;
+    L0.dinv = F.dinv;
     L0.b = ps->r;
     L0.x = ps->z;
-    build_hierarchy(ps->ld, ps->nlev, s);
+    build_hierarchy(ps->ld, ps->nlev, ps->cinv_d, cs == 0, s);
   } else {
     Level<float>& L0 = ps->lf[0];
     const int g = grid_for(n);
     for (int a = 0; a < 3; a++) MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.T[a], L0.T[a], n);
     MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.Dd, L0.Dd, n);
     MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.diag, L0.diag, n);
-    build_hierarchy(ps->lf, ps->nlev, s);
+    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_reciprocal_f, L0.diag, L0.dinv, n);
+    build_hierarchy(ps->lf, ps->nlev, ps->cinv_f, cs == 0, s);
   }
   cudaGraphConditionalHandle handle = 0;
   cudaGraph_t graph = nullptr;
@@ -733,11 +822,11 @@ cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, doubl
   // one CG iteration, preconditioner first; the last finalizer decides whether to continue
   auto body = [&](cudaStream_t bs) {
     if (!flexible) {
-      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, bs);
+      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, (const double*)ps->cinv_d, bs);
     } else {
       const int g = grid_for(n);
       MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_d2f, ps->r, ps->lf[0].b, n);
-      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, bs);
+      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, (const float*)ps->cinv_f, bs);
       MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_f2d, ps->lf[0].x, ps->z, n);
     }
     MDBS_LAUNCH(K_DOTS, nb, kBlock, bs, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, flexible);

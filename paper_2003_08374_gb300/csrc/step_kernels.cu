@@ -451,7 +451,7 @@ __global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp
       tt += ts * inv_h;
     }
   }
-  F.aP[d][f] = ap;
+  F.aP[d][f] = 1.0 / ap;  // stored as the reciprocal: every later use multiplies
   F.rhs0[d][f] = S + V * (tt + Bf);
 }
 
@@ -497,7 +497,7 @@ __global__ void k_jacobi(Prm P, Fld F, Faces3 in, Faces3 out) {
   }
   const double* u[3] = {in.a[0], in.a[1], in.a[2]};
   const double hs = face_H(P, F, u, d, i, j, k, f);
-  out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) / F.aP[d][f];  // V/h = A
+  out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) * F.aP[d][f];  // V/h = A; aP = 1/a_P
 }
 
 __global__ void k_copy_faces(Prm P, Faces3 src, Faces3 dst) {
@@ -520,7 +520,7 @@ __global__ void k_hbya(Prm P, Fld F) {
     return;
   }
   const double* u[3] = {F.u[0], F.u[1], F.u[2]};
-  F.hbya[d][f] = face_H(P, F, u, d, i, j, k, f) / F.aP[d][f];
+  F.hbya[d][f] = face_H(P, F, u, d, i, j, k, f) * F.aP[d][f];
 }
 
 // corrected velocity, Eq. 51
@@ -531,7 +531,7 @@ __global__ void k_correct(Prm P, Fld F) {
   if (!decode_face(P, t, d, i, j, k, f)) return;
   const int cd = d == 0 ? i : (d == 1 ? j : k);
   if (face_kind(P, d, cd) == 1) return;
-  F.u[d][f] = F.hbya[d][f] - (P.A / F.aP[d][f]) * face_dp(P, F.p, d, i, j, k);
+  F.u[d][f] = F.hbya[d][f] - (P.A * F.aP[d][f]) * face_dp(P, F.p, d, i, j, k);
 }
 
 __global__ void k_boundary_velocities(Prm P, Fld F) {

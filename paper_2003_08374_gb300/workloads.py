@@ -72,7 +72,7 @@ class Case:
     max_cg: int = 200
     mg_nu1: int = 2
     mg_nu2: int = 2
-    mg_coarse_sweeps: int = 8
+    mg_coarse_sweeps: int = 0  # 0: exact solve of the coarsest level
     bc: tuple = (INLET, OUTLET, WALL, WALL, WALL, WALL)
     inlet_u: float = 1e-3
     inlet_alpha: float = 1.0
