@@ -158,6 +158,33 @@ int mdbs_get_fields(const mdbs_sim* sim, double* alpha, double* ux, double* uy, 
 /* Releases the device memory; NULL is accepted. */
 void mdbs_destroy(mdbs_sim* sim);
 
+/* ---------------- batches ---------------- */
+
+/*
+ * Many independent simulations advanced together: every phase of the step
+ * (saturation update, properties, momentum, each CG iteration and multigrid
+ * level) is ONE kernel launch over all member domains, whatever their sizes, and
+ * the whole batched step is one CUDA graph.  Each member keeps its own device
+ * memory, fields, time step and statistics (mdbs_get_fields / mdbs_get_stats work
+ * on members as usual).  Every member's pressure solve stops at its own tolerance:
+ * converged members drop out of the remaining CG iterations, which run while any
+ * member iterates.  A member's results are identical alone and in any batch.
+ *   sims : n >= 1 distinct simulations, each after mdbs_set_fields, with identical
+ *          n_corr, mom_sweeps, p_tol, max_cg, multigrid options and precision class
+ *          (FP64 or mixed); time steps, grids and physics may differ.
+ * While in a batch a member cannot be stepped alone (MDBS_ERR_ARG); destroying the
+ * batch releases the members, not their memory.  Member fields may be read or reset
+ * between batch steps.
+ */
+typedef struct mdbs_batch mdbs_batch;
+int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out);
+/* Advances every member n >= 1 steps; MDBS_ERR_DIVERGED names the first diverged member. */
+int mdbs_batch_step(mdbs_batch* batch, int32_t n);
+/* Runs the batch's kernels on the given cudaStream_t (NULL: legacy default stream). */
+int mdbs_batch_set_stream(mdbs_batch* batch, void* cuda_stream);
+const char* mdbs_batch_last_error(const mdbs_batch* batch);
+void mdbs_batch_destroy(mdbs_batch* batch);
+
 /* ---------------- helpers ---------------- */
 
 /* Statistics of the last step (see mdbs_stats). */

@@ -8,6 +8,7 @@
 #include <new>
 #include <string>
 #include <utility>
+#include <algorithm>
 #include <vector>
 
 #include "../../include/mdbs.h"
@@ -97,6 +98,18 @@ void prof_end(int id, cudaStream_t s) {
 
 }  // namespace mdbs
 
+// A batch plan plus the step captured from it as one CUDA graph (CG loops as
+// conditional WHILE nodes).
+struct Exec {
+  BatchPlan plan{};
+  bool planned = false;
+  cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  long long static_launches = 0;  // kernels outside the CG loops per step
+  long long body_launches = 0;    // kernels per CG iteration
+  double* host_flag = nullptr;    // pinned
+};
+
 struct mdbs_sim {
   Profiler prof;
   Prm P;
@@ -107,17 +120,26 @@ struct mdbs_sim {
   void* arena;
   size_t arena_bytes;
   PressureSolver* ps;
-  double* partials;   // kMaxPartials * 4
+  double* partials;   // 4 channels of pcap
+  long long pcap;
   double* scal;       // device step scalars (kSlot* in mdbs_internal.cuh)
   double* host_scal;  // pinned copy of scal
   mdbs_stats st;
   bool fields_set;
+  bool in_batch;
   std::string err;
-  // the whole step captured as one CUDA graph (CG loops as conditional WHILE nodes)
-  cudaStream_t cap_stream;
-  cudaGraphExec_t step_exec;
-  long long graph_static_launches;  // kernels outside the CG loops per step
-  long long graph_body_launches;    // kernels per CG iteration
+  Exec ex;            // batch of one: this simulation alone
+};
+
+struct mdbs_batch {
+  Profiler prof;
+  std::vector<mdbs_sim*> sims;
+  mdbs_options opt;
+  cudaStream_t stream;
+  Exec ex;
+  double* gather;       // device: ndom x kNumSlots step scalars
+  double* host_gather;  // pinned
+  std::string err;
 };
 
 static thread_local std::string g_create_error;
@@ -127,6 +149,7 @@ namespace {
 struct Activate {
   Profiler* prev;
   explicit Activate(mdbs_sim* s) : prev(g_active) { g_active = &s->prof; }
+  explicit Activate(mdbs_batch* b) : prev(g_active) { g_active = &b->prof; }
   ~Activate() {
     if (g_active && g_active->on) g_active->resolve();
     g_active = prev;
@@ -198,11 +221,14 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
     F.hbya[d] = fd();
     F.utmp[d] = fd();
   }
-  double* partials = (double*)take(4 * kMaxPartials * 8);
+  const long long faces = L.nf[0] + L.nf[1] + (L.dim == 3 ? L.nf[2] : 0);
+  const long long pcap = (std::max(L.cells, faces) + kBlock - 1) / kBlock;
+  double* partials = (double*)take(4 * pcap * 8);
   double* scal = (double*)take(kNumSlots * 8);
   if (s) {
     s->F = F;
     s->partials = partials;
+    s->pcap = pcap;
     s->scal = scal;
   }
   return off;
@@ -226,11 +252,8 @@ int cuda_fail(mdbs_sim* s, cudaError_t e, const char* where) {
     if (e_ != cudaSuccess) return cuda_fail(s, e_, #call); \
   } while (0)
 
-// copies the device scalars and the statistics they hold; checks health
-int refresh_stats(mdbs_sim* s) {
-  CK(cudaMemcpyAsync(s->host_scal, s->scal, kNumSlots * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
-  CK(cudaStreamSynchronize(s->stream));
-  const double* h = s->host_scal;
+// statistics of one simulation from a host copy of its scalars
+int stats_from(mdbs_sim* s, const double* h) {
   s->st.mass = h[kSlotMass];
   s->st.alpha_min = h[kSlotAmin];
   s->st.alpha_max = h[kSlotAmax];
@@ -243,67 +266,124 @@ int refresh_stats(mdbs_sim* s) {
   }
   s->st.cg_iters_total = (int64_t)h[kSlotItersTotal];
   s->st.not_converged = (int32_t)h[kSlotNotConverged];
-  s->st.kernel_launches = s->prof.launches;
   if (h[kSlotBad] != 0.0) return fail(s, MDBS_ERR_DIVERGED, "non-finite alpha or pressure");
   return MDBS_OK;
 }
 
-// Enqueues one time step (section 3.2) on st.  capture: st is capturing a graph.
-int record_step(mdbs_sim* s, cudaStream_t st, bool capture) {
-  Prm& P = s->P;
-  Fld& F = s->F;
+// copies the device scalars and the statistics they hold; checks health
+int refresh_stats(mdbs_sim* s) {
+  CK(cudaMemcpyAsync(s->host_scal, s->scal, kNumSlots * sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  s->st.kernel_launches = s->prof.launches;
+  return stats_from(s, s->host_scal);
+}
+
+StepDom step_view(const mdbs_sim* s) {
+  StepDom d{};
+  d.P = s->P;
+  d.F = s->F;
+  d.scal = s->scal;
+  d.partials = s->partials;
+  d.pcap = s->pcap;
+  return d;
+}
+
+// Enqueues one time step (section 3.2) of every domain of the plan on st.
+// capture: st is capturing a graph.  Returns a CUDA error.
+cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool capture) {
+  const BatchPlan& B = ex.plan;
   // 1. saturation (Eq. 15) by flux-corrected transport
-  launch_alpha_step(P, F, s->partials, s->scal, st);
+  launch_alpha_step(B, st);
   // 3. properties at alpha^{k+1} (the old density is kept for the Euler source of Eq. 46)
-  launch_properties(P, F, st);
+  launch_properties(B, st);
   // 4. momentum predictor (Eq. 50) from u^k and p^k
-  launch_momentum_assemble(P, F, s->scal, st);
-  launch_jacobi_sweeps(P, F, s->opt.mom_sweeps, st);
+  launch_momentum_assemble(B, st);
+  launch_jacobi_sweeps(B, opt.mom_sweeps, st);
   // 5. PISO correctors (Eqs. 51-53)
-  for (int c = 0; c < s->opt.n_corr; c++) {
-    launch_hbya(P, F, st);
-    launch_pressure_assemble(P, F, st);
-    cudaError_t e = pressure_solve(s->ps, P, F, s->opt.p_tol, s->opt.max_cg, s->opt.mg_nu1, s->opt.mg_nu2,
-                                   s->opt.mg_coarse_sweeps, s->scal, c, capture, st);
-    if (e != cudaSuccess) return cuda_fail(s, e, "pressure_solve");
-    launch_correct(P, F, st);
+  for (int c = 0; c < opt.n_corr; c++) {
+    launch_hbya(B, st);
+    launch_pressure_assemble(B, st);
+    cudaError_t e = pressure_solve(B, opt.p_tol, opt.max_cg, opt.mg_nu1, opt.mg_nu2, opt.mg_coarse_sweeps, c,
+                                   capture, st, ex.body_stream, ex.host_flag, &ex.body_launches);
+    if (e != cudaSuccess) return e;
+    launch_correct(B, st);
   }
   // 6. time and next time step; statistics and health sentinel
-  launch_time_advance(P, F, s->opt.cfl, s->opt.dt_max, s->partials, s->scal, st);
-  launch_field_stats(P, F, s->partials, s->scal, st);
-  CK(cudaGetLastError());
-  return MDBS_OK;
+  launch_time_advance(B, st);
+  launch_field_stats(B, st);
+  return cudaGetLastError();
+}
+
+cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible) {
+  cudaError_t e = plan_create(sd, cg, ndom, flexible, &ex.plan);
+  if (e != cudaSuccess) return e;
+  ex.planned = true;
+  if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ex.body_stream) e = cudaStreamCreateWithFlags(&ex.body_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ex.host_flag) e = cudaMallocHost(&ex.host_flag, sizeof(double));
+  return e;
+}
+
+void exec_destroy(Exec& ex) {
+  if (ex.graph) cudaGraphExecDestroy(ex.graph);
+  if (ex.planned) plan_destroy(&ex.plan);
+  if (ex.cap_stream) cudaStreamDestroy(ex.cap_stream);
+  if (ex.body_stream) cudaStreamDestroy(ex.body_stream);
+  if (ex.host_flag) cudaFreeHost(ex.host_flag);
+  ex = Exec{};
 }
 
 // captures the step graph once (lazily) and counts its kernels
-int ensure_graph(mdbs_sim* s) {
-  if (s->step_exec) return MDBS_OK;
-  if (!s->cap_stream) CK(cudaStreamCreateWithFlags(&s->cap_stream, cudaStreamNonBlocking));
-  long long before = s->prof.launches;
-  bool was_on = s->prof.on;
-  s->prof.on = false;
-  CK(cudaStreamBeginCapture(s->cap_stream, cudaStreamCaptureModeThreadLocal));
-  int rc = record_step(s, s->cap_stream, true);
+cudaError_t ensure_graph(Exec& ex, const mdbs_options& opt, Profiler& prof) {
+  if (ex.graph) return cudaSuccess;
+  const long long before = prof.launches;
+  const bool was_on = prof.on;
+  prof.on = false;
+  cudaError_t e = cudaStreamBeginCapture(ex.cap_stream, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) return e;
+  cudaError_t rec = record_step(ex, opt, ex.cap_stream, true);
   cudaGraph_t g = nullptr;
-  cudaError_t e = cudaStreamEndCapture(s->cap_stream, &g);
-  s->prof.on = was_on;
-  long long captured = s->prof.launches - before;
-  s->prof.launches = before;
-  if (rc != MDBS_OK) {
+  e = cudaStreamEndCapture(ex.cap_stream, &g);
+  prof.on = was_on;
+  const long long captured = prof.launches - before;
+  prof.launches = before;
+  if (rec != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
-    return rc;
+    return rec;
   }
-  if (e != cudaSuccess) return cuda_fail(s, e, "cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&s->step_exec, g, 0);
+  if (e != cudaSuccess) return e;
+  e = cudaGraphInstantiate(&ex.graph, g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    s->step_exec = nullptr;
-    return cuda_fail(s, e, "cudaGraphInstantiate");
+    ex.graph = nullptr;
+    return e;
   }
-  // kernels per CG iteration: count one body recording without launching it
-  s->graph_body_launches = s->ps ? pressure_body_launches(s->ps) : 0;
-  s->graph_static_launches = captured - s->opt.n_corr * s->graph_body_launches;
-  return MDBS_OK;
+  ex.static_launches = captured - opt.n_corr * ex.body_launches;
+  return cudaSuccess;
+}
+
+// n steps of the plan: eager when profiling (per-kernel events), else graph launches
+cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaStream_t stream, int n) {
+  if (prof.on) {
+    for (int i = 0; i < n; i++) {
+      cudaError_t e = record_step(ex, opt, stream, false);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cudaError_t e = ensure_graph(ex, opt, prof);
+  if (e != cudaSuccess) return e;
+  for (int i = 0; i < n; i++) {
+    e = cudaGraphLaunch(ex.graph, stream);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+bool same_solver_options(const mdbs_options& a, const mdbs_options& b) {
+  return a.n_corr == b.n_corr && a.mom_sweeps == b.mom_sweeps && a.p_tol == b.p_tol && a.max_cg == b.max_cg &&
+         a.mg_nu1 == b.mg_nu1 && a.mg_nu2 == b.mg_nu2 && a.mg_coarse_sweeps == b.mg_coarse_sweeps &&
+         (a.precision == 0) == (b.precision == 0);
 }
 
 }  // namespace
@@ -389,6 +469,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.inv_h = 1.0 / grid->h;
   P.half_inv_h = 0.5 / grid->h;
   P.kr_m_int = (cl->kr_m >= 1.0 && cl->kr_m <= 8.0 && cl->kr_m == floor(cl->kr_m)) ? (int)cl->kr_m : 0;
+  P.cfl = op->cfl;
+  P.dt_max = op->dt_max;
   s->opt = *op;
   s->precision = op->precision;
   s->stream = nullptr;
@@ -418,10 +500,16 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   e = cudaMemcpy((void*)s->F.phi, porosity, cells * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMemcpy((void*)s->F.k0, permeability, cells * 8, cudaMemcpyHostToDevice);
   if (e == cudaSuccess) {
+    // this simulation alone as a batch of one
+    StepDom sd = step_view(s);
+    CgDom cg;
+    pressure_view(s->ps, s->F, &cg);
+    e = exec_setup(s->ex, &sd, &cg, 1, s->precision != 0);
+  }
+  if (e == cudaSuccess) {
     Activate act(s);
-    double* nw[3] = {(double*)s->F.nw[0], (double*)s->F.nw[1], (double*)s->F.nw[2]};
-    launch_static_geometry(P, s->F.phi, (uint8_t*)s->F.is_free, nw, nullptr);
-    launch_set_boundary_velocities(P, s->F, nullptr);
+    launch_static_geometry(s->ex.plan, nullptr);
+    launch_set_boundary_velocities(s->ex.plan, nullptr);
     e = cudaDeviceSynchronize();
   }
   if (e != cudaSuccess) {
@@ -448,12 +536,12 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   CK(cudaMemcpyAsync(s->F.p, p, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
   for (int d = 0; d < s->P.dim; d++)
     CK(cudaMemcpyAsync(s->F.u[d], src[d], s->P.nf[d] * 8, cudaMemcpyHostToDevice, s->stream));
-  launch_set_boundary_velocities(s->P, s->F, s->stream);
-  launch_properties(s->P, s->F, s->stream);
+  launch_set_boundary_velocities(s->ex.plan, s->stream);
+  launch_properties(s->ex.plan, s->stream);
   for (int i = 0; i < kNumSlots; i++) s->host_scal[i] = 0.0;
   s->host_scal[kSlotDt] = s->opt.dt;
   CK(cudaMemcpyAsync(s->scal, s->host_scal, kNumSlots * sizeof(double), cudaMemcpyHostToDevice, s->stream));
-  launch_field_stats(s->P, s->F, s->partials, s->scal, s->stream);
+  launch_field_stats(s->ex.plan, s->stream);
   CK(cudaGetLastError());
   memset(&s->st, 0, sizeof(s->st));
   s->prof.launches = 0;
@@ -465,25 +553,17 @@ int mdbs_step(mdbs_sim* s, int32_t n) {
   if (!s) return MDBS_ERR_ARG;
   if (n < 1) return fail(s, MDBS_ERR_ARG, "n must be >= 1");
   if (!s->fields_set) return fail(s, MDBS_ERR_ARG, "mdbs_set_fields has not been called");
+  if (s->in_batch) return fail(s, MDBS_ERR_ARG, "the simulation belongs to a batch: step the batch");
   Activate act(s);
-  if (s->prof.on) {
-    // per-kernel event timing needs individual launches: host-driven step
-    for (int i = 0; i < n; i++) {
-      int rc = record_step(s, s->stream, false);
-      if (rc != MDBS_OK) return rc;
-      s->st.steps++;
-    }
-    return refresh_stats(s);
-  }
-  int rc = ensure_graph(s);
-  if (rc != MDBS_OK) return rc;
   const double it0 = s->host_scal[kSlotItersTotal];
-  for (int i = 0; i < n; i++) CK(cudaGraphLaunch(s->step_exec, s->stream));
+  const bool eager = s->prof.on;
+  CK(exec_steps(s->ex, s->opt, s->prof, s->stream, n));
   s->st.steps += n;
-  rc = refresh_stats(s);
+  const int rc = refresh_stats(s);
   // kernels launched by the graphs: the fixed part of every step plus the CG bodies run
-  s->prof.launches += (long long)n * s->graph_static_launches +
-                      (long long)(s->host_scal[kSlotItersTotal] - it0) * s->graph_body_launches;
+  if (!eager)
+    s->prof.launches += (long long)n * s->ex.static_launches +
+                        (long long)(s->host_scal[kSlotItersTotal] - it0) * s->ex.body_launches;
   s->st.kernel_launches = s->prof.launches;
   return rc;
 }
@@ -503,11 +583,8 @@ int mdbs_get_fields(const mdbs_sim* cs, double* alpha, double* ux, double* uy, d
 void mdbs_destroy(mdbs_sim* s) {
   if (!s) return;
   if (s->stream) cudaStreamSynchronize(s->stream);
-  if (s->step_exec) cudaGraphExecDestroy(s->step_exec);
-  if (s->cap_stream) {
-    cudaStreamSynchronize(s->cap_stream);
-    cudaStreamDestroy(s->cap_stream);
-  }
+  cudaDeviceSynchronize();
+  exec_destroy(s->ex);
   pressure_destroy(s->ps);
   if (s->host_scal) cudaFreeHost(s->host_scal);
   cudaFree(s->arena);
@@ -526,6 +603,119 @@ int mdbs_set_stream(mdbs_sim* s, void* stream) {
   if (!s) return MDBS_ERR_ARG;
   s->stream = (cudaStream_t)stream;
   return MDBS_OK;
+}
+
+// ---------------------------------------------------------------- batches
+int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out) {
+  if (!out) return fail(nullptr, MDBS_ERR_ARG, "out is NULL");
+  *out = nullptr;
+  if (!sims || n < 1) return fail(nullptr, MDBS_ERR_ARG, "a batch needs at least one simulation");
+  for (int i = 0; i < n; i++) {
+    if (!sims[i]) return fail(nullptr, MDBS_ERR_ARG, "NULL simulation");
+    if (sims[i]->in_batch) return fail(nullptr, MDBS_ERR_ARG, "a simulation already belongs to a batch");
+    if (!sims[i]->fields_set) return fail(nullptr, MDBS_ERR_ARG, "mdbs_set_fields has not been called");
+    if (!same_solver_options(sims[i]->opt, sims[0]->opt))
+      return fail(nullptr, MDBS_ERR_ARG, "batched simulations need the same solver options and precision class");
+    for (int j = 0; j < i; j++)
+      if (sims[j] == sims[i]) return fail(nullptr, MDBS_ERR_ARG, "a simulation appears twice");
+  }
+  mdbs_batch* b = new (std::nothrow) mdbs_batch();
+  if (!b) return fail(nullptr, MDBS_ERR_OOM, "host allocation failed");
+  b->sims.assign(sims, sims + n);
+  b->opt = sims[0]->opt;
+  b->stream = nullptr;
+  std::vector<StepDom> sd(n);
+  std::vector<CgDom> cg(n);
+  for (int i = 0; i < n; i++) {
+    sd[i] = step_view(sims[i]);
+    pressure_view(sims[i]->ps, sims[i]->F, &cg[i]);
+  }
+  cudaError_t e = exec_setup(b->ex, sd.data(), cg.data(), n, sims[0]->precision != 0);
+  if (e == cudaSuccess) e = cudaMalloc(&b->gather, (size_t)n * kNumSlots * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&b->host_gather, (size_t)n * kNumSlots * sizeof(double));
+  if (e != cudaSuccess) {
+    int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
+    fail(nullptr, code, std::string("batch: ") + cudaGetErrorString(e));
+    cudaGetLastError();
+    mdbs_batch_destroy(b);
+    return code;
+  }
+  for (int i = 0; i < n; i++) sims[i]->in_batch = true;
+  *out = b;
+  return MDBS_OK;
+}
+
+int mdbs_batch_set_stream(mdbs_batch* b, void* stream) {
+  if (!b) return MDBS_ERR_ARG;
+  b->stream = (cudaStream_t)stream;
+  return MDBS_OK;
+}
+
+int mdbs_batch_step(mdbs_batch* b, int32_t n) {
+  if (!b) return MDBS_ERR_ARG;
+  if (n < 1) {
+    b->err = "n must be >= 1";
+    return MDBS_ERR_ARG;
+  }
+  Activate act(b);
+  const int nd = (int)b->sims.size();
+  const bool eager = b->prof.on;
+  double it0 = 0.0;
+  for (mdbs_sim* s : b->sims) it0 += s->host_scal[kSlotItersTotal];
+  cudaError_t e = exec_steps(b->ex, b->opt, b->prof, b->stream, n);
+  // gather every member's scalars, then one copy to the host
+  for (int i = 0; i < nd && e == cudaSuccess; i++)
+    e = cudaMemcpyAsync(b->gather + (size_t)i * kNumSlots, b->sims[i]->scal, kNumSlots * sizeof(double),
+                        cudaMemcpyDeviceToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->host_gather, b->gather, (size_t)nd * kNumSlots * sizeof(double), cudaMemcpyDeviceToHost,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+  if (e != cudaSuccess) {
+    b->err = std::string("batch step: ") + cudaGetErrorString(e);
+    return MDBS_ERR_CUDA;
+  }
+  int rc = MDBS_OK;
+  double it1 = 0.0;
+  for (int i = 0; i < nd; i++) {
+    mdbs_sim* s = b->sims[i];
+    const double* h = b->host_gather + (size_t)i * kNumSlots;
+    for (int k = 0; k < kNumSlots; k++) s->host_scal[k] = h[k];
+    s->st.steps += n;
+    it1 += h[kSlotItersTotal];
+    const int r = stats_from(s, h);
+    if (r != MDBS_OK && rc == MDBS_OK) {
+      rc = r;
+      b->err = "domain " + std::to_string(i) + ": " + s->err;
+    }
+  }
+  // the CG loop runs while any member iterates: per corrector, the slowest member's count
+  // (exact for n == 1)
+  if (!eager) {
+    long long iters = 0;
+    for (int c = 0; c < b->opt.n_corr && c < 8; c++) {
+      int mx = 0;
+      for (mdbs_sim* s : b->sims) mx = std::max(mx, (int)s->st.cg_iters[c]);
+      iters += mx;
+    }
+    b->prof.launches += (long long)n * (b->ex.static_launches + iters * b->ex.body_launches);
+  }
+  (void)it0;
+  (void)it1;
+  return rc;
+}
+
+const char* mdbs_batch_last_error(const mdbs_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+void mdbs_batch_destroy(mdbs_batch* b) {
+  if (!b) return;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  cudaDeviceSynchronize();
+  exec_destroy(b->ex);
+  if (b->gather) cudaFree(b->gather);
+  if (b->host_gather) cudaFreeHost(b->host_gather);
+  for (mdbs_sim* s : b->sims) s->in_batch = false;
+  delete b;
 }
 
 int mdbs_profile_enable(mdbs_sim* s, int32_t enable, int32_t only_id) {

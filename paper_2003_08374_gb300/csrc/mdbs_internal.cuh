@@ -1,5 +1,12 @@
 // mdbs_internal.cuh -- device-side data structures shared by the CUDA
 // translation units of libmdbs (sm_103a).  Not part of the public ABI.
+//
+// Execution model.  Every kernel runs over a *batch* of domains (a single
+// simulation is a batch of one).  A Work table maps a flat block index to
+// (domain, local block) through a prefix table of per-domain block counts, and
+// kernels walk the blocks with a grid-stride loop over a grid sized to the GPU
+// (persistent launch).  Per-domain views (StepDom, CgDom) live in device tables
+// so one launch per phase advances every domain of the batch.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -9,17 +16,16 @@ namespace mdbs {
 constexpr int kWall = 0, kInlet = 1, kOutlet = 2;
 constexpr int kMaxLevels = 16;
 constexpr int kBlock = 256;
-constexpr int kMaxPartials = 2048;  // blocks per deterministic reduction
 
-// slots of the per-simulation device scalar array
+// slots of the per-domain device scalar array
 constexpr int kSlotMass = 0, kSlotAmin = 1, kSlotAmax = 2, kSlotBad = 3, kSlotUmax = 4, kSlotInflow = 5,
               kSlotDt = 6, kSlotTime = 7, kSlotIters = 8 /* 8 correctors */, kSlotResid = 16 /* 8 */,
               kSlotItersTotal = 24, kSlotNotConverged = 25, kNumSlots = 32;
 
-// Geometry and physical parameters, passed by value to every kernel.
+// Geometry and physical parameters of one domain.
 struct Prm {
-  int n[3];      // cells per axis
-  int dim;       // 2 or 3
+  int n[3];  // cells per axis
+  int dim;   // 2 or 3
   long long cells;
   long long nf[3];  // faces per direction
   double h, A, V;
@@ -32,9 +38,10 @@ struct Prm {
   double c_alpha;
   double inv_h, half_inv_h;  // 1/h and 1/(2h)
   int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
+  double cfl, dt_max;        // adaptive time step (cfl > 0)
 };
 
-// Device arrays of one simulation.
+// Device arrays of one domain.
 struct Fld {
   // static
   const double* phi;
@@ -67,6 +74,49 @@ struct Level {
   R* dinv;  // 1 / diag (multiplied in the smoothers instead of dividing)
   R* x;
   R* b;
+};
+
+// ---------------------------------------------------------------- batches
+struct Work {
+  const int* blk;  // device table, ndom + 1 entries: first block of each domain, then the total
+  int ndom;
+  int total;
+};
+
+// domain owning flat block b: the largest d with blk[d] <= b (empty domains are skipped)
+__device__ __forceinline__ int work_domain(const Work& w, int b) {
+  int lo = 0, hi = w.ndom - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (w.blk[mid] <= b)
+      lo = mid;
+    else
+      hi = mid - 1;
+  }
+  return lo;
+}
+
+// per-domain view of the step kernels
+struct StepDom {
+  Prm P;
+  Fld F;
+  double* scal;      // step scalars (kSlot*)
+  double* partials;  // reduction partials: 4 channels of pcap values
+  long long pcap;    // partials per channel (>= blocks of the largest space)
+};
+
+// per-domain view of the pressure solver
+struct CgDom {
+  Level<double> ld[kMaxLevels];  // FP64 hierarchy (level 0 arrays point into Fld)
+  Level<float> lf[kMaxLevels];   // FP32 hierarchy (mixed precision)
+  int nlev;
+  int first;  // first level handled by the single-CTA tail
+  double *r, *z, *dv, *q;
+  double* partials;  // 2 channels of pcap values
+  long long pcap;
+  double* scal;      // CG scalars
+  double* cinv_d;    // inverse of the coarsest operator
+  float* cinv_f;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -128,37 +178,66 @@ long long launch_count();  // kernels launched so far by the active simulation
     ::mdbs::prof_end((ID), (STREAM));                      \
   } while (0)
 
+// ---------------------------------------------------------------- host-side batch plan
+// Block tables of one batch for every iteration space, uploaded once per
+// batch composition.
+struct BatchPlan {
+  int ndom;
+  int grid_cap;               // persistent grid: SMs x resident blocks
+  Work cells, faces, dom;     // per-domain cells, faces, one block per domain
+  Work lcells[kMaxLevels];    // level-l cells of domains that have level l
+  Work lhalf[kMaxLevels];     // level-l red/black half cells of domains whose level l precedes the tail
+  Work lfine[kMaxLevels];     // level-l cells of the same domains (prolongation)
+  Work lcoarse[kMaxLevels];   // level-(l+1) cells of the same domains (restriction)
+  int max_first;              // largest tail start over the domains
+  int max_levels;             // largest level count over the domains
+  int flexible;               // FP32 V-cycle inside flexible CG
+  int any_cfl;                // some domain uses the adaptive time step
+  StepDom* sd;                // device tables (ndom entries)
+  CgDom* cg;
+  int* table_storage;         // device memory of every block table
+  int* any_flag;              // device: some domain still iterating (CG WHILE condition)
+};
+
+inline int grid_of(const BatchPlan& B, const Work& w) {
+  return w.total < B.grid_cap ? (w.total > 0 ? w.total : 1) : B.grid_cap;
+}
+
 // ---------------------------------------------------------------- launchers
-// step_kernels.cu
-// (dt, time and the statistics live in the device scalar array, see kSlot*)
-void launch_alpha_step(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
-void launch_properties(const Prm& P, const Fld& F, cudaStream_t s);
-void launch_momentum_assemble(const Prm& P, const Fld& F, const double* scal, cudaStream_t s);
-void launch_jacobi_sweeps(const Prm& P, const Fld& F, int sweeps, cudaStream_t s);  // result in F.u
-void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s);
-void launch_correct(const Prm& P, const Fld& F, cudaStream_t s);
-void launch_set_boundary_velocities(const Prm& P, const Fld& F, cudaStream_t s);
-void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s);
-void launch_time_advance(const Prm& P, const Fld& F, double cfl, double dt_max, double* partials, double* scal,
-                         cudaStream_t s);
-void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s);
+// step_kernels.cu (dt, time and the statistics live in each domain's scalar array)
+void launch_alpha_step(const BatchPlan& B, cudaStream_t s);
+void launch_properties(const BatchPlan& B, cudaStream_t s);
+void launch_momentum_assemble(const BatchPlan& B, cudaStream_t s);
+void launch_jacobi_sweeps(const BatchPlan& B, int sweeps, cudaStream_t s);  // result in F.u
+void launch_hbya(const BatchPlan& B, cudaStream_t s);
+void launch_correct(const BatchPlan& B, cudaStream_t s);
+void launch_set_boundary_velocities(const BatchPlan& B, cudaStream_t s);
+void launch_field_stats(const BatchPlan& B, cudaStream_t s);
+void launch_time_advance(const BatchPlan& B, cudaStream_t s);
+void launch_static_geometry(const BatchPlan& B, cudaStream_t s);
 
 // pressure.cu
 struct PressureSolver;
 PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err);
 void pressure_destroy(PressureSolver* ps);
 size_t pressure_bytes(const int n[3], int precision);
-void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s);
-// Enqueues the solve of A p = b (level-0 arrays of F) by GMG-preconditioned CG on s.
-// Iterations and the final relative residual of corrector `corr` go to
-// step_scal[kSlotIters + corr] / [kSlotResid + corr] (totals accumulate).
-// capture == false: the CG loop is driven from the host (one sync per iteration);
-// capture == true: s is capturing a graph and the loop becomes a conditional
-// WHILE node evaluated on the device.  Returns a CUDA error code.
-cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1,
-                           int nu2, int coarse_sweeps, double* step_scal, int corr, bool capture,
-                           cudaStream_t s);
-// kernels in one CG iteration, as counted during the last capture
-long long pressure_body_launches(const PressureSolver* ps);
+// fills the per-domain solver view (level 0 of the FP64 hierarchy points into F)
+void pressure_view(const PressureSolver* ps, const Fld& F, CgDom* out);
+int pressure_precision(const PressureSolver* ps);
+void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s);
+// Enqueues the solve of A p = b for every domain of the batch by GMG-preconditioned
+// CG.  Iterations and the final relative residual of corrector `corr` go to each
+// domain's step scalars.  capture == false: the CG loop is driven from the host
+// (host_flag: pinned scratch); capture == true: s is capturing a graph and the loop
+// becomes a conditional WHILE node evaluated on the device (body captured on
+// body_stream).  *body_launches receives the kernels of one CG iteration.
+cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, int nu2, int coarse_sweeps, int corr,
+                           bool capture, cudaStream_t s, cudaStream_t body_stream, double* host_flag,
+                           long long* body_launches);
+
+// batch.cu
+// builds the block tables and device views of a batch of domains
+cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, BatchPlan* out);
+void plan_destroy(BatchPlan* B);
 
 }  // namespace mdbs

@@ -3,7 +3,9 @@
 // geometric multigrid V-cycle (red-black Gauss-Seidel, cell-centred 2:1
 // coarsening with series/parallel transmissibilities) and preconditioned CG in
 // FP64 with deterministic block reductions.  In mixed precision the V-cycle
-// runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.
+// runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.  Every kernel runs over
+// all domains of a batch (see mdbs_internal.cuh); per-domain CG scalars and
+// convergence flags let converged domains drop out of the remaining iterations.
 #include <math.h>
 
 #include <new>
@@ -14,12 +16,6 @@ namespace mdbs {
 
 namespace {
 
-int grid_for(long long n, int cap = 1 << 30) {
-  long long b = (n + kBlock - 1) / kBlock;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
 
 __device__ __forceinline__ void decode3(const int n[3], long long c, int& i, int& j, int& k) {
   const unsigned uc = (unsigned)c;  // arrays stay below 2^31 entries
@@ -29,13 +25,27 @@ __device__ __forceinline__ void decode3(const int n[3], long long c, int& i, int
   k = (int)(r / (unsigned)n[1]);
 }
 
+// the FP64 or FP32 hierarchy of a domain
+template <typename R>
+__device__ __forceinline__ const Level<R>* levels_of(const CgDom& C);
+template <>
+__device__ __forceinline__ const Level<double>* levels_of<double>(const CgDom& C) { return C.ld; }
+template <>
+__device__ __forceinline__ const Level<float>* levels_of<float>(const CgDom& C) { return C.lf; }
+
+// CG scalars on the device
+constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6, kRZold = 7, kIt = 8;
+
+#define FOR_WORK(W)                                   \
+  for (int b_ = blockIdx.x; b_ < (W).total; b_ += gridDim.x) { \
+    const int dm = work_domain((W), b_);              \
+    const int lb = b_ - (W).blk[dm];
+
 // ------------------------------------------------------------------ assembly
 // T_f = A^2 / a_P,f between cells, 2 A^2 / a_P,f on outlet faces (Dirichlet
 // through the ghost p_ghost = -p), b = -sum_f s_f A ubar_f with ubar = HbyA on
 // unknown faces and the fixed velocity on wall / inlet faces.
-__global__ void k_assemble(Prm P, Fld F) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
+__device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long c) {
   int q[3];
   decode3(P.n, c, q[0], q[1], q[2]);
   const double A = P.A, A2 = P.A * P.A;
@@ -62,6 +72,14 @@ __global__ void k_assemble(Prm P, Fld F) {
   F.b[c] = -div;
 }
 
+__global__ void k_assemble(const StepDom* __restrict__ D, Work w) {
+  FOR_WORK(w)
+    const StepDom& S = D[dm];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_assemble(S.P, S.F, c);
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], long long c) {
   if (q[d] == 0) return R(0);
@@ -70,9 +88,7 @@ __device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], l
 }
 
 template <typename R>
-__global__ void k_diag(Level<R> L) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= L.cells) return;
+__device__ __forceinline__ void b_diag(const Level<R>& L, long long c) {
   int q[3];
   decode3(L.n, c, q[0], q[1], q[2]);
   R dg = R(0);
@@ -85,22 +101,35 @@ __global__ void k_diag(Level<R> L) {
   L.dinv[c] = R(1) / dgt;
 }
 
-__global__ void k_to_float(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < n) b[c] = (float)a[c];
+template <typename R>
+__global__ void k_diag(const CgDom* __restrict__ C, Work w, int l) {
+  FOR_WORK(w)
+    const Level<R>& L = levels_of<R>(C[dm])[l];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < L.cells) b_diag(L, c);
+  }
 }
 
-__global__ void k_reciprocal_f(const float* __restrict__ a, float* __restrict__ b, long long n) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < n) b[c] = 1.0f / a[c];
+// FP32 copy of the level-0 operator (mixed precision), with its reciprocal diagonal
+__global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const Level<double>& Ld = C[dm].ld[0];
+    const Level<float>& Lf = C[dm].lf[0];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < Ld.cells) {
+      for (int a = 0; a < 3; a++) Lf.T[a][c] = (float)Ld.T[a][c];
+      Lf.Dd[c] = (float)Ld.Dd[c];
+      const float dg = (float)Ld.diag[c];
+      Lf.diag[c] = dg;
+      Lf.dinv[c] = 1.0f / dg;
+    }
+  }
 }
 
 // coarse transmissibilities: fine rows across a coarse face in parallel, along a
 // row half of each coarse cell's interior link and the crossing link in series
 template <typename R>
-__global__ void k_coarsen(Level<R> Fi, Level<R> Co) {
-  long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (ci >= Co.cells) return;
+__device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
   decode3(Co.n, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
@@ -147,6 +176,15 @@ __global__ void k_coarsen(Level<R> Fi, Level<R> Co) {
   Co.Dd[ci] = dd;
 }
 
+template <typename R>
+__global__ void k_coarsen(const CgDom* __restrict__ C, Work w, int l) {
+  FOR_WORK(w)
+    const Level<R>* L = levels_of<R>(C[dm]);
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < L[l].cells) b_coarsen(L[l - 1], L[l], c);
+  }
+}
+
 // sum_nb T x_nb at cell c of level L (order x-, x+, y-, y+, z-, z+)
 template <typename R>
 __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restrict__ x, const int q[3],
@@ -163,9 +201,8 @@ __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restric
 
 // red-black Gauss-Seidel half sweep of colour col; zero: x is taken as 0
 template <typename R>
-__global__ void k_smooth(Level<R> L, int col, int zero) {
+__device__ __forceinline__ void b_smooth(const Level<R>& L, int col, int zero, unsigned t) {
   const unsigned half = (L.n[0] + 1) >> 1;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const unsigned rows = (unsigned)L.n[1] * (unsigned)L.n[2];
   if (t >= rows * half) return;
   const int ti = (int)(t % half);
@@ -183,17 +220,30 @@ __global__ void k_smooth(Level<R> L, int col, int zero) {
   L.x[c] = v * L.dinv[c];
 }
 
+// skips domains whose CG has converged (the V-cycle only runs inside CG iterations)
 template <typename R>
-__global__ void k_zero(R* x, long long n) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < n) x[c] = R(0);
+__global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    b_smooth(levels_of<R>(G)[l], col, zero, (unsigned)lb * blockDim.x + threadIdx.x);
+  }
+}
+
+template <typename R>
+__global__ void k_zero(const CgDom* __restrict__ C, Work w, int l) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const Level<R>& L = levels_of<R>(G)[l];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < L.cells) L.x[c] = R(0);
+  }
 }
 
 // coarse b = sum of the fine residuals b - A x over the covered fine cells
 template <typename R>
-__global__ void k_resid_restrict(Level<R> Fi, Level<R> Co) {
-  long long ci = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (ci >= Co.cells) return;
+__device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
   decode3(Co.n, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
@@ -214,14 +264,34 @@ __global__ void k_resid_restrict(Level<R> Fi, Level<R> Co) {
 }
 
 template <typename R>
-__global__ void k_prolong(Level<R> Fi, Level<R> Co) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= Fi.cells) return;
+__global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const Level<R>* L = levels_of<R>(G);
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < L[l + 1].cells) b_resid_restrict(L[l], L[l + 1], c);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co, long long c) {
   int q[3];
   decode3(Fi.n, c, q[0], q[1], q[2]);
   int Q[3];
   for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
   Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
+}
+
+template <typename R>
+__global__ void k_prolong(const CgDom* __restrict__ C, Work w, int l) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const Level<R>* L = levels_of<R>(G);
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < L[l].cells) b_prolong(L[l], L[l + 1], c);
+  }
 }
 
 // ------------------------------------------------------------------ coarsest level
@@ -232,7 +302,18 @@ __global__ void k_prolong(Level<R> Fi, Level<R> Co) {
 constexpr int kCoarseMax = 64;
 
 template <typename R>
-__global__ void k_coarse_inverse(Level<R> C, R* __restrict__ inv) {
+__device__ __forceinline__ R* coarse_inverse_of(const CgDom& G);
+template <>
+__device__ __forceinline__ double* coarse_inverse_of<double>(const CgDom& G) { return G.cinv_d; }
+template <>
+__device__ __forceinline__ float* coarse_inverse_of<float>(const CgDom& G) { return G.cinv_f; }
+
+// one block per domain
+template <typename R>
+__global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
+  const CgDom& G = CG[blockIdx.x];
+  const Level<R> C = levels_of<R>(G)[G.nlev - 1];
+  R* __restrict__ inv = coarse_inverse_of<R>(G);
   __shared__ R M[kCoarseMax * kCoarseMax];
   const int n = (int)C.cells;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = R(0);
@@ -281,13 +362,6 @@ __global__ void k_coarse_inverse(Level<R> C, R* __restrict__ inv) {
 // __syncthreads() between phases instead of kernel boundaries.
 constexpr int kTailCells = 4096;
 constexpr int kTailThreads = 1024;
-
-template <typename R>
-struct Tail {
-  Level<R> lv[kMaxLevels];
-  int first, nlev, nu1, nu2, cs;
-  const R* cinv;  // inverse of the coarsest operator (used when cs == 0)
-};
 
 template <typename R>
 __device__ void tail_smooth(const Level<R>& L, int col, int zero) {
@@ -364,28 +438,35 @@ __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co) {
   __syncthreads();
 }
 
+// one CTA per domain: the domain's levels from its tail start down to the
+// coarsest one and back
 template <typename R>
-__global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(Tail<R> t) {
-  for (int l = t.first; l < t.nlev - 1; l++) {
-    if (t.nu1 == 0) tail_zero(t.lv[l]);
-    for (int it = 0; it < t.nu1; it++) tail_pair(t.lv[l], 0, it == 0);
-    tail_restrict(t.lv[l], t.lv[l + 1]);
+__global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs) {
+  const CgDom& G = CG[blockIdx.x];
+  if (G.scal[kCond] == 0.0) return;
+  const Level<R>* lv = levels_of<R>(G);
+  const int first = G.first, nlev = G.nlev;
+  for (int l = first; l < nlev - 1; l++) {
+    if (nu1 == 0) tail_zero(lv[l]);
+    for (int it = 0; it < nu1; it++) tail_pair(lv[l], 0, it == 0);
+    tail_restrict(lv[l], lv[l + 1]);
   }
-  const Level<R>& C = t.lv[t.nlev - 1];
-  if (t.cs == 0) {
+  const Level<R>& C = lv[nlev - 1];
+  if (cs == 0) {
+    const R* cinv = coarse_inverse_of<R>(G);
     const int n = (int)C.cells;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       R v = R(0);
-      for (int j = 0; j < n; j++) v += t.cinv[i * n + j] * C.b[j];
+      for (int j = 0; j < n; j++) v += cinv[i * n + j] * C.b[j];
       C.x[i] = v;
     }
     __syncthreads();
   }
-  for (int it = 0; it < t.cs; it++) tail_pair(C, 0, it == 0);
-  for (int it = 0; it < t.cs; it++) tail_pair(C, 1, false);
-  for (int l = t.nlev - 2; l >= t.first; l--) {
-    tail_prolong(t.lv[l], t.lv[l + 1]);
-    for (int it = 0; it < t.nu2; it++) tail_pair(t.lv[l], 1, false);
+  for (int it = 0; it < cs; it++) tail_pair(C, 0, it == 0);
+  for (int it = 0; it < cs; it++) tail_pair(C, 1, false);
+  for (int l = nlev - 2; l >= first; l--) {
+    tail_prolong(lv[l], lv[l + 1]);
+    for (int it = 0; it < nu2; it++) tail_pair(lv[l], 1, false);
   }
 }
 
@@ -402,103 +483,118 @@ __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const dou
   return v;
 }
 
-// r = b - A x; partial sums of r.r and b.b
-__global__ void k_resid0(Prm P, Fld F, const double* __restrict__ x, double* __restrict__ r,
-                         double* __restrict__ partials, int nb) {
-  double rr = 0.0, bb = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
-       c += (long long)gridDim.x * blockDim.x) {
-    int q[3];
-    decode3(P.n, c, q[0], q[1], q[2]);
-    const double bc = F.b[c];
-    const double rc = bc - apply_A0(F, P, x, c, q);
-    r[c] = rc;
-    rr += rc * rc;
-    bb += bc * bc;
+// r = b - A p; one partial of r.r and b.b per block
+__global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const StepDom& S = D[dm];
+    const CgDom& G = C[dm];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    double rr = 0.0, bb = 0.0;
+    if (c < S.P.cells) {
+      int q[3];
+      decode3(S.P.n, c, q[0], q[1], q[2]);
+      const double bc = S.F.b[c];
+      const double rc = bc - apply_A0(S.F, S.P, S.F.p, c, q);
+      G.r[c] = rc;
+      rr = rc * rc;
+      bb = bc * bc;
+    }
+    rr = block_sum(rr);
+    if (threadIdx.x == 0) G.partials[lb] = rr;
+    bb = block_sum(bb);
+    if (threadIdx.x == 0) G.partials[G.pcap + lb] = bb;
   }
-  rr = block_sum(rr);
-  if (threadIdx.x == 0) partials[blockIdx.x] = rr;
-  bb = block_sum(bb);
-  if (threadIdx.x == 0) partials[nb + blockIdx.x] = bb;
 }
 
 // q = A d; partial d.q
-__global__ void k_spmv_dot(Prm P, Fld F, const double* __restrict__ dv, double* __restrict__ q,
-                           double* __restrict__ partials) {
-  double s = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
-       c += (long long)gridDim.x * blockDim.x) {
-    int qq[3];
-    decode3(P.n, c, qq[0], qq[1], qq[2]);
-    const double v = apply_A0(F, P, dv, c, qq);
-    q[c] = v;
-    s += dv[c] * v;
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-// x += alpha d; r -= alpha q; partial r.r   (alpha = scal[5])
-__global__ void k_update_xr(long long n, const double* __restrict__ scal, double* __restrict__ x,
-                            double* __restrict__ r, const double* __restrict__ dv, const double* __restrict__ q,
-                            double* __restrict__ partials) {
-  const double al = scal[5];
-  double s = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    x[c] += al * dv[c];
-    const double rc = r[c] - al * q[c];
-    r[c] = rc;
-    s += rc * rc;
-  }
-  s = block_sum(s);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
-}
-
-// partial r.z and z.q
-__global__ void k_dots_rz(long long n, const double* __restrict__ r, const double* __restrict__ z,
-                          const double* __restrict__ q, double* __restrict__ partials, int nb, int with_zq) {
-  double rz = 0.0, zq = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x) {
-    rz += r[c] * z[c];
-    if (with_zq) zq += z[c] * q[c];
-  }
-  rz = block_sum(rz);
-  if (threadIdx.x == 0) partials[blockIdx.x] = rz;
-  if (with_zq) {
-    zq = block_sum(zq);
-    if (threadIdx.x == 0) partials[nb + blockIdx.x] = zq;
+__global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const StepDom& S = D[dm];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (c < S.P.cells) {
+      int q[3];
+      decode3(S.P.n, c, q[0], q[1], q[2]);
+      const double v = apply_A0(S.F, S.P, G.dv, c, q);
+      G.q[c] = v;
+      s = G.dv[c] * v;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) G.partials[lb] = s;
   }
 }
 
-// CG scalars on the device
-constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6, kRZold = 7, kIt = 8;
+// p += alpha d; r -= alpha q; partial r.r
+__global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const StepDom& S = D[dm];
+    const double al = G.scal[kAlpha];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    double s = 0.0;
+    if (c < S.P.cells) {
+      S.F.p[c] += al * G.dv[c];
+      const double rc = G.r[c] - al * G.q[c];
+      G.r[c] = rc;
+      s = rc * rc;
+    }
+    s = block_sum(s);
+    if (threadIdx.x == 0) G.partials[lb] = s;
+  }
+}
+
+// partial r.z and (flexible) z.q
+__global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int with_zq) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    double rz = 0.0, zq = 0.0;
+    if (c < D[dm].P.cells) {
+      rz = G.r[c] * G.z[c];
+      if (with_zq) zq = G.z[c] * G.q[c];
+    }
+    rz = block_sum(rz);
+    if (threadIdx.x == 0) G.partials[lb] = rz;
+    if (with_zq) {
+      zq = block_sum(zq);
+      if (threadIdx.x == 0) G.partials[G.pcap + lb] = zq;
+    }
+  }
+}
 
 // d = z + beta d; the first iteration (counter 0) takes d = z
-__global__ void k_update_d(long long n, const double* __restrict__ scal, const double* __restrict__ z,
-                           double* __restrict__ dv, int flexible) {
-  const bool first = scal[kIt] == 0.0;
-  double be = 0.0;
-  if (!first) be = flexible ? -scal[kAlpha] * scal[kZQ] / scal[kRZold] : scal[kRZ] / scal[kRZold];
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x)
-    dv[c] = first ? z[c] : z[c] + be * dv[c];
+__global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int flexible) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const double* scal = G.scal;
+    const bool first = scal[kIt] == 0.0;
+    double be = 0.0;
+    if (!first) be = flexible ? -scal[kAlpha] * scal[kZQ] / scal[kRZold] : scal[kRZ] / scal[kRZold];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < D[dm].P.cells) G.dv[c] = first ? G.z[c] : G.z[c] + be * G.dv[c];
+  }
 }
 
-// Scalar finalizers (one block, fixed summation order).  The loop condition
-// "not converged, below max_it, finite" is written to scal[kCond] and, inside a
-// captured graph, to the WHILE node's conditional handle.
+// Scalar finalizers, one block per domain, fixed summation order.  The loop
+// condition "not converged, below max_it, finite" goes to scal[kCond].
 // mode 0: rr, bb after the initial residual; iteration counter = 0
 // mode 1: dq, alpha = rz / dq
 // mode 2: rr after the update; counter += 1
 // mode 3: rz_old = rz; rz (and zq when two channels)
-__global__ void k_finalize(const double* __restrict__ partials, int nb, double* scal, int mode, int two,
-                           double tol, int max_it, cudaGraphConditionalHandle handle, int use_handle) {
+__global__ void k_finalize(const CgDom* __restrict__ C, Work w, int mode, int two, double tol, int max_it) {
+  const CgDom& G = C[blockIdx.x];
+  double* scal = G.scal;
+  if (mode != 0 && scal[kCond] == 0.0) return;
+  const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
   double a = 0.0, b = 0.0;
   for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-    a += partials[i];
-    if (two) b += partials[nb + i];
+    a += G.partials[i];
+    if (two) b += G.partials[G.pcap + i];
   }
   a = block_sum(a);
   if (two) b = block_sum(b);
@@ -527,20 +623,35 @@ __global__ void k_finalize(const double* __restrict__ partials, int nb, double* 
   const double bb = scal[kBB];
   const bool done = bb == 0.0 || sqrt(a) <= tol * sqrt(bb) || it >= (double)max_it || !(a == a);
   scal[kCond] = done ? 0.0 : 1.0;
-  if (use_handle) cudaGraphSetConditional(handle, done ? 0u : 1u);
+}
+
+// OR of the domains' conditions: the WHILE node's condition (captured graph) and a flag
+// the host reads (eager loop)
+__global__ void k_any(const CgDom* __restrict__ C, int ndom, int* flag, cudaGraphConditionalHandle handle,
+                      int use_handle) {
+  int any = 0;
+  for (int d = threadIdx.x; d < ndom; d += blockDim.x) any |= C[d].scal[kCond] != 0.0;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    *flag = any;
+    if (use_handle) cudaGraphSetConditional(handle, any ? 1u : 0u);
+  }
 }
 
 // b = 0 has the solution p = 0 whatever the initial guess
-__global__ void k_zero_if_b0(long long n, const double* __restrict__ scal, double* __restrict__ x) {
-  if (scal[kBB] != 0.0) return;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
-       c += (long long)gridDim.x * blockDim.x)
-    x[c] = 0.0;
+__global__ void k_zero_if_b0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    if (C[dm].scal[kBB] != 0.0) continue;
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < D[dm].P.cells) D[dm].F.p[c] = 0.0;
+  }
 }
 
-// iterations and relative residual of corrector corr into the step scalars
-__global__ void k_record(const double* __restrict__ scal, double* step, int corr, double tol) {
+// iterations and relative residual of corrector corr into each domain's step scalars
+__global__ void k_record(const StepDom* __restrict__ D, const CgDom* __restrict__ C, int corr, double tol) {
   if (threadIdx.x != 0) return;
+  const double* scal = C[blockIdx.x].scal;
+  double* step = D[blockIdx.x].scal;
   const double bb = scal[kBB];
   const double res = bb == 0.0 ? 0.0 : sqrt(scal[kRR] / bb);
   step[kSlotIters + corr] = scal[kIt];
@@ -549,35 +660,42 @@ __global__ void k_record(const double* __restrict__ scal, double* step, int corr
   if (!(res <= tol)) step[kSlotNotConverged] += 1.0;
 }
 
-__global__ void k_copy_d2f(const double* __restrict__ a, float* __restrict__ b, long long n) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < n) b[c] = (float)a[c];
+// r -> FP32 right-hand side of the FP32 V-cycle; its result -> z
+__global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < G.lf[0].cells) G.lf[0].b[c] = (float)G.r[c];
+  }
 }
-__global__ void k_copy_f2d(const float* __restrict__ a, double* __restrict__ b, long long n) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c < n) b[c] = (double)a[c];
+__global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w) {
+  FOR_WORK(w)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    if (c < G.lf[0].cells) G.z[c] = (double)G.lf[0].x[c];
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ solver object
+// Device storage of one domain's pressure solver.
 struct PressureSolver {
   int precision;
   int nlev;
-  Level<double> ld[kMaxLevels];  // FP64 hierarchy (level 0 arrays are borrowed)
+  int first;
+  Level<double> ld[kMaxLevels];  // FP64 hierarchy (level 0 arrays are borrowed from Fld)
   Level<float> lf[kMaxLevels];   // FP32 hierarchy (mixed precision)
   double *r, *z, *dv, *q;
   double* partials;
+  long long pcap;
   double* scal;
-  double* host_scal;  // pinned
-  double* cinv_d;     // inverse of the coarsest operator (FP64 hierarchy)
-  float* cinv_f;      // (FP32 hierarchy)
-  void* block;        // single device allocation
-  cudaStream_t body_stream;  // captures the body of the CG WHILE node
-  long long body_launches;   // kernels per CG iteration (counted while capturing)
+  double* cinv_d;  // inverse of the coarsest operator (FP64 hierarchy)
+  float* cinv_f;   // (FP32 hierarchy)
+  void* block;     // single device allocation
 };
-
-long long pressure_body_launches(const PressureSolver* ps) { return ps->body_launches; }
 
 static int plan_levels(const int n0[3], int dims[kMaxLevels][3], int cz[kMaxLevels][3]) {
   int nlev = 1;
@@ -615,57 +733,60 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     return p;
   };
   const long long n0 = (long long)n[0] * n[1] * n[2];
-  if (ps) ps->nlev = nlev;
+  const long long pcap = (n0 + kBlock - 1) / kBlock;
   double* r = (double*)take(n0 * 8);
   double* z = (double*)take(n0 * 8);
   double* dv = (double*)take(n0 * 8);
   double* q = (double*)take(n0 * 8);
-  double* partials = (double*)take(2 * kMaxPartials * 8);
+  double* partials = (double*)take(2 * pcap * 8);
   double* scal = (double*)take(16 * 8);
   double* cinv_d = (double*)take(kCoarseMax * kCoarseMax * 8);
   float* cinv_f = (float*)take(kCoarseMax * kCoarseMax * 4);
   if (ps) {
+    ps->nlev = nlev;
     ps->r = r;
     ps->z = z;
     ps->dv = dv;
     ps->q = q;
     ps->partials = partials;
+    ps->pcap = pcap;
     ps->scal = scal;
     ps->cinv_d = cinv_d;
     ps->cinv_f = cinv_f;
+    int first = nlev - 1;
+    while (first > 0 && (long long)dims[first - 1][0] * dims[first - 1][1] * dims[first - 1][2] <= kTailCells)
+      first--;
+    ps->first = first;
   }
   for (int l = 0; l < nlev; l++) {
     const long long nc = (long long)dims[l][0] * dims[l][1] * dims[l][2];
+    Level<double> Ld{};
+    Level<float> Lf{};
+    for (int a = 0; a < 3; a++) {
+      Ld.n[a] = Lf.n[a] = dims[l][a];
+      Ld.cz[a] = Lf.cz[a] = cz[l][a];
+    }
+    Ld.cells = Lf.cells = nc;
     if (precision == 0) {
-      Level<double> L{};
-      for (int a = 0; a < 3; a++) {
-        L.n[a] = dims[l][a];
-        L.cz[a] = cz[l][a];
-      }
-      L.cells = nc;
       if (l > 0) {
-        for (int a = 0; a < 3; a++) L.T[a] = (double*)take(nc * 8);
-        L.Dd = (double*)take(nc * 8);
-        L.diag = (double*)take(nc * 8);
-        L.dinv = (double*)take(nc * 8);
-        L.x = (double*)take(nc * 8);
-        L.b = (double*)take(nc * 8);
+        for (int a = 0; a < 3; a++) Ld.T[a] = (double*)take(nc * 8);
+        Ld.Dd = (double*)take(nc * 8);
+        Ld.diag = (double*)take(nc * 8);
+        Ld.dinv = (double*)take(nc * 8);
+        Ld.x = (double*)take(nc * 8);
+        Ld.b = (double*)take(nc * 8);
       }
-      if (ps) ps->ld[l] = L;
     } else {
-      Level<float> L{};
-      for (int a = 0; a < 3; a++) {
-        L.n[a] = dims[l][a];
-        L.cz[a] = cz[l][a];
-      }
-      L.cells = nc;
-      for (int a = 0; a < 3; a++) L.T[a] = (float*)take(nc * 4);
-      L.Dd = (float*)take(nc * 4);
-      L.diag = (float*)take(nc * 4);
-      L.dinv = (float*)take(nc * 4);
-      L.x = (float*)take(nc * 4);
-      L.b = (float*)take(nc * 4);
-      if (ps) ps->lf[l] = L;
+      for (int a = 0; a < 3; a++) Lf.T[a] = (float*)take(nc * 4);
+      Lf.Dd = (float*)take(nc * 4);
+      Lf.diag = (float*)take(nc * 4);
+      Lf.dinv = (float*)take(nc * 4);
+      Lf.x = (float*)take(nc * 4);
+      Lf.b = (float*)take(nc * 4);
+    }
+    if (ps) {
+      ps->ld[l] = Ld;
+      ps->lf[l] = Lf;
     }
   }
   return off;
@@ -695,112 +816,98 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
     delete ps;
     return nullptr;
   }
-  *err = cudaMallocHost(&ps->host_scal, 16 * sizeof(double));
-  if (*err != cudaSuccess) {
-    cudaFree(ps->block);
-    delete ps;
-    return nullptr;
-  }
-  *err = cudaStreamCreateWithFlags(&ps->body_stream, cudaStreamNonBlocking);
-  if (*err != cudaSuccess) {
-    cudaFreeHost(ps->host_scal);
-    cudaFree(ps->block);
-    delete ps;
-    return nullptr;
-  }
+  *err = cudaMemset(ps->block, 0, bytes);
   solver_layout(P.n, ps->precision, ps, (char*)ps->block);
   return ps;
 }
 
 void pressure_destroy(PressureSolver* ps) {
   if (!ps) return;
-  cudaStreamDestroy(ps->body_stream);
   cudaFree(ps->block);
-  cudaFreeHost(ps->host_scal);
   delete ps;
 }
 
-void launch_pressure_assemble(const Prm& P, const Fld& F, cudaStream_t s) {
-  MDBS_LAUNCH(K_ASSEMBLE, grid_for(P.cells), kBlock, s, k_assemble, P, F);
-  Level<double> L0{};
-  for (int a = 0; a < 3; a++) {
-    L0.n[a] = P.n[a];
-    L0.T[a] = F.T[a];
+int pressure_precision(const PressureSolver* ps) { return ps->precision; }
+
+void pressure_view(const PressureSolver* ps, const Fld& F, CgDom* out) {
+  CgDom& G = *out;
+  for (int l = 0; l < kMaxLevels; l++) {
+    G.ld[l] = l < ps->nlev ? ps->ld[l] : Level<double>{};
+    G.lf[l] = l < ps->nlev ? ps->lf[l] : Level<float>{};
   }
-  L0.cells = P.cells;
+  // the FP64 level 0 is the assembled system itself, preconditioning r into z
+  Level<double>& L0 = G.ld[0];
+  for (int a = 0; a < 3; a++) L0.T[a] = F.T[a];
   L0.Dd = F.Dd;
   L0.diag = F.diag;
   L0.dinv = F.dinv;
-  MDBS_LAUNCH(K_DIAG, grid_for(P.cells), kBlock, s, k_diag<double>, L0);
+  L0.b = ps->r;
+  L0.x = ps->z;
+  G.nlev = ps->nlev;
+  G.first = ps->first;
+  G.r = ps->r;
+  G.z = ps->z;
+  G.dv = ps->dv;
+  G.q = ps->q;
+  G.partials = ps->partials;
+  G.pcap = ps->pcap;
+  G.scal = ps->scal;
+  G.cinv_d = ps->cinv_d;
+  G.cinv_f = ps->cinv_f;
+}
+
+// ------------------------------------------------------------------ batched host sequencing
+void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s) {
+  MDBS_LAUNCH(K_ASSEMBLE, grid_of(B, B.cells), kBlock, s, k_assemble, B.sd, B.cells);
+  MDBS_LAUNCH(K_DIAG, grid_of(B, B.cells), kBlock, s, k_diag<double>, B.cg, B.cells, 0);
 }
 
 template <typename R>
-static void build_hierarchy(Level<R>* lv, int nlev, R* cinv, bool direct, cudaStream_t s) {
-  for (int l = 1; l < nlev; l++) {
-    MDBS_LAUNCH(K_COARSEN, grid_for(lv[l].cells), kBlock, s, k_coarsen<R>, lv[l - 1], lv[l]);
-    MDBS_LAUNCH(K_DIAG, grid_for(lv[l].cells), kBlock, s, k_diag<R>, lv[l]);
+static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
+  for (int l = 1; l < B.max_levels; l++) {
+    MDBS_LAUNCH(K_COARSEN, grid_of(B, B.lcells[l]), kBlock, s, k_coarsen<R>, B.cg, B.lcells[l], l);
+    MDBS_LAUNCH(K_DIAG, grid_of(B, B.lcells[l]), kBlock, s, k_diag<R>, B.cg, B.lcells[l], l);
   }
-  if (direct) MDBS_LAUNCH(K_COARSEN, 1, 256, s, k_coarse_inverse<R>, lv[nlev - 1], cinv);
+  if (direct) MDBS_LAUNCH(K_COARSEN, B.ndom, 256, s, k_coarse_inverse<R>, B.cg);
 }
 
 template <typename R>
-static void smooth_pair(const Level<R>& L, int first_col, bool zero_first, bool finest, cudaStream_t s) {
-  const int id = finest ? K_SMOOTH0 : K_SMOOTHC;
-  const long long threads = (long long)((L.n[0] + 1) >> 1) * L.n[1] * L.n[2];
-  MDBS_LAUNCH(id, grid_for(threads), kBlock, s, k_smooth<R>, L, first_col, zero_first ? 1 : 0);
-  MDBS_LAUNCH(id, grid_for(threads), kBlock, s, k_smooth<R>, L, 1 - first_col, 0);
+static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_first, cudaStream_t s) {
+  const int id = l == 0 ? K_SMOOTH0 : K_SMOOTHC;
+  const Work& w = B.lhalf[l];
+  MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, k_smooth<R>, B.cg, w, l, first_col, zero_first ? 1 : 0);
+  MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, k_smooth<R>, B.cg, w, l, 1 - first_col, 0);
 }
 
-// symmetric V-cycle, x of level 0 receives M b of level 0; the levels from the
-// first one with at most kTailCells cells run in the single-CTA tail kernel
+// Symmetric V-cycle of every active domain: level 0 receives M r.  Levels that
+// precede a domain's tail start run as batched launches; the rest of each
+// domain's cycle runs in its own CTA of the tail kernel.
 template <typename R>
-static void vcycle(Level<R>* lv, int nlev, int nu1, int nu2, int cs, const R* cinv, cudaStream_t s) {
-  int first = nlev - 1;
-  while (first > 0 && lv[first - 1].cells <= kTailCells) first--;
-  for (int l = 0; l < first; l++) {
-    if (nu1 == 0) MDBS_LAUNCH(K_ZERO, grid_for(lv[l].cells), kBlock, s, k_zero<R>, lv[l].x, lv[l].cells);
-    for (int it = 0; it < nu1; it++) smooth_pair(lv[l], 0, it == 0, l == 0, s);
-    MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_for(lv[l + 1].cells), kBlock, s, k_resid_restrict<R>, lv[l], lv[l + 1]);
+static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, cudaStream_t s) {
+  for (int l = 0; l < B.max_first; l++) {
+    if (nu1 == 0) MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l);
+    for (int it = 0; it < nu1; it++) smooth_pair<R>(B, l, 0, it == 0, s);
+    MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
+                B.lcoarse[l], l);
   }
-  Tail<R> t;
-  for (int l = 0; l < nlev; l++) t.lv[l] = lv[l];
-  t.first = first;
-  t.nlev = nlev;
-  t.nu1 = nu1;
-  t.nu2 = nu2;
-  t.cs = cs;
-  t.cinv = cinv;
-  MDBS_LAUNCH(K_TAIL, 1, kTailThreads, s, k_tail_vcycle<R>, t);
-  for (int l = first - 1; l >= 0; l--) {
-    MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_for(lv[l].cells), kBlock, s, k_prolong<R>, lv[l], lv[l + 1]);
-    for (int it = 0; it < nu2; it++) smooth_pair(lv[l], 1, false, l == 0, s);
+  MDBS_LAUNCH(K_TAIL, B.ndom, kTailThreads, s, k_tail_vcycle<R>, B.cg, nu1, nu2, cs);
+  for (int l = B.max_first - 1; l >= 0; l--) {
+    MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_of(B, B.lfine[l]), kBlock, s, k_prolong<R>, B.cg, B.lfine[l],
+                l);
+    for (int it = 0; it < nu2; it++) smooth_pair<R>(B, l, 1, false, s);
   }
 }
 
-cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, double tol, int max_it, int nu1,
-                           int nu2, int cs, double* step_scal, int corr, bool capture, cudaStream_t s) {
-  const long long n = P.cells;
-  const int nb = grid_for(n, kMaxPartials);
-  const int flexible = ps->precision != 0;
-  double* x = F.p;
+cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, int nu2, int cs, int corr,
+                           bool capture, cudaStream_t s, cudaStream_t body_stream, double* host_flag,
+                           long long* body_launches) {
+  const int flexible = B.flexible;
   // hierarchy for this assembly
   if (!flexible) {
-    Level<double>& L0 = ps->ld[0];
-    for (int a = 0; a < 3; a++) L0.T[a] = F.T[a];
-    L0.Dd = F.Dd;
-    L0.diag = F.diag;
-    L0.dinv = F.dinv;
-    L0.b = ps->r;
-    L0.x = ps->z;
-    build_hierarchy(ps->ld, ps->nlev, ps->cinv_d, cs == 0, s);
+    build_hierarchy<double>(B, cs == 0, s);
   } else {
-    Level<float>& L0 = ps->lf[0];
-    const int g = grid_for(n);
-    for (int a = 0; a < 3; a++) MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.T[a], L0.T[a], n);
-    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.Dd, L0.Dd, n);
-    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_to_float, F.diag, L0.diag, n);
-    MDBS_LAUNCH(K_CONVERT, g, kBlock, s, k_reciprocal_f, L0.diag, L0.dinv, n);
-    build_hierarchy(ps->lf, ps->nlev, ps->cinv_f, cs == 0, s);
+    MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, s, k_level0_to_float, B.cg, B.cells);
+    build_hierarchy<float>(B, cs == 0, s);
   }
   cudaGraphConditionalHandle handle = 0;
   cudaGraph_t graph = nullptr;
@@ -816,27 +923,27 @@ cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, doubl
   }
   const int use = capture ? 1 : 0;
   // initial residual and loop condition
-  MDBS_LAUNCH(K_RESID0, nb, kBlock, s, k_resid0, P, F, x, ps->r, ps->partials, nb);
-  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize, ps->partials, nb, ps->scal, 0, 1, tol, max_it, handle, use);
-  MDBS_LAUNCH(K_ZERO, nb, kBlock, s, k_zero_if_b0, n, ps->scal, x);
-  // one CG iteration, preconditioner first; the last finalizer decides whether to continue
+  MDBS_LAUNCH(K_RESID0, grid_of(B, B.cells), kBlock, s, k_resid0, B.sd, B.cg, B.cells);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize, B.cg, B.cells, 0, 1, tol, max_it);
+  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_any, B.cg, B.ndom, B.any_flag, handle, use);
+  MDBS_LAUNCH(K_ZERO, grid_of(B, B.cells), kBlock, s, k_zero_if_b0, B.sd, B.cg, B.cells);
+  // one CG iteration, preconditioner first; the last kernels decide whether to continue
   auto body = [&](cudaStream_t bs) {
     if (!flexible) {
-      vcycle(ps->ld, ps->nlev, nu1, nu2, cs, (const double*)ps->cinv_d, bs);
+      vcycle<double>(B, nu1, nu2, cs, bs);
     } else {
-      const int g = grid_for(n);
-      MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_d2f, ps->r, ps->lf[0].b, n);
-      vcycle(ps->lf, ps->nlev, nu1, nu2, cs, (const float*)ps->cinv_f, bs);
-      MDBS_LAUNCH(K_CONVERT, g, kBlock, bs, k_copy_f2d, ps->lf[0].x, ps->z, n);
+      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_d2f, B.cg, B.cells);
+      vcycle<float>(B, nu1, nu2, cs, bs);
+      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells);
     }
-    MDBS_LAUNCH(K_DOTS, nb, kBlock, bs, k_dots_rz, n, ps->r, ps->z, ps->q, ps->partials, nb, flexible);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 3, flexible, tol, max_it,
-                handle, use);
-    MDBS_LAUNCH(K_UPDATE_D, nb, kBlock, bs, k_update_d, n, ps->scal, ps->z, ps->dv, flexible);
-    MDBS_LAUNCH(K_SPMV_DOT, nb, kBlock, bs, k_spmv_dot, P, F, ps->dv, ps->q, ps->partials);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 1, 0, tol, max_it, handle, use);
-    MDBS_LAUNCH(K_UPDATE_XR, nb, kBlock, bs, k_update_xr, n, ps->scal, x, ps->r, ps->dv, ps->q, ps->partials);
-    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_finalize, ps->partials, nb, ps->scal, 2, 0, tol, max_it, handle, use);
+    MDBS_LAUNCH(K_DOTS, grid_of(B, B.cells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.cells, flexible);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 3, flexible, tol, max_it);
+    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.cells), kBlock, bs, k_update_d, B.sd, B.cg, B.cells, flexible);
+    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.cells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.cells);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 1, 0, tol, max_it);
+    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.cells), kBlock, bs, k_update_xr, B.sd, B.cg, B.cells);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 2, 0, tol, max_it);
+    MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   };
   if (capture) {
     cudaStreamCaptureStatus st;
@@ -855,25 +962,25 @@ cudaError_t pressure_solve(PressureSolver* ps, const Prm& P, const Fld& F, doubl
     cudaGraph_t body_graph = prm.conditional.phGraph_out[0];
     e = cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies);
     if (e != cudaSuccess) return e;
-    e = cudaStreamBeginCaptureToGraph(ps->body_stream, body_graph, nullptr, nullptr, 0,
+    e = cudaStreamBeginCaptureToGraph(body_stream, body_graph, nullptr, nullptr, 0,
                                       cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return e;
     const long long c0 = launch_count();
-    body(ps->body_stream);
-    ps->body_launches = launch_count() - c0;
+    body(body_stream);
+    if (body_launches) *body_launches = launch_count() - c0;
     cudaGraph_t out = nullptr;
-    e = cudaStreamEndCapture(ps->body_stream, &out);
+    e = cudaStreamEndCapture(body_stream, &out);
     if (e != cudaSuccess) return e;
   } else {
     for (;;) {
-      cudaError_t e = cudaMemcpyAsync(ps->host_scal, ps->scal + kCond, sizeof(double), cudaMemcpyDeviceToHost, s);
+      cudaError_t e = cudaMemcpyAsync(host_flag, B.any_flag, sizeof(int), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
       if (e != cudaSuccess) return e;
-      if (ps->host_scal[0] == 0.0) break;
+      if (*(volatile int*)host_flag == 0) break;
       body(s);
     }
   }
-  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_record, ps->scal, step_scal, corr, tol);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_record, B.sd, B.cg, corr, tol);
   return cudaGetLastError();
 }
 

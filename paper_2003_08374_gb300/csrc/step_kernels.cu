@@ -67,27 +67,20 @@ __device__ __forceinline__ double warp_reduce_max(double v) {
   return v;
 }
 
-int grid_for(long long n, int cap = 1 << 30) {
-  long long b = (n + kBlock - 1) / kBlock;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (int)b;
-}
 
 // ------------------------------------------------------------------ saturation
 // Face fluxes of the saturation equation (Eq. 15): upwind (low-order) flux,
 // Van Leer high-order flux (section 3.1) plus the relative-velocity flux --
 // compression in solid-free faces (Eq. 22 oriented as Eq. 41) or the porous
 // phase-flux difference (Eq. 34 times a_l a_g).  AF = high - low order.
-__global__ void k_alpha_flux(Prm P, Fld F, double* __restrict__ partials) {
+// returns the boundary inflow of face t (0 for interior faces)
+__device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long long t) {
   double inflow = 0.0;
-  const long long total = total_faces(P);
-  const double inv_h = 1.0 / P.h;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+  const double inv_h = P.inv_h;
+  {
     int d, i, j, k;
     long long f;
-    decode_face(P, t, d, i, j, k, f);
+    if (!decode_face(P, t, d, i, j, k, f)) return 0.0;
     const double uf = F.u[d][f];
     const double Q = P.A * uf;
     const int cd = d == 0 ? i : (d == 1 ? j : k);
@@ -151,15 +144,24 @@ __global__ void k_alpha_flux(Prm P, Fld F, double* __restrict__ partials) {
       inflow += high ? -flo : flo;
     }
   }
-  double s = block_sum(inflow);
-  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  return inflow;
+}
+
+// one partial sum of the boundary inflow per block (deterministic)
+__global__ void k_alpha_flux(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const int lb = b - w.blk[dm];
+    const long long t = (long long)lb * blockDim.x + threadIdx.x;
+    const double v = t < total_faces(S.P) ? b_alpha_flux(S.P, S.F, t) : 0.0;
+    const double sum = block_sum(v);
+    if (threadIdx.x == 0) S.partials[lb] = sum;
+  }
 }
 
 // low-order (upwind) update
-__global__ void k_alpha_lo(Prm P, Fld F, const double* __restrict__ dtp) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
-  const double dt = *dtp;
+__device__ __forceinline__ void b_alpha_lo(const Prm& P, const Fld& F, long long c, double dt) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double div = 0.0;
@@ -175,10 +177,7 @@ __global__ void k_alpha_lo(Prm P, Fld F, const double* __restrict__ dtp) {
 // low-order solutions over the cell and its face neighbours (within [0, 1]) in
 // solid-free cells; [0, 1] in porous cells, where the relative flux is the
 // physical Darcy phase flux of Eq. 34.
-__global__ void k_alpha_limit(Prm P, Fld F, const double* __restrict__ dtp) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
-  const double dt = *dtp;
+__device__ __forceinline__ void b_alpha_limit(const Prm& P, const Fld& F, long long c, double dt) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   const double a0 = F.alpha[c], aLc = F.aL[c];
@@ -225,10 +224,7 @@ __device__ __forceinline__ double limited_af(const Prm& P, const Fld& F, int d, 
   return lam * a;
 }
 
-__global__ void k_alpha_update(Prm P, Fld F, const double* __restrict__ dtp) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
-  const double dt = *dtp;
+__device__ __forceinline__ void b_alpha_update(const Prm& P, const Fld& F, long long c, double dt) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double corr = 0.0;
@@ -240,20 +236,20 @@ __global__ void k_alpha_update(Prm P, Fld F, const double* __restrict__ dtp) {
   F.alpha[c] = F.aL[c] - dt / (F.phi[c] * P.V) * corr;
 }
 
-// deterministic final sum of nb partials: scal[slot] += dt * sum
-__global__ void k_finalize_sum(const double* __restrict__ partials, int nb, double* scal, int slot,
-                               const double* __restrict__ dtp) {
+// per domain (one block each): scal[slot] += dt * (deterministic sum of the domain's
+// partials, one per block of the space w)
+__global__ void k_finalize_inflow(const StepDom* __restrict__ D, Work w, int slot) {
+  const StepDom& S = D[blockIdx.x];
+  const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
   double v = 0.0;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += partials[b];
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += S.partials[b];
   v = block_sum(v);
-  if (threadIdx.x == 0) scal[slot] += *dtp * v;
+  if (threadIdx.x == 0) S.scal[slot] += S.scal[kSlotDt] * v;
 }
 
 // ------------------------------------------------------------------ closures
 // Appendix A closures, Eqs. 42 and 45 densities / drag, Eq. 38 coefficient.
-__global__ void k_properties(Prm P, Fld F) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
+__device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long long c) {
   F.rho_old[c] = F.rho[c];  // the density of the previous step feeds the Euler source (Eq. 46)
   const double a = F.alpha[c];
   F.mu[c] = a * P.mu_l + (1.0 - a) * P.mu_g;
@@ -308,9 +304,7 @@ __global__ void k_properties(Prm P, Fld F) {
 
 // interface normal toward the liquid (Eq. 24 with the orientation of Eq. 41)
 // and the contact-angle normal of Eq. 40 in free cells next to porous cells
-__global__ void k_normals(Prm P, Fld F) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
+__device__ __forceinline__ void b_normals(const Prm& P, const Fld& F, long long c) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double g[3] = {0.0, 0.0, 0.0};
@@ -336,9 +330,7 @@ __global__ void k_normals(Prm P, Fld F) {
 }
 
 // curvature kappa = -div(m) (Eq. 27 / 43)
-__global__ void k_curvature(Prm P, Fld F) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
+__device__ __forceinline__ void b_curvature(const Prm& P, const Fld& F, long long c) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double kap = 0.0;
@@ -351,8 +343,7 @@ __global__ void k_curvature(Prm P, Fld F) {
 // coefficients (implicit upwind convection of rho u u / phi^2 and viscous
 // diffusion), and rhs0 = Euler source + explicit transpose viscous stress +
 // body force (gravity rho g and capillary force F_c, Eqs. 38, 43, 45).
-__global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, long long t, double dt) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -388,7 +379,7 @@ __global__ void k_momentum_assemble(Prm P, Fld F, const double* __restrict__ dtp
   }
   F.B[d][f] = Bf;
   const double uf = F.u[d][f];
-  const double inv_phidt = 1.0 / (phif * *dtp);
+  const double inv_phidt = 1.0 / (phif * dt);
   const double inv_phi = 1.0 / phif;
   const double inv_h = P.inv_h;
   const double at = V * rhof * inv_phidt;
@@ -485,8 +476,7 @@ struct Faces3 {
 };
 
 // one Jacobi sweep of the momentum predictor (Eq. 50): out = (H(in) - V grad p^k)/a_P
-__global__ void k_jacobi(Prm P, Fld F, Faces3 in, Faces3 out) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_jacobi(const Prm& P, const Fld& F, long long t, Faces3 in, Faces3 out) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -500,17 +490,20 @@ __global__ void k_jacobi(Prm P, Fld F, Faces3 in, Faces3 out) {
   out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) * F.aP[d][f];  // V/h = A; aP = 1/a_P
 }
 
-__global__ void k_copy_faces(Prm P, Faces3 src, Faces3 dst) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int d, i, j, k;
-  long long f;
-  if (!decode_face(P, t, d, i, j, k, f)) return;
-  dst.a[d][f] = src.a[d][f];
+// utmp -> u (after an odd number of Jacobi sweeps)
+__global__ void k_copy_faces(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    int d, i, j, k;
+    long long f;
+    if (decode_face(S.P, t, d, i, j, k, f)) S.F.u[d][f] = S.F.utmp[d][f];
+  }
 }
 
 // HbyA = H(u)/a_P (Eq. 51 without the pressure gradient)
-__global__ void k_hbya(Prm P, Fld F) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_hbya(const Prm& P, const Fld& F, long long t) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -524,8 +517,7 @@ __global__ void k_hbya(Prm P, Fld F) {
 }
 
 // corrected velocity, Eq. 51
-__global__ void k_correct(Prm P, Fld F) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_correct(const Prm& P, const Fld& F, long long t) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -534,8 +526,7 @@ __global__ void k_correct(Prm P, Fld F) {
   F.u[d][f] = F.hbya[d][f] - (P.A * F.aP[d][f]) * face_dp(P, F.p, d, i, j, k);
 }
 
-__global__ void k_boundary_velocities(Prm P, Fld F) {
-  long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void b_boundary_velocities(const Prm& P, const Fld& F, long long t) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -547,110 +538,121 @@ __global__ void k_boundary_velocities(Prm P, Fld F) {
   F.u[d][f] = v;
 }
 
-// mass, alpha min / max and a non-finite sentinel over the cells
-__global__ void k_field_stats(Prm P, Fld F, double* __restrict__ partials, int nb) {
-  double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
-  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < P.cells;
-       c += (long long)gridDim.x * blockDim.x) {
-    const double a = F.alpha[c];
-    mass += F.phi[c] * a * P.V;
-    amin = fmin(amin, a);
-    amax = fmax(amax, a);
-    if (!isfinite(a) || !isfinite(F.p[c])) bad += 1.0;
-  }
-  mass = block_sum(mass);
-  if (threadIdx.x == 0) partials[blockIdx.x] = mass;
-  __syncthreads();
-  bad = block_sum(bad);
-  if (threadIdx.x == 0) partials[3 * nb + blockIdx.x] = bad;
-  // min / max through the max reduction
+// mass, alpha min / max and a non-finite sentinel: one partial per block in four
+// channels of the domain's partials (stride pcap)
+__global__ void k_field_stats(const StepDom* __restrict__ D, Work w) {
   __shared__ double smx[32], smn[32];
-  double vmx = warp_reduce_max(amax), vmn = -warp_reduce_max(-amin);
-  if ((threadIdx.x & 31) == 0) {
-    smx[threadIdx.x >> 5] = vmx;
-    smn[threadIdx.x >> 5] = vmn;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = -INFINITY, b = INFINITY;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
-      a = fmax(a, smx[w]);
-      b = fmin(b, smn[w]);
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const int lb = b - w.blk[dm];
+    const long long c = (long long)lb * blockDim.x + threadIdx.x;
+    double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
+    if (c < S.P.cells) {
+      const double a = S.F.alpha[c];
+      mass = S.F.phi[c] * a * S.P.V;
+      amin = a;
+      amax = a;
+      if (!isfinite(a) || !isfinite(S.F.p[c])) bad = 1.0;
     }
-    partials[nb + blockIdx.x] = b;
-    partials[2 * nb + blockIdx.x] = a;
+    const long long pc = S.pcap;
+    mass = block_sum(mass);
+    if (threadIdx.x == 0) S.partials[lb] = mass;
+    bad = block_sum(bad);
+    if (threadIdx.x == 0) S.partials[3 * pc + lb] = bad;
+    double vmx = warp_reduce_max(amax), vmn = -warp_reduce_max(-amin);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) {
+      smx[threadIdx.x >> 5] = vmx;
+      smn[threadIdx.x >> 5] = vmn;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = -INFINITY, bb = INFINITY;
+      for (int q = 0; q < (int)(blockDim.x >> 5); q++) {
+        a = fmax(a, smx[q]);
+        bb = fmin(bb, smn[q]);
+      }
+      S.partials[pc + lb] = bb;
+      S.partials[2 * pc + lb] = a;
+    }
   }
 }
 
-__global__ void k_finalize_stats(const double* __restrict__ partials, int nb, double* scal) {
+// per domain (one block each): fold the partials of the cells space into the scalars
+__global__ void k_finalize_stats(const StepDom* __restrict__ D, Work w) {
   if (threadIdx.x != 0) return;
+  const StepDom& S = D[blockIdx.x];
+  const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
+  const long long pc = S.pcap;
   double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
   for (int b = 0; b < nb; b++) {
-    mass += partials[b];
-    amin = fmin(amin, partials[nb + b]);
-    amax = fmax(amax, partials[2 * nb + b]);
-    bad += partials[3 * nb + b];
+    mass += S.partials[b];
+    amin = fmin(amin, S.partials[pc + b]);
+    amax = fmax(amax, S.partials[2 * pc + b]);
+    bad += S.partials[3 * pc + b];
   }
-  scal[0] = mass;
-  scal[1] = amin;
-  scal[2] = amax;
-  scal[3] = bad;
+  S.scal[kSlotMass] = mass;
+  S.scal[kSlotAmin] = amin;
+  S.scal[kSlotAmax] = amax;
+  S.scal[kSlotBad] = bad;
 }
 
-// max over faces of |u_f| / phi_f (CFL time step, section 3.2)
-__global__ void k_cfl(Prm P, Fld F, double* __restrict__ partials) {
-  double vmax = 0.0;
-  const long long total = total_faces(P);
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
+// max over faces of |u_f| / phi_f (CFL time step, section 3.2), one partial per block
+__global__ void k_cfl(const StepDom* __restrict__ D, Work w) {
+  __shared__ double sm[32];
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const int lb = b - w.blk[dm];
+    const long long t = (long long)lb * blockDim.x + threadIdx.x;
+    double vmax = 0.0;
     int d, i, j, k;
     long long f;
-    decode_face(P, t, d, i, j, k, f);
-    const double phif = 0.5 * (ghost_read(F.phi, P.n, i - (d == 0), j - (d == 1), k - (d == 2)) +
-                               ghost_read(F.phi, P.n, i, j, k));
-    vmax = fmax(vmax, fabs(F.u[d][f]) / phif);
-  }
-  __shared__ double sm[32];
-  vmax = warp_reduce_max(vmax);
-  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = vmax;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); w++) a = fmax(a, sm[w]);
-    partials[blockIdx.x] = a;
+    if (decode_face(S.P, t, d, i, j, k, f)) {
+      const double phif = 0.5 * (ghost_read(S.F.phi, S.P.n, i - (d == 0), j - (d == 1), k - (d == 2)) +
+                                 ghost_read(S.F.phi, S.P.n, i, j, k));
+      vmax = fabs(S.F.u[d][f]) / phif;
+    }
+    vmax = warp_reduce_max(vmax);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = vmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double a = 0.0;
+      for (int q = 0; q < (int)(blockDim.x >> 5); q++) a = fmax(a, sm[q]);
+      S.partials[lb] = a;
+    }
   }
 }
 
-// CFL time step (section 3.2): time += dt; dt = min(cfl h / max|u/phi|, 1.2 dt, dt_max)
-__global__ void k_finalize_cfl(const double* __restrict__ partials, int nb, double* scal, double cfl, double h,
-                               double dt_max) {
+// per domain: time += dt; with cfl > 0 the next dt = min(cfl h / max|u/phi|, 1.2 dt, dt_max)
+__global__ void k_finalize_time(const StepDom* __restrict__ D, Work w) {
   if (threadIdx.x != 0) return;
-  double a = 0.0;
-  for (int b = 0; b < nb; b++) a = fmax(a, partials[b]);
+  const StepDom& S = D[blockIdx.x];
+  double* scal = S.scal;
   const double dt = scal[kSlotDt];
-  scal[kSlotUmax] = a;
   scal[kSlotTime] += dt;
-  double dtn = a > 0.0 ? cfl * h / a : dt_max;
+  if (!(S.P.cfl > 0.0)) return;
+  const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
+  double a = 0.0;
+  for (int b = 0; b < nb; b++) a = fmax(a, S.partials[b]);
+  scal[kSlotUmax] = a;
+  double dtn = a > 0.0 ? S.P.cfl * S.P.h / a : S.P.dt_max;
   dtn = fmin(dtn, 1.2 * dt);
-  dtn = fmin(dtn, dt_max);
+  dtn = fmin(dtn, S.P.dt_max);
   scal[kSlotDt] = dtn;
-}
-
-__global__ void k_advance_time(double* scal) {
-  if (threadIdx.x == 0) scal[kSlotTime] += scal[kSlotDt];
 }
 
 // static geometry: solid-free flag (porosity exactly 1) and, in free cells with a
 // porous face neighbour, the wall normal n_w = -grad(phi)/|grad(phi)| pointing
 // into the porous side (used by the contact-angle normal of Eq. 40)
-__global__ void k_static_geometry(Prm P, const double* __restrict__ phi, uint8_t* __restrict__ is_free,
-                                  double* __restrict__ nwx, double* __restrict__ nwy, double* __restrict__ nwz) {
-  long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (c >= P.cells) return;
+__device__ __forceinline__ void b_static_geometry(const Prm& P, const Fld& F, long long c) {
+  const double* __restrict__ phi = F.phi;
   int i, j, k;
   decode_cell(P, c, i, j, k);
   const bool fr = phi[c] == 1.0;
-  is_free[c] = fr ? 1 : 0;
+  const_cast<uint8_t*>(F.is_free)[c] = fr ? 1 : 0;
   double n[3] = {0.0, 0.0, 0.0};
   if (fr) {
     bool touch = false;
@@ -668,83 +670,170 @@ __global__ void k_static_geometry(Prm P, const double* __restrict__ phi, uint8_t
         for (int e = 0; e < 3; e++) n[e] = -g[e] / mag;
     }
   }
-  nwx[c] = n[0];
-  nwy[c] = n[1];
-  nwz[c] = n[2];
+  for (int e = 0; e < 3; e++) const_cast<double*>(F.nw[e])[c] = n[e];
+}
+
+__global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_static_geometry(S.P, S.F, c);
+  }
+}
+
+// ------------------------------------------------------------------ batched entry points
+__global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_alpha_lo(S.P, S.F, c, S.scal[kSlotDt]);
+  }
+}
+
+__global__ void k_alpha_limit(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_alpha_limit(S.P, S.F, c, S.scal[kSlotDt]);
+  }
+}
+
+__global__ void k_alpha_update(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_alpha_update(S.P, S.F, c, S.scal[kSlotDt]);
+  }
+}
+
+__global__ void k_properties(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_properties(S.P, S.F, c);
+  }
+}
+
+__global__ void k_normals(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_normals(S.P, S.F, c);
+  }
+}
+
+__global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (c < S.P.cells) b_curvature(S.P, S.F, c);
+  }
+}
+
+__global__ void k_momentum_assemble(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (t < total_faces(S.P)) b_momentum_assemble(S.P, S.F, t, S.scal[kSlotDt]);
+  }
+}
+
+__global__ void k_jacobi(const StepDom* __restrict__ D, Work w, int parity) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    Faces3 a{{S.F.u[0], S.F.u[1], S.F.u[2]}}, c{{S.F.utmp[0], S.F.utmp[1], S.F.utmp[2]}};
+    if (parity)
+      b_jacobi(S.P, S.F, t, c, a);
+    else
+      b_jacobi(S.P, S.F, t, a, c);
+  }
+}
+
+__global__ void k_hbya(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (t < total_faces(S.P)) b_hbya(S.P, S.F, t);
+  }
+}
+
+__global__ void k_correct(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (t < total_faces(S.P)) b_correct(S.P, S.F, t);
+  }
+}
+
+__global__ void k_boundary_velocities(const StepDom* __restrict__ D, Work w) {
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    if (t < total_faces(S.P)) b_boundary_velocities(S.P, S.F, t);
+  }
 }
 
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
-static long long faces_total_host(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P.nf[2] : 0); }
+#define BATCH_LAUNCH(ID, SPACE, KERNEL, ...) \
+  MDBS_LAUNCH(ID, grid_of(B, B.SPACE), kBlock, s, KERNEL, B.sd, B.SPACE, ##__VA_ARGS__)
 
-void launch_alpha_step(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
-  const double* dtp = scal + kSlotDt;
-  const int gf = grid_for(faces_total_host(P), kMaxPartials);
-  MDBS_LAUNCH(K_ALPHA_FLUX, gf, kBlock, s, k_alpha_flux, P, F, partials);
-  MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_finalize_sum, partials, gf, scal, kSlotInflow, dtp);
-  const int gc = grid_for(P.cells);
-  MDBS_LAUNCH(K_ALPHA_LO, gc, kBlock, s, k_alpha_lo, P, F, dtp);
-  MDBS_LAUNCH(K_ALPHA_LIMIT, gc, kBlock, s, k_alpha_limit, P, F, dtp);
-  MDBS_LAUNCH(K_ALPHA_UPDATE, gc, kBlock, s, k_alpha_update, P, F, dtp);
+void launch_alpha_step(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_ALPHA_FLUX, faces, k_alpha_flux);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_inflow, B.sd, B.faces, kSlotInflow);
+  BATCH_LAUNCH(K_ALPHA_LO, cells, k_alpha_lo);
+  BATCH_LAUNCH(K_ALPHA_LIMIT, cells, k_alpha_limit);
+  BATCH_LAUNCH(K_ALPHA_UPDATE, cells, k_alpha_update);
 }
 
-void launch_properties(const Prm& P, const Fld& F, cudaStream_t s) {
-  const int gc = grid_for(P.cells);
-  MDBS_LAUNCH(K_PROPERTIES, gc, kBlock, s, k_properties, P, F);
-  MDBS_LAUNCH(K_NORMALS, gc, kBlock, s, k_normals, P, F);
-  MDBS_LAUNCH(K_CURVATURE, gc, kBlock, s, k_curvature, P, F);
+void launch_properties(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_PROPERTIES, cells, k_properties);
+  BATCH_LAUNCH(K_NORMALS, cells, k_normals);
+  BATCH_LAUNCH(K_CURVATURE, cells, k_curvature);
 }
 
-void launch_momentum_assemble(const Prm& P, const Fld& F, const double* scal, cudaStream_t s) {
-  MDBS_LAUNCH(K_MOM_ASSEMBLE, grid_for(faces_total_host(P)), kBlock, s, k_momentum_assemble, P, F,
-              scal + kSlotDt);
+void launch_momentum_assemble(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_MOM_ASSEMBLE, faces, k_momentum_assemble);
 }
 
-void launch_jacobi_sweeps(const Prm& P, const Fld& F, int sweeps, cudaStream_t s) {
-  Faces3 a{{F.u[0], F.u[1], F.u[2]}}, b{{F.utmp[0], F.utmp[1], F.utmp[2]}};
-  const int g = grid_for(faces_total_host(P));
-  for (int it = 0; it < sweeps; it++) {
-    MDBS_LAUNCH(K_JACOBI, g, kBlock, s, k_jacobi, P, F, a, b);
-    Faces3 t = a;
-    a = b;
-    b = t;
-  }
+void launch_jacobi_sweeps(const BatchPlan& B, int sweeps, cudaStream_t s) {
+  for (int it = 0; it < sweeps; it++) BATCH_LAUNCH(K_JACOBI, faces, k_jacobi, it & 1);
   // an odd sweep count leaves the result in the scratch buffers
-  if (sweeps & 1) MDBS_LAUNCH(K_JACOBI, g, kBlock, s, k_copy_faces, P, a, b);
+  if (sweeps & 1) BATCH_LAUNCH(K_JACOBI, faces, k_copy_faces);
 }
 
-void launch_hbya(const Prm& P, const Fld& F, cudaStream_t s) {
-  MDBS_LAUNCH(K_HBYA, grid_for(faces_total_host(P)), kBlock, s, k_hbya, P, F);
+void launch_hbya(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_HBYA, faces, k_hbya); }
+
+void launch_correct(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_CORRECT, faces, k_correct); }
+
+void launch_set_boundary_velocities(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_BOUNDARY, faces, k_boundary_velocities);
 }
 
-void launch_correct(const Prm& P, const Fld& F, cudaStream_t s) {
-  MDBS_LAUNCH(K_CORRECT, grid_for(faces_total_host(P)), kBlock, s, k_correct, P, F);
+void launch_field_stats(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_STATS, cells, k_field_stats);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_stats, B.sd, B.cells);
 }
 
-void launch_set_boundary_velocities(const Prm& P, const Fld& F, cudaStream_t s) {
-  MDBS_LAUNCH(K_BOUNDARY, grid_for(faces_total_host(P)), kBlock, s, k_boundary_velocities, P, F);
+void launch_time_advance(const BatchPlan& B, cudaStream_t s) {
+  if (B.any_cfl) BATCH_LAUNCH(K_CFL, faces, k_cfl);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_time, B.sd, B.faces);
 }
 
-void launch_field_stats(const Prm& P, const Fld& F, double* partials, double* scal, cudaStream_t s) {
-  const int nb = grid_for(P.cells, 512);
-  MDBS_LAUNCH(K_STATS, nb, kBlock, s, k_field_stats, P, F, partials, nb);
-  MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_stats, partials, nb, scal);
-}
-
-void launch_time_advance(const Prm& P, const Fld& F, double cfl, double dt_max, double* partials, double* scal,
-                         cudaStream_t s) {
-  if (cfl > 0.0) {
-    const int nb = grid_for(faces_total_host(P), 512);
-    MDBS_LAUNCH(K_CFL, nb, kBlock, s, k_cfl, P, F, partials);
-    MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_finalize_cfl, partials, nb, scal, cfl, P.h, dt_max);
-  } else {
-    MDBS_LAUNCH(K_FINALIZE, 1, 32, s, k_advance_time, scal);
-  }
-}
-
-void launch_static_geometry(const Prm& P, const double* phi, uint8_t* is_free, double* nw[3], cudaStream_t s) {
-  MDBS_LAUNCH(K_STATIC, grid_for(P.cells), kBlock, s, k_static_geometry, P, phi, is_free, nw[0], nw[1], nw[2]);
-}
+void launch_static_geometry(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_STATIC, cells, k_static_geometry); }
 
 }  // namespace mdbs

@@ -80,6 +80,12 @@ def lib():
         L.mdbs_profile_count.restype = C.c_int32
         L.mdbs_profile_read.argtypes = [C.c_void_p, C.c_int32, C.POINTER(C.c_char_p), _D,
                                         C.POINTER(C.c_int64)]
+        L.mdbs_batch_create.argtypes = [C.POINTER(C.c_void_p), C.c_int32, C.POINTER(C.c_void_p)]
+        L.mdbs_batch_step.argtypes = [C.c_void_p, C.c_int32]
+        L.mdbs_batch_set_stream.argtypes = [C.c_void_p, C.c_void_p]
+        L.mdbs_batch_last_error.argtypes = [C.c_void_p]
+        L.mdbs_batch_last_error.restype = C.c_char_p
+        L.mdbs_batch_destroy.argtypes = [C.c_void_p]
         L.mdbs_field_stats_static.argtypes = [C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p]
         L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
@@ -212,6 +218,39 @@ class Simulation:
     def close(self):
         if getattr(self, "h", None):
             lib().mdbs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Member simulations advanced together, one launch per step phase (mdbs_batch_*)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value if isinstance(s.h, C.c_void_p) else s.h
+                                              for s in self.sims])
+        h = C.c_void_p()
+        rc = lib().mdbs_batch_create(arr, len(self.sims), C.byref(h))
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_batch_last_error(None).decode())
+        self.h = h
+
+    def step(self, n=1):
+        rc = lib().mdbs_batch_step(self.h, int(n))
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_batch_last_error(self.h).decode())
+
+    def set_stream(self, stream_handle: int):
+        lib().mdbs_batch_set_stream(self.h, C.c_void_p(stream_handle))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().mdbs_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):
