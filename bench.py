@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
+    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched"])
+    ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
+    ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
     return ap.parse_args()
 
 
@@ -369,10 +372,52 @@ def gpu_arm(args):
     return 0
 
 
+def batched_arm(args):
+    """Many uneven independent domains advanced as one batch (one launch per step phase,
+    one CUDA graph per step): sides log-uniform in [32, 96] (3-D) or [64, 256] (2-D)."""
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2003_08374_gb300.build import build_library
+    build_library()
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    cases = W.batched_domains(count=args.domains, seed=4, p_tol=1e-8, max_cg=200, precision=args.precision)
+    cells = sum(c.cells for c in cases)
+    stream = torch.cuda.current_stream()
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims)
+    b.set_stream(stream.cuda_stream)
+    for _ in range(args.warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local) as clk:
+        e0.record(stream)
+        for _ in range(args.steps):
+            b.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    iters = [s.stats()["cg_iters"] for s in sims]
+    line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "batched_%d_domains" % len(cases), "cells": cells,
+                       "precision": "fp64" if args.precision == 0 else "mixed",
+                       "cg_iters_max": max(max(i) for i in iters), "cg_iters_mean": float(np.mean(iters))},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    b.close()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
+    if args.workload == "batched":
+        return batched_arm(args)
     return gpu_arm(args)
 
 

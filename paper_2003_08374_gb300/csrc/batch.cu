@@ -10,7 +10,7 @@ namespace mdbs {
 
 namespace {
 
-long long blocks_of(long long n) { return (n + kBlock - 1) / kBlock; }
+long long items_of(long long n, int rep) { return (n + (long long)kBlock * rep - 1) / ((long long)kBlock * rep); }
 
 long long faces_total(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P.nf[2] : 0); }
 
@@ -23,9 +23,11 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  B.grid_cap = sms * (2048 / kBlock);  // one wave of fully resident blocks
+  // grids cover every work item (one item per block) up to 64 waves of resident
+  // blocks; larger spaces loop (grid stride)
+  B.grid_cap = sms * (2048 / kBlock) * 64;
   // host block tables: spaces in a fixed order, each ndom + 1 prefix entries
-  const int nspace = 3 + 4 * kMaxLevels;
+  const int nspace = 5 + 4 * kMaxLevels;
   std::vector<int> tab((size_t)nspace * (ndom + 1), 0);
   auto fill = [&](int space, auto count) -> int {
     int* t = &tab[(size_t)space * (ndom + 1)];
@@ -37,10 +39,19 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     t[ndom] = (int)acc;
     return (int)acc;
   };
-  int totals[3 + 4 * kMaxLevels];
-  totals[0] = fill(0, [&](int d) { return blocks_of(sd[d].P.cells); });
-  totals[1] = fill(1, [&](int d) { return blocks_of(faces_total(sd[d].P)); });
+  int totals[5 + 4 * kMaxLevels];
+  // one row of kBlock elements per item, except the reduction spaces (kRepBig rows:
+  // fewer block reductions and partials)
+  int reps[5 + 4 * kMaxLevels];
+  for (int q = 0; q < 5 + 4 * kMaxLevels; q++) reps[q] = 1;
+  reps[3] = reps[4] = kRepBig;
+  reps[5 + kMaxLevels] = kRepBig;  // finest-level red/black half sweeps
+  auto blocks_of = [&](long long n, int space) { return items_of(n, reps[space]); };
+  totals[0] = fill(0, [&](int d) { return blocks_of(sd[d].P.cells, 0); });
+  totals[1] = fill(1, [&](int d) { return blocks_of(faces_total(sd[d].P), 1); });
   totals[2] = fill(2, [&](int) { return 1LL; });
+  totals[3] = fill(3, [&](int d) { return blocks_of(sd[d].P.cells, 3); });
+  totals[4] = fill(4, [&](int d) { return blocks_of(faces_total(sd[d].P), 4); });
   B.max_first = 0;
   B.max_levels = 0;
   B.any_cfl = 0;
@@ -54,16 +65,15 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
       const Level<double>& L = cg[d].ld[lev];
       return (long long)L.n[0] * L.n[1] * L.n[2];
     };
-    totals[3 + l] = fill(3 + l, [&](int d) { return l < cg[d].nlev ? blocks_of(cells_at(d, l)) : 0LL; });
-    totals[3 + kMaxLevels + l] = fill(3 + kMaxLevels + l, [&](int d) -> long long {
+    const int s0 = 5 + l, s1 = 5 + kMaxLevels + l, s2 = 5 + 2 * kMaxLevels + l, s3 = 5 + 3 * kMaxLevels + l;
+    totals[s0] = fill(s0, [&](int d) { return l < cg[d].nlev ? blocks_of(cells_at(d, l), s0) : 0LL; });
+    totals[s1] = fill(s1, [&](int d) -> long long {
       if (l >= cg[d].first) return 0;
       const Level<double>& L = cg[d].ld[l];
-      return blocks_of((long long)((L.n[0] + 1) / 2) * L.n[1] * L.n[2]);
+      return blocks_of((long long)((L.n[0] + 1) / 2) * L.n[1] * L.n[2], s1);
     });
-    totals[3 + 2 * kMaxLevels + l] =
-        fill(3 + 2 * kMaxLevels + l, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l)) : 0LL; });
-    totals[3 + 3 * kMaxLevels + l] =
-        fill(3 + 3 * kMaxLevels + l, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l + 1)) : 0LL; });
+    totals[s2] = fill(s2, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l), s2) : 0LL; });
+    totals[s3] = fill(s3, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l + 1), s3) : 0LL; });
   }
   cudaError_t e = cudaMalloc(&B.table_storage, tab.size() * sizeof(int));
   if (e != cudaSuccess) return e;
@@ -82,16 +92,19 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     w.blk = B.table_storage + (size_t)space * (ndom + 1);
     w.ndom = ndom;
     w.total = totals[space];
+    w.rep = reps[space];
     return w;
   };
   B.cells = work(0);
   B.faces = work(1);
   B.dom = work(2);
+  B.rcells = work(3);
+  B.rfaces = work(4);
   for (int l = 0; l < kMaxLevels; l++) {
-    B.lcells[l] = work(3 + l);
-    B.lhalf[l] = work(3 + kMaxLevels + l);
-    B.lfine[l] = work(3 + 2 * kMaxLevels + l);
-    B.lcoarse[l] = work(3 + 3 * kMaxLevels + l);
+    B.lcells[l] = work(5 + l);
+    B.lhalf[l] = work(5 + kMaxLevels + l);
+    B.lfine[l] = work(5 + 2 * kMaxLevels + l);
+    B.lcoarse[l] = work(5 + 3 * kMaxLevels + l);
   }
   *out = B;
   return cudaSuccess;

@@ -222,7 +222,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
     F.utmp[d] = fd();
   }
   const long long faces = L.nf[0] + L.nf[1] + (L.dim == 3 ? L.nf[2] : 0);
-  const long long pcap = (std::max(L.cells, faces) + kBlock - 1) / kBlock;
+  const long long pcap = (std::max(L.cells, faces) + kBlock * kRepBig - 1) / (kBlock * kRepBig);
   double* partials = (double*)take(4 * pcap * 8);
   double* scal = (double*)take(kNumSlots * 8);
   if (s) {

@@ -16,6 +16,7 @@ namespace mdbs {
 constexpr int kWall = 0, kInlet = 1, kOutlet = 2;
 constexpr int kMaxLevels = 16;
 constexpr int kBlock = 256;
+constexpr int kRepBig = 8;  // rows of kBlock per work item in the cell and face spaces
 
 // slots of the per-domain device scalar array
 constexpr int kSlotMass = 0, kSlotAmin = 1, kSlotAmax = 2, kSlotBad = 3, kSlotUmax = 4, kSlotInflow = 5,
@@ -78,9 +79,10 @@ struct Level {
 
 // ---------------------------------------------------------------- batches
 struct Work {
-  const int* blk;  // device table, ndom + 1 entries: first block of each domain, then the total
+  const int* blk;  // device table, ndom + 1 entries: first item of each domain, then the total
   int ndom;
-  int total;
+  int total;       // work items; item i of a domain covers elements [i*rep*blockDim, (i+1)*rep*blockDim)
+  int rep;         // blockDim-sized rows per work item
 };
 
 // domain owning flat block b: the largest d with blk[d] <= b (empty domains are skipped)
@@ -102,7 +104,7 @@ struct StepDom {
   Fld F;
   double* scal;      // step scalars (kSlot*)
   double* partials;  // reduction partials: 4 channels of pcap values
-  long long pcap;    // partials per channel (>= blocks of the largest space)
+  long long pcap;    // partials per channel (>= work items of the largest space)
 };
 
 // per-domain view of the pressure solver
@@ -184,7 +186,8 @@ long long launch_count();  // kernels launched so far by the active simulation
 struct BatchPlan {
   int ndom;
   int grid_cap;               // persistent grid: SMs x resident blocks
-  Work cells, faces, dom;     // per-domain cells, faces, one block per domain
+  Work cells, faces, dom;     // per-domain cells, faces (one row per item), one block per domain
+  Work rcells, rfaces;        // the same with kRepBig rows per item: kernels with block reductions
   Work lcells[kMaxLevels];    // level-l cells of domains that have level l
   Work lhalf[kMaxLevels];     // level-l red/black half cells of domains whose level l precedes the tail
   Work lfine[kMaxLevels];     // level-l cells of the same domains (prolongation)

@@ -75,8 +75,10 @@ __device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long
 __global__ void k_assemble(const StepDom* __restrict__ D, Work w) {
   FOR_WORK(w)
     const StepDom& S = D[dm];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_assemble(S.P, S.F, c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_assemble(S.P, S.F, c);
+    }
   }
 }
 
@@ -105,8 +107,10 @@ template <typename R>
 __global__ void k_diag(const CgDom* __restrict__ C, Work w, int l) {
   FOR_WORK(w)
     const Level<R>& L = levels_of<R>(C[dm])[l];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < L.cells) b_diag(L, c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < L.cells) b_diag(L, c);
+    }
   }
 }
 
@@ -115,13 +119,15 @@ __global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
   FOR_WORK(w)
     const Level<double>& Ld = C[dm].ld[0];
     const Level<float>& Lf = C[dm].lf[0];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < Ld.cells) {
-      for (int a = 0; a < 3; a++) Lf.T[a][c] = (float)Ld.T[a][c];
-      Lf.Dd[c] = (float)Ld.Dd[c];
-      const float dg = (float)Ld.diag[c];
-      Lf.diag[c] = dg;
-      Lf.dinv[c] = 1.0f / dg;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < Ld.cells) {
+        for (int a = 0; a < 3; a++) Lf.T[a][c] = (float)Ld.T[a][c];
+        Lf.Dd[c] = (float)Ld.Dd[c];
+        const float dg = (float)Ld.diag[c];
+        Lf.diag[c] = dg;
+        Lf.dinv[c] = 1.0f / dg;
+      }
     }
   }
 }
@@ -180,8 +186,10 @@ template <typename R>
 __global__ void k_coarsen(const CgDom* __restrict__ C, Work w, int l) {
   FOR_WORK(w)
     const Level<R>* L = levels_of<R>(C[dm]);
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < L[l].cells) b_coarsen(L[l - 1], L[l], c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < L[l].cells) b_coarsen(L[l - 1], L[l], c);
+    }
   }
 }
 
@@ -220,13 +228,50 @@ __device__ __forceinline__ void b_smooth(const Level<R>& L, int col, int zero, u
   L.x[c] = v * L.dinv[c];
 }
 
-// skips domains whose CG has converged (the V-cycle only runs inside CG iterations)
-template <typename R>
+// Skips domains whose CG has converged (the V-cycle only runs inside CG
+// iterations).  The level's arrays go to restrict-qualified registers once per
+// work item so that the REP rows of an item overlap their loads: the colour being
+// written and the colour being read are disjoint cells of the same array.
+template <typename R, int REP>
 __global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero) {
   FOR_WORK(w)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
-    b_smooth(levels_of<R>(G)[l], col, zero, (unsigned)lb * blockDim.x + threadIdx.x);
+    const Level<R>& Lr = levels_of<R>(G)[l];
+    const int n0 = Lr.n[0], n1 = Lr.n[1], n2 = Lr.n[2];
+    const R* __restrict__ bb = Lr.b;
+    const R* __restrict__ dinv = Lr.dinv;
+    const R* __restrict__ xr = Lr.x;
+    R* __restrict__ xw = Lr.x;
+    const R* __restrict__ Tx = Lr.T[0];
+    const R* __restrict__ Ty = Lr.T[1];
+    const R* __restrict__ Tz = Lr.T[2];
+    const unsigned half = (n0 + 1) >> 1;
+    const unsigned total = half * (unsigned)n1 * (unsigned)n2;
+    const long long sy = n0, sz = (long long)n0 * n1;
+#pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
+      if (t >= total) continue;
+      const int ti = (int)(t % half);
+      const unsigned row = t / half;
+      const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
+      const int i = ((j + k + col) & 1) + 2 * ti;
+      if (i >= n0) continue;
+      const long long c = i + (long long)n0 * row;
+      if (zero) {
+        xw[c] = bb[c] * dinv[c];
+        continue;
+      }
+      R v = bb[c];
+      if (i > 0) v += Tx[c - 1] * xr[c - 1];
+      if (i + 1 < n0) v += Tx[c] * xr[c + 1];
+      if (j > 0) v += Ty[c - sy] * xr[c - sy];
+      if (j + 1 < n1) v += Ty[c] * xr[c + sy];
+      if (k > 0) v += Tz[c - sz] * xr[c - sz];
+      if (k + 1 < n2) v += Tz[c] * xr[c + sz];
+      xw[c] = v * dinv[c];
+    }
   }
 }
 
@@ -236,8 +281,10 @@ __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l) {
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>& L = levels_of<R>(G)[l];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < L.cells) L.x[c] = R(0);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < L.cells) L.x[c] = R(0);
+    }
   }
 }
 
@@ -269,8 +316,10 @@ __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l) {
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>* L = levels_of<R>(G);
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < L[l + 1].cells) b_resid_restrict(L[l], L[l + 1], c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < L[l + 1].cells) b_resid_restrict(L[l], L[l + 1], c);
+    }
   }
 }
 
@@ -289,8 +338,10 @@ __global__ void k_prolong(const CgDom* __restrict__ C, Work w, int l) {
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>* L = levels_of<R>(G);
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < L[l].cells) b_prolong(L[l], L[l + 1], c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < L[l].cells) b_prolong(L[l], L[l + 1], c);
+    }
   }
 }
 
@@ -488,16 +539,18 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
   FOR_WORK(w)
     const StepDom& S = D[dm];
     const CgDom& G = C[dm];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
     double rr = 0.0, bb = 0.0;
-    if (c < S.P.cells) {
-      int q[3];
-      decode3(S.P.n, c, q[0], q[1], q[2]);
-      const double bc = S.F.b[c];
-      const double rc = bc - apply_A0(S.F, S.P, S.F.p, c, q);
-      G.r[c] = rc;
-      rr = rc * rc;
-      bb = bc * bc;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) {
+        int q[3];
+        decode3(S.P.n, c, q[0], q[1], q[2]);
+        const double bc = S.F.b[c];
+        const double rc = bc - apply_A0(S.F, S.P, S.F.p, c, q);
+        G.r[c] = rc;
+        rr += rc * rc;
+        bb += bc * bc;
+      }
     }
     rr = block_sum(rr);
     if (threadIdx.x == 0) G.partials[lb] = rr;
@@ -512,14 +565,31 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const StepDom& S = D[dm];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
     double s = 0.0;
-    if (c < S.P.cells) {
-      int q[3];
-      decode3(S.P.n, c, q[0], q[1], q[2]);
-      const double v = apply_A0(S.F, S.P, G.dv, c, q);
-      G.q[c] = v;
-      s = G.dv[c] * v;
+    const int n0 = S.P.n[0], n1 = S.P.n[1], n2 = S.P.n[2];
+    const long long n = S.P.cells, sy = n0, sz = (long long)n0 * n1;
+    const double* __restrict__ dv = G.dv;
+    double* __restrict__ qv = G.q;
+    const double* __restrict__ dg = S.F.diag;
+    const double* __restrict__ Tx = S.F.T[0];
+    const double* __restrict__ Ty = S.F.T[1];
+    const double* __restrict__ Tz = S.F.T[2];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < n) {
+        int i, j, k;
+        decode3(S.P.n, c, i, j, k);
+        const double dc = dv[c];
+        double v = dg[c] * dc;
+        if (i > 0) v -= Tx[c - 1] * dv[c - 1];
+        if (i + 1 < n0) v -= Tx[c] * dv[c + 1];
+        if (j > 0) v -= Ty[c - sy] * dv[c - sy];
+        if (j + 1 < n1) v -= Ty[c] * dv[c + sy];
+        if (k > 0) v -= Tz[c - sz] * dv[c - sz];
+        if (k + 1 < n2) v -= Tz[c] * dv[c + sz];
+        qv[c] = v;
+        s += dc * v;
+      }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) G.partials[lb] = s;
@@ -533,13 +603,20 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
     if (G.scal[kCond] == 0.0) continue;
     const StepDom& S = D[dm];
     const double al = G.scal[kAlpha];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
     double s = 0.0;
-    if (c < S.P.cells) {
-      S.F.p[c] += al * G.dv[c];
-      const double rc = G.r[c] - al * G.q[c];
-      G.r[c] = rc;
-      s = rc * rc;
+    const long long n = S.P.cells;
+    double* __restrict__ p = S.F.p;
+    double* __restrict__ rv = G.r;
+    const double* __restrict__ dv = G.dv;
+    const double* __restrict__ qv = G.q;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < n) {
+        p[c] += al * dv[c];
+        const double rc = rv[c] - al * qv[c];
+        rv[c] = rc;
+        s += rc * rc;
+      }
     }
     s = block_sum(s);
     if (threadIdx.x == 0) G.partials[lb] = s;
@@ -551,11 +628,17 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
   FOR_WORK(w)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
     double rz = 0.0, zq = 0.0;
-    if (c < D[dm].P.cells) {
-      rz = G.r[c] * G.z[c];
-      if (with_zq) zq = G.z[c] * G.q[c];
+    const long long n = D[dm].P.cells;
+    const double* __restrict__ rv = G.r;
+    const double* __restrict__ z = G.z;
+    const double* __restrict__ qv = G.q;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < n) {
+        rz += rv[c] * z[c];
+        if (with_zq) zq += z[c] * qv[c];
+      }
     }
     rz = block_sum(rz);
     if (threadIdx.x == 0) G.partials[lb] = rz;
@@ -575,8 +658,13 @@ __global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restric
     const bool first = scal[kIt] == 0.0;
     double be = 0.0;
     if (!first) be = flexible ? -scal[kAlpha] * scal[kZQ] / scal[kRZold] : scal[kRZ] / scal[kRZold];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < D[dm].P.cells) G.dv[c] = first ? G.z[c] : G.z[c] + be * G.dv[c];
+    const long long n = D[dm].P.cells;
+    const double* __restrict__ z = G.z;
+    double* __restrict__ dv = G.dv;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < n) dv[c] = first ? z[c] : z[c] + be * dv[c];
+    }
   }
 }
 
@@ -642,8 +730,10 @@ __global__ void k_any(const CgDom* __restrict__ C, int ndom, int* flag, cudaGrap
 __global__ void k_zero_if_b0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
   FOR_WORK(w)
     if (C[dm].scal[kBB] != 0.0) continue;
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < D[dm].P.cells) D[dm].F.p[c] = 0.0;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < D[dm].P.cells) D[dm].F.p[c] = 0.0;
+    }
   }
 }
 
@@ -665,16 +755,20 @@ __global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w) {
   FOR_WORK(w)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < G.lf[0].cells) G.lf[0].b[c] = (float)G.r[c];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < G.lf[0].cells) G.lf[0].b[c] = (float)G.r[c];
+    }
   }
 }
 __global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w) {
   FOR_WORK(w)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
-    if (c < G.lf[0].cells) G.z[c] = (double)G.lf[0].x[c];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < G.lf[0].cells) G.z[c] = (double)G.lf[0].x[c];
+    }
   }
 }
 
@@ -733,7 +827,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     return p;
   };
   const long long n0 = (long long)n[0] * n[1] * n[2];
-  const long long pcap = (n0 + kBlock - 1) / kBlock;
+  const long long pcap = (n0 + kBlock * kRepBig - 1) / (kBlock * kRepBig);
   double* r = (double*)take(n0 * 8);
   double* z = (double*)take(n0 * 8);
   double* dv = (double*)take(n0 * 8);
@@ -872,11 +966,19 @@ static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
 }
 
 template <typename R>
-static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_first, cudaStream_t s) {
+static void smooth_half(const BatchPlan& B, int l, int col, int zero, cudaStream_t s) {
   const int id = l == 0 ? K_SMOOTH0 : K_SMOOTHC;
   const Work& w = B.lhalf[l];
-  MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, k_smooth<R>, B.cg, w, l, first_col, zero_first ? 1 : 0);
-  MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, k_smooth<R>, B.cg, w, l, 1 - first_col, 0);
+  if (w.rep == kRepBig)
+    MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, kRepBig>), B.cg, w, l, col, zero);
+  else
+    MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 1>), B.cg, w, l, col, zero);
+}
+
+template <typename R>
+static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_first, cudaStream_t s) {
+  smooth_half<R>(B, l, first_col, zero_first ? 1 : 0, s);
+  smooth_half<R>(B, l, 1 - first_col, 0, s);
 }
 
 // Symmetric V-cycle of every active domain: level 0 receives M r.  Levels that
@@ -923,8 +1025,8 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
   }
   const int use = capture ? 1 : 0;
   // initial residual and loop condition
-  MDBS_LAUNCH(K_RESID0, grid_of(B, B.cells), kBlock, s, k_resid0, B.sd, B.cg, B.cells);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize, B.cg, B.cells, 0, 1, tol, max_it);
+  MDBS_LAUNCH(K_RESID0, grid_of(B, B.rcells), kBlock, s, k_resid0, B.sd, B.cg, B.rcells);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize, B.cg, B.rcells, 0, 1, tol, max_it);
   MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   MDBS_LAUNCH(K_ZERO, grid_of(B, B.cells), kBlock, s, k_zero_if_b0, B.sd, B.cg, B.cells);
   // one CG iteration, preconditioner first; the last kernels decide whether to continue
@@ -936,13 +1038,13 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
       vcycle<float>(B, nu1, nu2, cs, bs);
       MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells);
     }
-    MDBS_LAUNCH(K_DOTS, grid_of(B, B.cells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.cells, flexible);
-    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 3, flexible, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.cells), kBlock, bs, k_update_d, B.sd, B.cg, B.cells, flexible);
-    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.cells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.cells);
-    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 1, 0, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.cells), kBlock, bs, k_update_xr, B.sd, B.cg, B.cells);
-    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.cells, 2, 0, tol, max_it);
+    MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.rcells, flexible);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 3, flexible, tol, max_it);
+    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, k_update_d, B.sd, B.cg, B.rcells, flexible);
+    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.rcells);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 1, 0, tol, max_it);
+    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, k_update_xr, B.sd, B.cg, B.rcells);
+    MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 2, 0, tol, max_it);
     MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   };
   if (capture) {

@@ -153,8 +153,11 @@ __global__ void k_alpha_flux(const StepDom* __restrict__ D, Work w) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
-    const long long t = (long long)lb * blockDim.x + threadIdx.x;
-    const double v = t < total_faces(S.P) ? b_alpha_flux(S.P, S.F, t) : 0.0;
+    double v = 0.0;
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) v += b_alpha_flux(S.P, S.F, t);
+    }
     const double sum = block_sum(v);
     if (threadIdx.x == 0) S.partials[lb] = sum;
   }
@@ -495,10 +498,13 @@ __global__ void k_copy_faces(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    int d, i, j, k;
-    long long f;
-    if (decode_face(S.P, t, d, i, j, k, f)) S.F.u[d][f] = S.F.utmp[d][f];
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      int d, i, j, k;
+      long long f;
+      if (decode_face(S.P, t, d, i, j, k, f)) S.F.u[d][f] = S.F.utmp[d][f];
+    }
   }
 }
 
@@ -546,14 +552,16 @@ __global__ void k_field_stats(const StepDom* __restrict__ D, Work w) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
-    const long long c = (long long)lb * blockDim.x + threadIdx.x;
     double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
-    if (c < S.P.cells) {
-      const double a = S.F.alpha[c];
-      mass = S.F.phi[c] * a * S.P.V;
-      amin = a;
-      amax = a;
-      if (!isfinite(a) || !isfinite(S.F.p[c])) bad = 1.0;
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) {
+        const double a = S.F.alpha[c];
+        mass += S.F.phi[c] * a * S.P.V;
+        amin = fmin(amin, a);
+        amax = fmax(amax, a);
+        if (!isfinite(a) || !isfinite(S.F.p[c])) bad += 1.0;
+      }
     }
     const long long pc = S.pcap;
     mass = block_sum(mass);
@@ -605,14 +613,16 @@ __global__ void k_cfl(const StepDom* __restrict__ D, Work w) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
-    const long long t = (long long)lb * blockDim.x + threadIdx.x;
     double vmax = 0.0;
-    int d, i, j, k;
-    long long f;
-    if (decode_face(S.P, t, d, i, j, k, f)) {
-      const double phif = 0.5 * (ghost_read(S.F.phi, S.P.n, i - (d == 0), j - (d == 1), k - (d == 2)) +
-                                 ghost_read(S.F.phi, S.P.n, i, j, k));
-      vmax = fabs(S.F.u[d][f]) / phif;
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      int d, i, j, k;
+      long long f;
+      if (decode_face(S.P, t, d, i, j, k, f)) {
+        const double phif = 0.5 * (ghost_read(S.F.phi, S.P.n, i - (d == 0), j - (d == 1), k - (d == 2)) +
+                                   ghost_read(S.F.phi, S.P.n, i, j, k));
+        vmax = fmax(vmax, fabs(S.F.u[d][f]) / phif);
+      }
     }
     vmax = warp_reduce_max(vmax);
     __syncthreads();
@@ -677,8 +687,11 @@ __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_static_geometry(S.P, S.F, c);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_static_geometry(S.P, S.F, c);
+    }
   }
 }
 
@@ -687,8 +700,11 @@ __global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_alpha_lo(S.P, S.F, c, S.scal[kSlotDt]);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_alpha_lo(S.P, S.F, c, S.scal[kSlotDt]);
+    }
   }
 }
 
@@ -696,8 +712,11 @@ __global__ void k_alpha_limit(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_alpha_limit(S.P, S.F, c, S.scal[kSlotDt]);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_alpha_limit(S.P, S.F, c, S.scal[kSlotDt]);
+    }
   }
 }
 
@@ -705,8 +724,11 @@ __global__ void k_alpha_update(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_alpha_update(S.P, S.F, c, S.scal[kSlotDt]);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_alpha_update(S.P, S.F, c, S.scal[kSlotDt]);
+    }
   }
 }
 
@@ -714,8 +736,11 @@ __global__ void k_properties(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_properties(S.P, S.F, c);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_properties(S.P, S.F, c);
+    }
   }
 }
 
@@ -723,8 +748,11 @@ __global__ void k_normals(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_normals(S.P, S.F, c);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_normals(S.P, S.F, c);
+    }
   }
 }
 
@@ -732,8 +760,11 @@ __global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long c = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (c < S.P.cells) b_curvature(S.P, S.F, c);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_curvature(S.P, S.F, c);
+    }
   }
 }
 
@@ -741,8 +772,11 @@ __global__ void k_momentum_assemble(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (t < total_faces(S.P)) b_momentum_assemble(S.P, S.F, t, S.scal[kSlotDt]);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) b_momentum_assemble(S.P, S.F, t, S.scal[kSlotDt]);
+    }
   }
 }
 
@@ -750,12 +784,15 @@ __global__ void k_jacobi(const StepDom* __restrict__ D, Work w, int parity) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
+    const int lb = b - w.blk[dm];
     Faces3 a{{S.F.u[0], S.F.u[1], S.F.u[2]}}, c{{S.F.utmp[0], S.F.utmp[1], S.F.utmp[2]}};
-    if (parity)
-      b_jacobi(S.P, S.F, t, c, a);
-    else
-      b_jacobi(S.P, S.F, t, a, c);
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (parity)
+        b_jacobi(S.P, S.F, t, c, a);
+      else
+        b_jacobi(S.P, S.F, t, a, c);
+    }
   }
 }
 
@@ -763,8 +800,11 @@ __global__ void k_hbya(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (t < total_faces(S.P)) b_hbya(S.P, S.F, t);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) b_hbya(S.P, S.F, t);
+    }
   }
 }
 
@@ -772,8 +812,11 @@ __global__ void k_correct(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (t < total_faces(S.P)) b_correct(S.P, S.F, t);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) b_correct(S.P, S.F, t);
+    }
   }
 }
 
@@ -781,8 +824,11 @@ __global__ void k_boundary_velocities(const StepDom* __restrict__ D, Work w) {
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
-    const long long t = (long long)(b - w.blk[dm]) * blockDim.x + threadIdx.x;
-    if (t < total_faces(S.P)) b_boundary_velocities(S.P, S.F, t);
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) b_boundary_velocities(S.P, S.F, t);
+    }
   }
 }
 
@@ -793,8 +839,8 @@ __global__ void k_boundary_velocities(const StepDom* __restrict__ D, Work w) {
   MDBS_LAUNCH(ID, grid_of(B, B.SPACE), kBlock, s, KERNEL, B.sd, B.SPACE, ##__VA_ARGS__)
 
 void launch_alpha_step(const BatchPlan& B, cudaStream_t s) {
-  BATCH_LAUNCH(K_ALPHA_FLUX, faces, k_alpha_flux);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_inflow, B.sd, B.faces, kSlotInflow);
+  BATCH_LAUNCH(K_ALPHA_FLUX, rfaces, k_alpha_flux);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_inflow, B.sd, B.rfaces, kSlotInflow);
   BATCH_LAUNCH(K_ALPHA_LO, cells, k_alpha_lo);
   BATCH_LAUNCH(K_ALPHA_LIMIT, cells, k_alpha_limit);
   BATCH_LAUNCH(K_ALPHA_UPDATE, cells, k_alpha_update);
@@ -825,13 +871,13 @@ void launch_set_boundary_velocities(const BatchPlan& B, cudaStream_t s) {
 }
 
 void launch_field_stats(const BatchPlan& B, cudaStream_t s) {
-  BATCH_LAUNCH(K_STATS, cells, k_field_stats);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_stats, B.sd, B.cells);
+  BATCH_LAUNCH(K_STATS, rcells, k_field_stats);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_stats, B.sd, B.rcells);
 }
 
 void launch_time_advance(const BatchPlan& B, cudaStream_t s) {
-  if (B.any_cfl) BATCH_LAUNCH(K_CFL, faces, k_cfl);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_time, B.sd, B.faces);
+  if (B.any_cfl) BATCH_LAUNCH(K_CFL, rfaces, k_cfl);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_time, B.sd, B.rfaces);
 }
 
 void launch_static_geometry(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_STATIC, cells, k_static_geometry); }
