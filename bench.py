@@ -48,7 +48,11 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched"])
+    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched", "serving"])
+    ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
+    ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window [s]")
+    ap.add_argument("--max-side", type=int, default=96, help="serving: largest cube side")
+    ap.add_argument("--req-steps", type=int, default=100, help="serving: steps per request")
     ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
     return ap.parse_args()
@@ -412,8 +416,42 @@ def batched_arm(args):
     return 0
 
 
+def serving_arm(args):
+    """Continuous batching of a seeded Poisson trace of fractured-porous requests (sides
+    log-uniform in [32, max_side], capillary number log-uniform in [1e-5, 1e-2])."""
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2003_08374_gb300.build import build_library
+    build_library()
+    from paper_2003_08374_gb300 import workloads as W
+    from paper_2003_08374_gb300.serve import Request, Server, fractured_request_case
+    trace = W.poisson_requests(rate=args.rate, duration=args.duration, seed=5, lo=32, hi=args.max_side)
+    reqs = [Request(rid=i, arrival=t["t"], steps=args.req_steps,
+                    case=fractured_request_case(t["side"], t["ca"], t["seed"], precision=args.precision,
+                                                p_tol=1e-8, max_cg=200))
+            for i, t in enumerate(trace)]
+    offered = sum(r.case.cells * r.steps for r in reqs) / args.duration
+    srv = Server(max_active=256, round_steps=10, keep_fields=False,
+                 stream_handle=torch.cuda.current_stream().cuda_stream)
+    with ClockSampler(local) as clk:
+        summary = srv.run(reqs)
+    line = {"metric": METRIC, "value": summary["served_cell_steps_per_s"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.req_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "serving_poisson_%.0fps_%.0fs_side32-%d_%dsteps" % (args.rate, args.duration,
+                                                                                    args.max_side, args.req_steps),
+                       "precision": "fp64" if args.precision == 0 else "mixed",
+                       "offered_cell_steps_per_s": offered},
+            "serving": summary, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
+    if args.workload == "serving" and args.impl != "reference":
+        return serving_arm(args)
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batched":
