@@ -292,6 +292,9 @@ def gpu_arm(args):
         return ms, prof, clk.summary(), st["kernel_launches"] - l0, st
 
     case = workload(args.n)
+    if args.precision == 1:  # the mixed variant alone (profiling runs)
+        case = case.replace(precision=W.MIXED)
+        args.no_mixed = True
     sim = mdbs.Simulation(case)
     sim.set_stream(stream.cuda_stream)
     # headline: every step is one CUDA-graph launch (CG loops as device-side WHILE nodes)
@@ -305,7 +308,7 @@ def gpu_arm(args):
     _, prof, _, _, _ = timed(sim, args.steps, args.warmup, "*")
     breakdown = {k: round(v[0] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
-    roof = roofline(prof, case.cells, 8, fp64=True)
+    roof = roofline(prof, case.cells, 8 if args.precision == 0 else 4, fp64=args.precision == 0)
 
     mixed = None
     if not args.no_mixed:
@@ -362,7 +365,7 @@ def gpu_arm(args):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": case.name, "cells": case.cells, "p_tol": case.p_tol, "n_corr": case.n_corr,
+            "config": {"workload": case.name + ("" if args.precision == 0 else " (mixed)"), "cells": case.cells, "p_tol": case.p_tol, "n_corr": case.n_corr,
                        "mom_sweeps": case.mom_sweeps, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%.1f GB device state)" % (mdbs.bytes_required(case) / 1e9),
                        "cg_iters_last_step": cg_iters},
