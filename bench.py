@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--req-steps", type=int, default=100, help="serving: steps per request")
     ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
     return ap.parse_args()
 
 
@@ -297,6 +298,8 @@ def gpu_arm(args):
         args.no_mixed = True
     sim = mdbs.Simulation(case)
     sim.set_stream(stream.cuda_stream)
+    # schedule of the multigrid kernels picked by timing real steps (state restored after)
+    tuning, tune_ms = (sim.tuning(), []) if args.no_autotune else sim.autotune(trial_steps=2)
     # headline: every step is one CUDA-graph launch (CG loops as device-side WHILE nodes)
     ms, _, clocks, launches, st = timed(sim, args.steps, args.warmup)
     ms = max_over_ranks(ms)
@@ -315,12 +318,13 @@ def gpu_arm(args):
         mcase = case.replace(precision=W.MIXED)
         msim = mdbs.Simulation(mcase)
         msim.set_stream(stream.cuda_stream)
+        mtuning = msim.tuning() if args.no_autotune else msim.autotune(trial_steps=2)[0]
         mms, _, _, _, mst = timed(msim, args.steps, args.warmup)
         mms = max_over_ranks(mms)
         mval = case.cells * args.steps * world / (mms / 1e3)
         msim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
         _, mprof, _, _, _ = timed(msim, args.steps, args.warmup, DOMINANT)
-        mixed = {"value": mval, "ms_per_step": mms / args.steps, "speedup_vs_fp64": mval / value,
+        mixed = {"value": mval, "ms_per_step": mms / args.steps, "speedup_vs_fp64": mval / value, "tuning": mtuning,
                  "cg_iters_last_step": mst["cg_iters"], "roofline": roofline(mprof, case.cells, 4, fp64=False)}
         msim.close()
 
@@ -368,7 +372,8 @@ def gpu_arm(args):
             "config": {"workload": case.name + ("" if args.precision == 0 else " (mixed)"), "cells": case.cells, "p_tol": case.p_tol, "n_corr": case.n_corr,
                        "mom_sweeps": case.mom_sweeps, "parallelism": "replicas" if world > 1 else "single",
                        "l2": "inputs larger than L2 (%.1f GB device state)" % (mdbs.bytes_required(case) / 1e9),
-                       "cg_iters_last_step": cg_iters},
+                       "cg_iters_last_step": cg_iters, "tuning": tuning,
+                       "autotune_ms_per_trial": [round(t, 3) for t in tune_ms]},
             "mixed": mixed, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches,
             "kernel_ms_per_step": breakdown,
@@ -395,6 +400,7 @@ def batched_arm(args):
     sims = [mdbs.Simulation(c) for c in cases]
     b = mdbs.Batch(sims)
     b.set_stream(stream.cuda_stream)
+    tuning, tune_ms = (b.tuning(), []) if args.no_autotune else b.autotune(trial_steps=1)
     for _ in range(args.warmup):
         b.step(1)
     torch.cuda.synchronize()
@@ -412,7 +418,8 @@ def batched_arm(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "batched_%d_domains" % len(cases), "cells": cells,
                        "precision": "fp64" if args.precision == 0 else "mixed",
-                       "cg_iters_max": max(max(i) for i in iters), "cg_iters_mean": float(np.mean(iters))},
+                       "cg_iters_max": max(max(i) for i in iters), "cg_iters_mean": float(np.mean(iters)),
+                       "tuning": tuning, "autotune_ms_per_trial": [round(t, 2) for t in tune_ms]},
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
     b.close()

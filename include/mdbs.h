@@ -185,6 +185,59 @@ int mdbs_batch_set_stream(mdbs_batch* batch, void* cuda_stream);
 const char* mdbs_batch_last_error(const mdbs_batch* batch);
 void mdbs_batch_destroy(mdbs_batch* batch);
 
+/* ---------------- execution schedule and autotuning ---------------- */
+
+/*
+ * How the pressure solver's multigrid kernels are scheduled (no counterpart in the
+ * paper: the schedule decides speed only).  Every schedule computes every value
+ * with the same arithmetic in the same order, so results are bitwise identical
+ * under any schedule; only the time per step changes.
+ *   smooth_rows : 1, 2, 4 or 8 rows of 256 cells per CTA work item in the
+ *                 finest-level red-black sweeps (fewer rows: more CTAs in flight)
+ *   tail_cells  : 0 .. 32768; levels with at most this many cells run, with all
+ *                 coarser ones, inside one CTA per domain (fewer launches, less
+ *                 parallelism)
+ *   snake       : 0 or 1; 1 alternates the traversal direction of consecutive
+ *                 kernels over one level, so each starts on the cache lines the
+ *                 previous one touched last
+ *   sweep_kz    : 0, 4, 8, 16 or 32; > 0 runs each red-black sweep pair as ONE fused
+ *                 launch over tiles of 30 x 14 columns and chunks of sweep_kz
+ *                 planes (every array read once per pair); 0 runs two half sweeps
+ *                 (then smooth_rows applies)
+ * Default: {1, 4096, 0, 0}.  Values outside these sets give MDBS_ERR_ARG.
+ */
+typedef struct {
+  int32_t smooth_rows;
+  int32_t tail_cells;
+  int32_t snake;
+  int32_t sweep_kz;
+} mdbs_tuning;
+
+/* Sets or reads the schedule of a simulation that is not in a batch (the step
+ * graph is rebuilt at the next step), or of a batch (default: its first member's). */
+int mdbs_set_tuning(mdbs_sim* sim, const mdbs_tuning* tuning);
+int mdbs_get_tuning(const mdbs_sim* sim, mdbs_tuning* out);
+int mdbs_batch_set_tuning(mdbs_batch* batch, const mdbs_tuning* tuning);
+int mdbs_batch_get_tuning(const mdbs_batch* batch, mdbs_tuning* out);
+
+/*
+ * Picks the fastest schedule for this simulation (or batch) by timing real steps:
+ * starting from the current schedule it tries the alternatives of snake, then of
+ * smooth_rows, then of tail_cells (coordinate descent), each for one untimed and
+ * trial_steps >= 1 timed steps (CUDA events on the simulation's stream), and keeps
+ * a change only when it is faster.  The device state (fields, step scalars) is
+ * copied aside first and restored after every trial, so the simulation continues
+ * exactly as if mdbs_autotune had not run (the statistics, too).  Needs free device
+ * memory for one copy of the simulation's (or every member's) arena:
+ * MDBS_ERR_OOM otherwise, with nothing changed.  *chosen (may be NULL) receives
+ * the schedule kept; trial_ms (may be NULL, capacity entries) receives the
+ * per-step time of every trial in order, and *trials (may be NULL) their count.
+ */
+int mdbs_autotune(mdbs_sim* sim, int32_t trial_steps, mdbs_tuning* chosen, double* trial_ms, int32_t capacity,
+                  int32_t* trials);
+int mdbs_batch_autotune(mdbs_batch* batch, int32_t trial_steps, mdbs_tuning* chosen, double* trial_ms,
+                        int32_t capacity, int32_t* trials);
+
 /* ---------------- helpers ---------------- */
 
 /* Statistics of the last step (see mdbs_stats). */

@@ -16,10 +16,13 @@ long long faces_total(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P
 
 }  // namespace
 
-cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, BatchPlan* out) {
+cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
+                        int sweep_kz, BatchPlan* out) {
   BatchPlan B{};
   B.ndom = ndom;
   B.flexible = flexible;
+  B.snake = snake;
+  B.sweep_kz = sweep_kz;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -27,7 +30,7 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   // blocks; larger spaces loop (grid stride)
   B.grid_cap = sms * (2048 / kBlock) * 64;
   // host block tables: spaces in a fixed order, each ndom + 1 prefix entries
-  const int nspace = 5 + 4 * kMaxLevels;
+  const int nspace = 5 + 5 * kMaxLevels;
   std::vector<int> tab((size_t)nspace * (ndom + 1), 0);
   auto fill = [&](int space, auto count) -> int {
     int* t = &tab[(size_t)space * (ndom + 1)];
@@ -39,13 +42,13 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     t[ndom] = (int)acc;
     return (int)acc;
   };
-  int totals[5 + 4 * kMaxLevels];
+  int totals[5 + 5 * kMaxLevels];
   // one row of kBlock elements per item, except the reduction spaces (kRepBig rows:
   // fewer block reductions and partials)
-  int reps[5 + 4 * kMaxLevels];
-  for (int q = 0; q < 5 + 4 * kMaxLevels; q++) reps[q] = 1;
+  int reps[5 + 5 * kMaxLevels];
+  for (int q = 0; q < 5 + 5 * kMaxLevels; q++) reps[q] = 1;
   reps[3] = reps[4] = kRepBig;
-  reps[5 + kMaxLevels] = kRepBig;  // finest-level red/black half sweeps
+  reps[5 + kMaxLevels] = smooth_rows;  // finest-level red/black half sweeps
   auto blocks_of = [&](long long n, int space) { return items_of(n, reps[space]); };
   totals[0] = fill(0, [&](int d) { return blocks_of(sd[d].P.cells, 0); });
   totals[1] = fill(1, [&](int d) { return blocks_of(faces_total(sd[d].P), 1); });
@@ -74,6 +77,13 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     });
     totals[s2] = fill(s2, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l), s2) : 0LL; });
     totals[s3] = fill(s3, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l + 1), s3) : 0LL; });
+    const int s4 = 5 + 4 * kMaxLevels + l;
+    totals[s4] = fill(s4, [&](int d) -> long long {
+      if (l >= cg[d].first || sweep_kz <= 0) return 0;
+      const Level<double>& L = cg[d].ld[l];
+      return (long long)((L.n[0] + kSweepTX - 1) / kSweepTX) * ((L.n[1] + kSweepTY - 1) / kSweepTY) *
+             ((L.n[2] + sweep_kz - 1) / sweep_kz);
+    });
   }
   cudaError_t e = cudaMalloc(&B.table_storage, tab.size() * sizeof(int));
   if (e != cudaSuccess) return e;
@@ -105,6 +115,7 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     B.lhalf[l] = work(5 + kMaxLevels + l);
     B.lfine[l] = work(5 + 2 * kMaxLevels + l);
     B.lcoarse[l] = work(5 + 3 * kMaxLevels + l);
+    B.lsweep[l] = work(5 + 4 * kMaxLevels + l);
   }
   *out = B;
   return cudaSuccess;

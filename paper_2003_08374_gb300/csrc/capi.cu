@@ -128,6 +128,7 @@ struct mdbs_sim {
   bool fields_set;
   bool in_batch;
   std::string err;
+  mdbs_tuning tun;    // schedule of the multigrid kernels
   Exec ex;            // batch of one: this simulation alone
 };
 
@@ -136,6 +137,7 @@ struct mdbs_batch {
   std::vector<mdbs_sim*> sims;
   mdbs_options opt;
   cudaStream_t stream;
+  mdbs_tuning tun;
   Exec ex;
   double* gather;       // device: ndom x kNumSlots step scalars
   double* host_gather;  // pinned
@@ -314,8 +316,8 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
   return cudaGetLastError();
 }
 
-cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible) {
-  cudaError_t e = plan_create(sd, cg, ndom, flexible, &ex.plan);
+cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible, const mdbs_tuning& t) {
+  cudaError_t e = plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, &ex.plan);
   if (e != cudaSuccess) return e;
   ex.planned = true;
   if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
@@ -380,6 +382,168 @@ cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaSt
   return cudaSuccess;
 }
 
+const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0};
+
+bool valid_tuning(const mdbs_tuning* t) {
+  return t && (t->smooth_rows == 1 || t->smooth_rows == 2 || t->smooth_rows == 4 || t->smooth_rows == 8) &&
+         t->tail_cells >= 0 && t->tail_cells <= kTailCellsMax && (t->snake == 0 || t->snake == 1) &&
+         (t->sweep_kz == 0 || t->sweep_kz == 4 || t->sweep_kz == 8 || t->sweep_kz == 16 || t->sweep_kz == 32);
+}
+
+// (re)builds the batch-of-one plan of a simulation for its schedule
+cudaError_t sim_exec_setup(mdbs_sim* s) {
+  if (s->ex.graph) cudaGraphExecDestroy(s->ex.graph);
+  s->ex.graph = nullptr;
+  if (s->ex.planned) plan_destroy(&s->ex.plan);
+  s->ex.planned = false;
+  StepDom sd = step_view(s);
+  CgDom cg;
+  pressure_view(s->ps, s->F, s->tun.tail_cells, &cg);
+  return exec_setup(s->ex, &sd, &cg, 1, s->precision != 0, s->tun);
+}
+
+cudaError_t batch_exec_setup(mdbs_batch* b) {
+  if (b->ex.graph) cudaGraphExecDestroy(b->ex.graph);
+  b->ex.graph = nullptr;
+  if (b->ex.planned) plan_destroy(&b->ex.plan);
+  b->ex.planned = false;
+  const int n = (int)b->sims.size();
+  std::vector<StepDom> sd(n);
+  std::vector<CgDom> cg(n);
+  for (int i = 0; i < n; i++) {
+    sd[i] = step_view(b->sims[i]);
+    pressure_view(b->sims[i]->ps, b->sims[i]->F, b->tun.tail_cells, &cg[i]);
+  }
+  return exec_setup(b->ex, sd.data(), cg.data(), n, b->sims[0]->precision != 0, b->tun);
+}
+
+// Device state of the simulations being tuned, copied aside so that every trial
+// starts from it and the simulations end where they were.
+struct Snapshot {
+  struct Part {
+    void* src;
+    void* copy;
+    size_t bytes;
+  };
+  std::vector<Part> parts;
+  std::vector<mdbs_stats> st;
+  std::vector<std::vector<double>> host_scal;
+  ~Snapshot() {
+    for (Part& p : parts)
+      if (p.copy) cudaFree(p.copy);
+  }
+  cudaError_t take(const std::vector<mdbs_sim*>& sims, cudaStream_t stream) {
+    for (mdbs_sim* s : sims) {
+      void* pp;
+      size_t pb;
+      pressure_storage(s->ps, &pp, &pb);
+      for (Part p : {Part{s->arena, nullptr, s->arena_bytes}, Part{pp, nullptr, pb}}) {
+        cudaError_t e = cudaMalloc(&p.copy, p.bytes);
+        if (e != cudaSuccess) return e;
+        parts.push_back(p);
+        e = cudaMemcpyAsync(p.copy, p.src, p.bytes, cudaMemcpyDeviceToDevice, stream);
+        if (e != cudaSuccess) return e;
+      }
+      st.push_back(s->st);
+      host_scal.emplace_back(s->host_scal, s->host_scal + kNumSlots);
+    }
+    return cudaStreamSynchronize(stream);
+  }
+  cudaError_t restore(cudaStream_t stream) const {
+    for (const Part& p : parts) {
+      cudaError_t e = cudaMemcpyAsync(p.src, p.copy, p.bytes, cudaMemcpyDeviceToDevice, stream);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(stream);
+  }
+  void restore_host(const std::vector<mdbs_sim*>& sims) const {
+    for (size_t i = 0; i < sims.size(); i++) {
+      sims[i]->st = st[i];
+      for (int k = 0; k < kNumSlots; k++) sims[i]->host_scal[k] = host_scal[i][k];
+    }
+  }
+};
+
+// Coordinate descent over the schedule (snake, then smooth_rows, then tail_cells):
+// every trial restores the snapshot, rebuilds the plan, runs one untimed and
+// `steps` timed graph steps.  setup(t) installs schedule t.
+template <typename Setup>
+int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_options& opt, Profiler& prof,
+                  cudaStream_t stream, mdbs_tuning& tun, Setup setup, int steps, double* trial_ms, int capacity,
+                  int* ntrials, std::string& err) {
+  Snapshot snap;
+  cudaError_t e = snap.take(sims, stream);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    err = std::string("autotune snapshot: ") + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
+  }
+  const bool was_on = prof.on;
+  const long long launches = prof.launches;
+  prof.on = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaEventCreate(&ev0);
+  cudaEventCreate(&ev1);
+  int count = 0;
+  auto trial = [&](const mdbs_tuning& t, double* ms) -> cudaError_t {
+    cudaError_t r = setup(t);
+    if (r == cudaSuccess) r = snap.restore(stream);
+    if (r == cudaSuccess) r = exec_steps(ex, opt, prof, stream, 1);
+    if (r == cudaSuccess) r = cudaEventRecord(ev0, stream);
+    if (r == cudaSuccess) r = exec_steps(ex, opt, prof, stream, steps);
+    if (r == cudaSuccess) r = cudaEventRecord(ev1, stream);
+    if (r == cudaSuccess) r = cudaEventSynchronize(ev1);
+    float f = 0.f;
+    if (r == cudaSuccess) r = cudaEventElapsedTime(&f, ev0, ev1);
+    *ms = (double)f / steps;
+    if (r == cudaSuccess) {
+      if (trial_ms && count < capacity) trial_ms[count] = *ms;
+      count++;
+    }
+    return r;
+  };
+  mdbs_tuning best = tun;
+  double best_ms = 0.0;
+  e = trial(best, &best_ms);
+  // axes in order; smooth_rows only matters for split half sweeps (sweep_kz == 0)
+  const int snakes[] = {0, 1};
+  const int kzs[] = {0, 4, 8, 16, 32};
+  const int rows[] = {1, 2, 4, 8};
+  const int tails[] = {0, 512, 4096, 32768};
+  for (int axis = 0; axis < 4 && e == cudaSuccess; axis++) {
+    if (axis == 2 && best.sweep_kz > 0) continue;
+    const int* vals = axis == 0 ? snakes : axis == 1 ? kzs : axis == 2 ? rows : tails;
+    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : 4;
+    const mdbs_tuning base = best;
+    for (int v = 0; v < nv && e == cudaSuccess; v++) {
+      mdbs_tuning t = base;
+      int* field = axis == 0 ? &t.snake : axis == 1 ? &t.sweep_kz : axis == 2 ? &t.smooth_rows : &t.tail_cells;
+      if (*field == vals[v]) continue;
+      *field = vals[v];
+      double ms = 0.0;
+      e = trial(t, &ms);
+      if (e == cudaSuccess && ms < best_ms) {
+        best = t;
+        best_ms = ms;
+      }
+    }
+  }
+  if (e == cudaSuccess) e = setup(best);
+  if (e == cudaSuccess) e = snap.restore(stream);
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  snap.restore_host(sims);
+  prof.on = was_on;
+  prof.launches = launches;
+  if (ntrials) *ntrials = count;
+  if (e != cudaSuccess) {
+    err = std::string("autotune: ") + cudaGetErrorString(e);
+    return MDBS_ERR_CUDA;
+  }
+  tun = best;
+  return MDBS_OK;
+}
+
 bool same_solver_options(const mdbs_options& a, const mdbs_options& b) {
   return a.n_corr == b.n_corr && a.mom_sweeps == b.mom_sweeps && a.p_tol == b.p_tol && a.max_cg == b.max_cg &&
          a.mg_nu1 == b.mg_nu1 && a.mg_nu2 == b.mg_nu2 && a.mg_coarse_sweeps == b.mg_coarse_sweeps &&
@@ -431,6 +595,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
 
   s = new (std::nothrow) mdbs_sim();
   if (!s) return fail(nullptr, MDBS_ERR_OOM, "host allocation failed");
+  s->tun = kDefaultTuning;
   Prm& P = s->P;
   P.n[0] = grid->nx;
   P.n[1] = grid->ny;
@@ -503,8 +668,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
     // this simulation alone as a batch of one
     StepDom sd = step_view(s);
     CgDom cg;
-    pressure_view(s->ps, s->F, &cg);
-    e = exec_setup(s->ex, &sd, &cg, 1, s->precision != 0);
+    pressure_view(s->ps, s->F, s->tun.tail_cells, &cg);
+    e = exec_setup(s->ex, &sd, &cg, 1, s->precision != 0, s->tun);
   }
   if (e == cudaSuccess) {
     Activate act(s);
@@ -624,13 +789,8 @@ int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out) {
   b->sims.assign(sims, sims + n);
   b->opt = sims[0]->opt;
   b->stream = nullptr;
-  std::vector<StepDom> sd(n);
-  std::vector<CgDom> cg(n);
-  for (int i = 0; i < n; i++) {
-    sd[i] = step_view(sims[i]);
-    pressure_view(sims[i]->ps, sims[i]->F, &cg[i]);
-  }
-  cudaError_t e = exec_setup(b->ex, sd.data(), cg.data(), n, sims[0]->precision != 0);
+  b->tun = sims[0]->tun;
+  cudaError_t e = batch_exec_setup(b);
   if (e == cudaSuccess) e = cudaMalloc(&b->gather, (size_t)n * kNumSlots * sizeof(double));
   if (e == cudaSuccess) e = cudaMallocHost(&b->host_gather, (size_t)n * kNumSlots * sizeof(double));
   if (e != cudaSuccess) {
@@ -643,6 +803,103 @@ int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out) {
   for (int i = 0; i < n; i++) sims[i]->in_batch = true;
   *out = b;
   return MDBS_OK;
+}
+
+// ---------------------------------------------------------------- schedule
+int mdbs_set_tuning(mdbs_sim* s, const mdbs_tuning* t) {
+  if (!s) return MDBS_ERR_ARG;
+  if (!valid_tuning(t)) return fail(s, MDBS_ERR_ARG, "invalid tuning");
+  if (s->in_batch) return fail(s, MDBS_ERR_ARG, "the simulation belongs to a batch: tune the batch");
+  CK(cudaStreamSynchronize(s->stream));
+  const mdbs_tuning old = s->tun;
+  s->tun = *t;
+  cudaError_t e = sim_exec_setup(s);
+  if (e != cudaSuccess) {
+    s->tun = old;
+    cudaGetLastError();
+    sim_exec_setup(s);
+    return cuda_fail(s, e, "set_tuning");
+  }
+  return MDBS_OK;
+}
+
+int mdbs_get_tuning(const mdbs_sim* s, mdbs_tuning* out) {
+  if (!s || !out) return MDBS_ERR_ARG;
+  *out = s->tun;
+  return MDBS_OK;
+}
+
+int mdbs_batch_set_tuning(mdbs_batch* b, const mdbs_tuning* t) {
+  if (!b) return MDBS_ERR_ARG;
+  if (!valid_tuning(t)) {
+    b->err = "invalid tuning";
+    return MDBS_ERR_ARG;
+  }
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  const mdbs_tuning old = b->tun;
+  b->tun = *t;
+  if (e == cudaSuccess) e = batch_exec_setup(b);
+  if (e != cudaSuccess) {
+    b->tun = old;
+    cudaGetLastError();
+    batch_exec_setup(b);
+    b->err = std::string("set_tuning: ") + cudaGetErrorString(e);
+    return MDBS_ERR_CUDA;
+  }
+  return MDBS_OK;
+}
+
+int mdbs_batch_get_tuning(const mdbs_batch* b, mdbs_tuning* out) {
+  if (!b || !out) return MDBS_ERR_ARG;
+  *out = b->tun;
+  return MDBS_OK;
+}
+
+int mdbs_autotune(mdbs_sim* s, int32_t trial_steps, mdbs_tuning* chosen, double* trial_ms, int32_t capacity,
+                  int32_t* trials) {
+  if (!s) return MDBS_ERR_ARG;
+  if (trial_steps < 1 || capacity < 0) return fail(s, MDBS_ERR_ARG, "trial_steps must be >= 1");
+  if (!s->fields_set) return fail(s, MDBS_ERR_ARG, "mdbs_set_fields has not been called");
+  if (s->in_batch) return fail(s, MDBS_ERR_ARG, "the simulation belongs to a batch: tune the batch");
+  Activate act(s);
+  CK(cudaStreamSynchronize(s->stream));
+  auto setup = [&](const mdbs_tuning& t) {
+    s->tun = t;
+    return sim_exec_setup(s);
+  };
+  std::vector<mdbs_sim*> one{s};
+  mdbs_tuning tun = s->tun;
+  int nt = 0;
+  const int rc = autotune_impl(one, s->ex, s->opt, s->prof, s->stream, tun, setup, trial_steps, trial_ms, capacity,
+                               &nt, s->err);
+  if (trials) *trials = nt;
+  if (rc == MDBS_OK && chosen) *chosen = s->tun;
+  return rc;
+}
+
+int mdbs_batch_autotune(mdbs_batch* b, int32_t trial_steps, mdbs_tuning* chosen, double* trial_ms,
+                        int32_t capacity, int32_t* trials) {
+  if (!b) return MDBS_ERR_ARG;
+  if (trial_steps < 1 || capacity < 0) {
+    b->err = "trial_steps must be >= 1";
+    return MDBS_ERR_ARG;
+  }
+  Activate act(b);
+  if (cudaStreamSynchronize(b->stream) != cudaSuccess) {
+    b->err = "stream error before autotune";
+    return MDBS_ERR_CUDA;
+  }
+  auto setup = [&](const mdbs_tuning& t) {
+    b->tun = t;
+    return batch_exec_setup(b);
+  };
+  mdbs_tuning tun = b->tun;
+  int nt = 0;
+  const int rc = autotune_impl(b->sims, b->ex, b->opt, b->prof, b->stream, tun, setup, trial_steps, trial_ms,
+                               capacity, &nt, b->err);
+  if (trials) *trials = nt;
+  if (rc == MDBS_OK && chosen) *chosen = b->tun;
+  return rc;
 }
 
 int mdbs_batch_set_stream(mdbs_batch* b, void* stream) {

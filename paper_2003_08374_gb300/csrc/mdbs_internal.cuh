@@ -74,6 +74,7 @@ struct Level {
   R* diag;
   R* dinv;  // 1 / diag (multiplied in the smoothers instead of dividing)
   R* x;
+  R* x2;    // second iterate buffer of the fused red-black sweeps (read one, write the other)
   R* b;
 };
 
@@ -192,10 +193,13 @@ struct BatchPlan {
   Work lhalf[kMaxLevels];     // level-l red/black half cells of domains whose level l precedes the tail
   Work lfine[kMaxLevels];     // level-l cells of the same domains (prolongation)
   Work lcoarse[kMaxLevels];   // level-(l+1) cells of the same domains (restriction)
+  Work lsweep[kMaxLevels];    // fused-sweep tiles (kSweepTX x kSweepTY columns x sweep_kz planes) of the same domains
   int max_first;              // largest tail start over the domains
   int max_levels;             // largest level count over the domains
   int flexible;               // FP32 V-cycle inside flexible CG
   int any_cfl;                // some domain uses the adaptive time step
+  int snake;                  // alternate the traversal direction of consecutive level kernels
+  int sweep_kz;               // > 0: fused red-black sweeps over chunks of this many planes; 0: half sweeps
   StepDom* sd;                // device tables (ndom entries)
   CgDom* cg;
   int* table_storage;         // device memory of every block table
@@ -224,8 +228,12 @@ struct PressureSolver;
 PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err);
 void pressure_destroy(PressureSolver* ps);
 size_t pressure_bytes(const int n[3], int precision);
-// fills the per-domain solver view (level 0 of the FP64 hierarchy points into F)
-void pressure_view(const PressureSolver* ps, const Fld& F, CgDom* out);
+// fills the per-domain solver view (level 0 of the FP64 hierarchy points into F);
+// levels with at most tail_cells cells (and all coarser ones) go to the single-CTA tail
+void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom* out);
+// the solver's single device allocation
+void pressure_storage(const PressureSolver* ps, void** ptr, size_t* bytes);
+constexpr int kTailCellsMax = 32768;
 int pressure_precision(const PressureSolver* ps);
 void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s);
 // Enqueues the solve of A p = b for every domain of the batch by GMG-preconditioned
@@ -240,7 +248,14 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
 
 // batch.cu
 // builds the block tables and device views of a batch of domains
-cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, BatchPlan* out);
+// Fused red-black sweep tiles: a CTA of kSweepBX x kSweepBY threads owns the interior
+// kSweepTX x kSweepTY columns plus a one-column halo ring.
+constexpr int kSweepBX = 32, kSweepBY = 16, kSweepTX = kSweepBX - 2, kSweepTY = kSweepBY - 2;
+
+// smooth_rows: kBlock rows per work item of the finest-level half sweeps (1, 2, 4, 8);
+// sweep_kz: planes per fused-sweep chunk (0: half sweeps)
+cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
+                        int sweep_kz, BatchPlan* out);
 void plan_destroy(BatchPlan* B);
 
 }  // namespace mdbs

@@ -41,6 +41,16 @@ constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6
     const int dm = work_domain((W), b_);              \
     const int lb = b_ - (W).blk[dm];
 
+// The same walk with the item order reversed when REV != 0.  Consecutive kernels
+// over one level alternate direction, so that each starts on the cache lines the
+// previous one touched last (still in L2).  Every item computes the same values,
+// and writes the same partial, in either order.
+#define FOR_WORK_DIR(W, REV)                                              \
+  for (int i_ = blockIdx.x; i_ < (W).total; i_ += gridDim.x) {            \
+    const int b_ = (REV) ? (W).total - 1 - i_ : i_;                        \
+    const int dm = work_domain((W), b_);                                  \
+    const int lb = b_ - (W).blk[dm];
+
 // ------------------------------------------------------------------ assembly
 // T_f = A^2 / a_P,f between cells, 2 A^2 / a_P,f on outlet faces (Dirichlet
 // through the ghost p_ghost = -p), b = -sum_f s_f A ubar_f with ubar = HbyA on
@@ -207,48 +217,57 @@ __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restric
   return v;
 }
 
-// red-black Gauss-Seidel half sweep of colour col; zero: x is taken as 0
+// fused multiply-add of the level's precision (every smoother spells out the same
+// fma chain, so no value depends on the compiler's contraction choices)
+__device__ __forceinline__ double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+
+// One red-black Gauss-Seidel update of cell c = (i, j, k):
+// x_c = (b_c + sum_nb T x_nb) / diag_c, neighbours in the order x-, x+, y-, y+,
+// z-, z+; zero: the other colour's x is taken as 0.  The batched sweeps and the
+// tail share this function, so a cell's value does not depend on which of them
+// updates it.
 template <typename R>
-__device__ __forceinline__ void b_smooth(const Level<R>& L, int col, int zero, unsigned t) {
-  const unsigned half = (L.n[0] + 1) >> 1;
-  const unsigned rows = (unsigned)L.n[1] * (unsigned)L.n[2];
-  if (t >= rows * half) return;
-  const int ti = (int)(t % half);
-  const unsigned row = t / half;
-  const int j = (int)(row % (unsigned)L.n[1]), k = (int)(row / (unsigned)L.n[1]);
-  const int i = ((j + k + col) & 1) + 2 * ti;
-  if (i >= L.n[0]) return;
-  const long long c = i + (long long)L.n[0] * row;
+__device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* __restrict__ dinv,
+                                            const R* __restrict__ xr, R* __restrict__ xw,
+                                            const R* __restrict__ Tx, const R* __restrict__ Ty,
+                                            const R* __restrict__ Tz, int n0, int n1, int n2, int i, int j, int k,
+                                            long long c, int zero) {
   if (zero) {
-    L.x[c] = L.b[c] * L.dinv[c];
+    xw[c] = bb[c] * dinv[c];
     return;
   }
-  const int q[3] = {i, j, k};
-  R v = L.b[c] + neighbour_sum(L, L.x, q, c);
-  L.x[c] = v * L.dinv[c];
+  const long long sy = n0, sz = (long long)n0 * n1;
+  R v = bb[c];
+  if (i > 0) v = fma_r(Tx[c - 1], xr[c - 1], v);
+  if (i + 1 < n0) v = fma_r(Tx[c], xr[c + 1], v);
+  if (j > 0) v = fma_r(Ty[c - sy], xr[c - sy], v);
+  if (j + 1 < n1) v = fma_r(Ty[c], xr[c + sy], v);
+  if (k > 0) v = fma_r(Tz[c - sz], xr[c - sz], v);
+  if (k + 1 < n2) v = fma_r(Tz[c], xr[c + sz], v);
+  xw[c] = v * dinv[c];
 }
 
-// Skips domains whose CG has converged (the V-cycle only runs inside CG
-// iterations).  The level's arrays go to restrict-qualified registers once per
+// Red-black half sweep of colour col over REP rows of kBlock half-row cells per
+// work item.  Skips domains whose CG has converged (the V-cycle only runs inside
+// CG iterations).  The level's arrays go to restrict-qualified registers once per
 // work item so that the REP rows of an item overlap their loads: the colour being
 // written and the colour being read are disjoint cells of the same array.
 template <typename R, int REP>
-__global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero) {
-  FOR_WORK(w)
+__global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>& Lr = levels_of<R>(G)[l];
     const int n0 = Lr.n[0], n1 = Lr.n[1], n2 = Lr.n[2];
     const R* __restrict__ bb = Lr.b;
     const R* __restrict__ dinv = Lr.dinv;
-    const R* __restrict__ xr = Lr.x;
-    R* __restrict__ xw = Lr.x;
+    R* __restrict__ x = Lr.x;
     const R* __restrict__ Tx = Lr.T[0];
     const R* __restrict__ Ty = Lr.T[1];
     const R* __restrict__ Tz = Lr.T[2];
     const unsigned half = (n0 + 1) >> 1;
     const unsigned total = half * (unsigned)n1 * (unsigned)n2;
-    const long long sy = n0, sz = (long long)n0 * n1;
 #pragma unroll
     for (int r = 0; r < REP; r++) {
       const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
@@ -259,31 +278,131 @@ __global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, in
       const int i = ((j + k + col) & 1) + 2 * ti;
       if (i >= n0) continue;
       const long long c = i + (long long)n0 * row;
-      if (zero) {
-        xw[c] = bb[c] * dinv[c];
-        continue;
-      }
-      R v = bb[c];
-      if (i > 0) v += Tx[c - 1] * xr[c - 1];
-      if (i + 1 < n0) v += Tx[c] * xr[c + 1];
-      if (j > 0) v += Ty[c - sy] * xr[c - sy];
-      if (j + 1 < n1) v += Ty[c] * xr[c + sy];
-      if (k > 0) v += Tz[c - sz] * xr[c - sz];
-      if (k + 1 < n2) v += Tz[c] * xr[c + sz];
-      xw[c] = v * dinv[c];
+      smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
     }
   }
 }
 
+// Fused red-black sweep: colour c1 everywhere, then the other colour, in one pass
+// over the level.  A CTA of kSweepBX x kSweepBY threads owns kSweepTX x kSweepTY
+// interior columns (one thread per column, plus a one-column halo ring) and marches
+// over a chunk [z0, z1) of kz planes.  At plane k it computes the first colour on
+// the interior and halo columns (old values of the other colour from x_in), keeps
+// them in shared memory, and computes the second colour on plane k - 1 of the
+// interior columns from those (the in-plane neighbours at the tile edge are the
+// halo values, the z neighbours planes k - 2 and k).  The first colour is therefore
+// computed twice on halo columns and on the chunk's end planes z0 - 1 and z1, with
+// identical inputs and arithmetic.  x_in is read and x_out written once per cell:
+// half the traffic of two half sweeps.  Each cell's arithmetic is smooth_cell's.
 template <typename R>
-__global__ void k_zero(const CgDom* __restrict__ C, Work w, int l) {
-  FOR_WORK(w)
+__global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
+    k_smooth_fused(const CgDom* __restrict__ C, Work w, int l, int c1, int zero, int src, int kz) {
+  __shared__ R xs[kSweepBY][kSweepBX];      // x_in of plane k
+  __shared__ R txs[3][kSweepBY][kSweepBX];  // T_x of planes k - 2 .. k (slot plane % 3)
+  __shared__ R tys[3][kSweepBY][kSweepBX];  // T_y
+  __shared__ R s1[3][kSweepBY][kSweepBX];   // new first-colour values
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  for (int b_ = blockIdx.x; b_ < w.total; b_ += gridDim.x) {
+    const int dm = work_domain(w, b_);
+    const int lb = b_ - w.blk[dm];
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;  // the same for the whole block
+    const Level<R>& L = levels_of<R>(G)[l];
+    const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+    const R* __restrict__ bb = L.b;
+    const R* __restrict__ dinv = L.dinv;
+    const R* __restrict__ Tx = L.T[0];
+    const R* __restrict__ Ty = L.T[1];
+    const R* __restrict__ Tz = L.T[2];
+    const R* __restrict__ xin = src ? L.x2 : L.x;
+    R* __restrict__ xout = src ? L.x : L.x2;
+    const int ntx = (n0 + kSweepTX - 1) / kSweepTX, nty = (n1 + kSweepTY - 1) / kSweepTY;
+    const int rr = lb / ntx;
+    const int i = (lb - rr * ntx) * kSweepTX - 1 + tx;
+    const int j = (rr % nty) * kSweepTY - 1 + ty;
+    const int z0 = (rr / nty) * kz, z1 = min(z0 + kz, n2);
+    const bool inside = i >= 0 && i < n0 && j >= 0 && j < n1;
+    const bool interior = inside && tx >= 1 && tx <= kSweepTX && ty >= 1 && ty <= kSweepTY;
+    // 32-bit cell indices (levels stay below 2^31 cells); plane -1 wraps but is never read
+    const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
+    const unsigned col = inside ? (unsigned)i + sy * (unsigned)j : 0u;  // this column's cell on plane 0
+    // registers: x_in of planes k - 1, k; T_z of planes k - 2, k - 1; b, 1/diag of plane k - 1
+    R xm = R(0), x0 = R(0), tzmm = R(0), tzm = R(0), bm = R(0), dm1 = R(0);
+    if (inside && !zero) {
+      if (z0 - 1 >= 0) x0 = xin[col + sz * (unsigned)(z0 - 1)];
+      if (z0 - 2 >= 0) xm = xin[col + sz * (unsigned)(z0 - 2)];
+    }
+    if (inside && z0 - 2 >= 0) tzm = Tz[col + sz * (unsigned)(z0 - 2)];
+    for (int k = z0 - 1; k <= z1; k++) {
+      const bool plane = k >= 0 && k < n2;
+      const unsigned c = col + sz * (unsigned)k;
+      R b0 = R(0), d0 = R(0), tx0 = R(0), ty0 = R(0), tz0 = R(0), xp = R(0);
+      if (inside && plane) {
+        b0 = bb[c];
+        d0 = dinv[c];
+        tx0 = Tx[c];
+        ty0 = Ty[c];
+        tz0 = Tz[c];
+      }
+      // x_in one plane ahead (also from plane -1 of the first chunk: plane 0)
+      if (inside && !zero && k + 1 >= 0 && k + 1 < n2) xp = xin[c + sz];
+      const int m3 = (k + 3) % 3;
+      xs[ty][tx] = x0;
+      txs[m3][ty][tx] = tx0;
+      tys[m3][ty][tx] = ty0;
+      __syncthreads();
+      if (inside && plane && ((i + j + k) & 1) == c1) {
+        R v = b0;
+        if (!zero) {
+          if (i > 0) v = fma_r(tx > 0 ? txs[m3][ty][tx - 1] : Tx[c - 1], tx > 0 ? xs[ty][tx - 1] : xin[c - 1], v);
+          if (i + 1 < n0) v = fma_r(tx0, tx + 1 < kSweepBX ? xs[ty][tx + 1] : xin[c + 1], v);
+          if (j > 0) v = fma_r(ty > 0 ? tys[m3][ty - 1][tx] : Ty[c - sy], ty > 0 ? xs[ty - 1][tx] : xin[c - sy], v);
+          if (j + 1 < n1) v = fma_r(ty0, ty + 1 < kSweepBY ? xs[ty + 1][tx] : xin[c + sy], v);
+          if (k > 0) v = fma_r(tzm, xm, v);
+          if (k + 1 < n2) v = fma_r(tz0, xp, v);
+        }
+        s1[m3][ty][tx] = v * d0;
+      }
+      __syncthreads();
+      const int km = k - 1;
+      if (interior && km >= z0 && km < z1) {
+        const int p3 = (km + 3) % 3;
+        R out;
+        if (((i + j + km) & 1) == c1) {
+          out = s1[p3][ty][tx];
+        } else {
+          R v = bm;
+          if (i > 0) v = fma_r(txs[p3][ty][tx - 1], s1[p3][ty][tx - 1], v);
+          if (i + 1 < n0) v = fma_r(txs[p3][ty][tx], s1[p3][ty][tx + 1], v);
+          if (j > 0) v = fma_r(tys[p3][ty - 1][tx], s1[p3][ty - 1][tx], v);
+          if (j + 1 < n1) v = fma_r(tys[p3][ty][tx], s1[p3][ty + 1][tx], v);
+          if (km > 0) v = fma_r(tzmm, s1[(km + 2) % 3][ty][tx], v);
+          if (km + 1 < n2) v = fma_r(tzm, s1[m3][ty][tx], v);
+          out = v * dm1;
+        }
+        xout[c - sz] = out;
+      }
+      bm = b0;
+      dm1 = d0;
+      tzmm = tzm;
+      tzm = tz0;
+      xm = x0;
+      x0 = xp;
+    }
+    __syncthreads();  // the next work item reuses the shared planes
+  }
+}
+
+template <typename R>
+__global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>& L = levels_of<R>(G)[l];
+    R* __restrict__ x = sel ? L.x2 : L.x;
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < L.cells) L.x[c] = R(0);
+      if (c < L.cells) x[c] = R(0);
     }
   }
 }
@@ -311,14 +430,16 @@ __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level
 }
 
 template <typename R>
-__global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l) {
-  FOR_WORK(w)
+__global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>* L = levels_of<R>(G);
+    Level<R> Fi = L[l];
+    if (sel) Fi.x = Fi.x2;  // the buffer holding the fine iterate
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < L[l + 1].cells) b_resid_restrict(L[l], L[l + 1], c);
+      if (c < L[l + 1].cells) b_resid_restrict(Fi, L[l + 1], c);
     }
   }
 }
@@ -333,14 +454,16 @@ __device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co
 }
 
 template <typename R>
-__global__ void k_prolong(const CgDom* __restrict__ C, Work w, int l) {
-  FOR_WORK(w)
+__global__ void k_prolong(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const Level<R>* L = levels_of<R>(G);
+    Level<R> Fi = L[l];
+    if (sel) Fi.x = Fi.x2;
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < L[l].cells) b_prolong(L[l], L[l + 1], c);
+      if (c < L[l].cells) b_prolong(Fi, L[l + 1], c);
     }
   }
 }
@@ -411,26 +534,20 @@ __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
 // The small levels (and the coarsest solve) of a V-cycle in one CTA: the same
 // per-cell arithmetic, in the same order, as the per-level kernels above, with
 // __syncthreads() between phases instead of kernel boundaries.
-constexpr int kTailCells = 4096;
 constexpr int kTailThreads = 1024;
 
 template <typename R>
 __device__ void tail_smooth(const Level<R>& L, int col, int zero) {
-  const unsigned half = (L.n[0] + 1) >> 1;
-  const unsigned total = half * (unsigned)L.n[1] * (unsigned)L.n[2];
+  const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
+  const unsigned half = (n0 + 1) >> 1;
+  const unsigned total = half * (unsigned)n1 * (unsigned)n2;
   for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
     const unsigned ti = t % half, row = t / half;
-    const int j = (int)(row % (unsigned)L.n[1]), k = (int)(row / (unsigned)L.n[1]);
+    const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
     const int i = ((j + k + col) & 1) + 2 * (int)ti;
-    if (i >= L.n[0]) continue;
-    const long long c = i + (long long)L.n[0] * row;
-    if (zero) {
-      L.x[c] = L.b[c] * L.dinv[c];
-    } else {
-      const int q[3] = {i, j, k};
-      R v = L.b[c] + neighbour_sum(L, L.x, q, c);
-      L.x[c] = v * L.dinv[c];
-    }
+    if (i >= n0) continue;
+    const long long c = i + (long long)n0 * row;
+    smooth_cell<R>(L.b, L.dinv, L.x, L.x, L.T[0], L.T[1], L.T[2], n0, n1, n2, i, j, k, c, zero);
   }
   __syncthreads();
 }
@@ -560,8 +677,8 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
 }
 
 // q = A d; partial d.q
-__global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
-  FOR_WORK(w)
+__global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const StepDom& S = D[dm];
@@ -597,8 +714,8 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
 }
 
 // p += alpha d; r -= alpha q; partial r.r
-__global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
-  FOR_WORK(w)
+__global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const StepDom& S = D[dm];
@@ -624,8 +741,8 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
 }
 
 // partial r.z and (flexible) z.q
-__global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int with_zq) {
-  FOR_WORK(w)
+__global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int with_zq, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     double rz = 0.0, zq = 0.0;
@@ -650,8 +767,8 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
 }
 
 // d = z + beta d; the first iteration (counter 0) takes d = z
-__global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int flexible) {
-  FOR_WORK(w)
+__global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int flexible, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     const double* scal = G.scal;
@@ -751,8 +868,8 @@ __global__ void k_record(const StepDom* __restrict__ D, const CgDom* __restrict_
 }
 
 // r -> FP32 right-hand side of the FP32 V-cycle; its result -> z
-__global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w) {
-  FOR_WORK(w)
+__global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     for (int r = 0; r < w.rep; r++) {
@@ -761,8 +878,8 @@ __global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w) {
     }
   }
 }
-__global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w) {
-  FOR_WORK(w)
+__global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w, int rev) {
+  FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
     for (int r = 0; r < w.rep; r++) {
@@ -779,16 +896,16 @@ __global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w) {
 struct PressureSolver {
   int precision;
   int nlev;
-  int first;
   Level<double> ld[kMaxLevels];  // FP64 hierarchy (level 0 arrays are borrowed from Fld)
   Level<float> lf[kMaxLevels];   // FP32 hierarchy (mixed precision)
-  double *r, *z, *dv, *q;
+  double *r, *z, *z2, *dv, *q;
   double* partials;
   long long pcap;
   double* scal;
   double* cinv_d;  // inverse of the coarsest operator (FP64 hierarchy)
   float* cinv_f;   // (FP32 hierarchy)
   void* block;     // single device allocation
+  size_t bytes;
 };
 
 static int plan_levels(const int n0[3], int dims[kMaxLevels][3], int cz[kMaxLevels][3]) {
@@ -830,6 +947,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
   const long long pcap = (n0 + kBlock * kRepBig - 1) / (kBlock * kRepBig);
   double* r = (double*)take(n0 * 8);
   double* z = (double*)take(n0 * 8);
+  double* z2 = (double*)take(n0 * 8);
   double* dv = (double*)take(n0 * 8);
   double* q = (double*)take(n0 * 8);
   double* partials = (double*)take(2 * pcap * 8);
@@ -840,6 +958,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     ps->nlev = nlev;
     ps->r = r;
     ps->z = z;
+    ps->z2 = z2;
     ps->dv = dv;
     ps->q = q;
     ps->partials = partials;
@@ -847,10 +966,6 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     ps->scal = scal;
     ps->cinv_d = cinv_d;
     ps->cinv_f = cinv_f;
-    int first = nlev - 1;
-    while (first > 0 && (long long)dims[first - 1][0] * dims[first - 1][1] * dims[first - 1][2] <= kTailCells)
-      first--;
-    ps->first = first;
   }
   for (int l = 0; l < nlev; l++) {
     const long long nc = (long long)dims[l][0] * dims[l][1] * dims[l][2];
@@ -868,6 +983,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
         Ld.diag = (double*)take(nc * 8);
         Ld.dinv = (double*)take(nc * 8);
         Ld.x = (double*)take(nc * 8);
+        Ld.x2 = (double*)take(nc * 8);
         Ld.b = (double*)take(nc * 8);
       }
     } else {
@@ -876,6 +992,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
       Lf.diag = (float*)take(nc * 4);
       Lf.dinv = (float*)take(nc * 4);
       Lf.x = (float*)take(nc * 4);
+      Lf.x2 = (float*)take(nc * 4);
       Lf.b = (float*)take(nc * 4);
     }
     if (ps) {
@@ -905,6 +1022,7 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
     }
   }
   size_t bytes = solver_layout(P.n, ps->precision, nullptr, nullptr);
+  ps->bytes = bytes;
   *err = cudaMalloc(&ps->block, bytes);
   if (*err != cudaSuccess) {
     delete ps;
@@ -923,7 +1041,12 @@ void pressure_destroy(PressureSolver* ps) {
 
 int pressure_precision(const PressureSolver* ps) { return ps->precision; }
 
-void pressure_view(const PressureSolver* ps, const Fld& F, CgDom* out) {
+void pressure_storage(const PressureSolver* ps, void** ptr, size_t* bytes) {
+  *ptr = ps->block;
+  *bytes = ps->bytes;
+}
+
+void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom* out) {
   CgDom& G = *out;
   for (int l = 0; l < kMaxLevels; l++) {
     G.ld[l] = l < ps->nlev ? ps->ld[l] : Level<double>{};
@@ -937,8 +1060,11 @@ void pressure_view(const PressureSolver* ps, const Fld& F, CgDom* out) {
   L0.dinv = F.dinv;
   L0.b = ps->r;
   L0.x = ps->z;
+  L0.x2 = ps->z2;
   G.nlev = ps->nlev;
-  G.first = ps->first;
+  int first = ps->nlev - 1;
+  while (first > 0 && ps->ld[first - 1].cells <= tail_cells) first--;
+  G.first = first;
   G.r = ps->r;
   G.z = ps->z;
   G.dv = ps->dv;
@@ -965,38 +1091,72 @@ static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
   if (direct) MDBS_LAUNCH(K_COARSEN, B.ndom, 256, s, k_coarse_inverse<R>, B.cg);
 }
 
+// Traversal direction of the next kernel over each level; flips at every launch
+// (level 0 is shared by the V-cycle and the CG vector kernels).
+struct Dirs {
+  int l[kMaxLevels] = {};
+  int on;
+  explicit Dirs(int snake) : on(snake) {}
+  int next(int lev) {
+    const int d = l[lev];
+    l[lev] ^= on;
+    return d;
+  }
+};
+
 template <typename R>
-static void smooth_half(const BatchPlan& B, int l, int col, int zero, cudaStream_t s) {
+static void smooth_half(const BatchPlan& B, int l, int col, int zero, Dirs& D, cudaStream_t s) {
   const int id = l == 0 ? K_SMOOTH0 : K_SMOOTHC;
   const Work& w = B.lhalf[l];
-  if (w.rep == kRepBig)
-    MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, kRepBig>), B.cg, w, l, col, zero);
-  else
-    MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 1>), B.cg, w, l, col, zero);
+  const int rev = D.next(l);
+  switch (w.rep) {
+    case 8: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 8>), B.cg, w, l, col, zero, rev); break;
+    case 4: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 4>), B.cg, w, l, col, zero, rev); break;
+    case 2: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 2>), B.cg, w, l, col, zero, rev); break;
+    default: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 1>), B.cg, w, l, col, zero, rev); break;
+  }
 }
 
 template <typename R>
-static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_first, cudaStream_t s) {
-  smooth_half<R>(B, l, first_col, zero_first ? 1 : 0, s);
-  smooth_half<R>(B, l, 1 - first_col, 0, s);
+static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_first, Dirs& D, cudaStream_t s) {
+  smooth_half<R>(B, l, first_col, zero_first ? 1 : 0, D, s);
+  smooth_half<R>(B, l, 1 - first_col, 0, D, s);
+}
+
+// One pre- (first colour 0) or post-smoothing (first colour 1) sweep pair of level l.
+// Fused: one launch from buffer src into the other one; split: two in-place half sweeps.
+template <typename R>
+static void sweep(const BatchPlan& B, int l, int first_col, bool zero, int src, Dirs& D, cudaStream_t s) {
+  if (B.sweep_kz > 0) {
+    const dim3 blk(kSweepBX, kSweepBY);
+    MDBS_LAUNCH(l == 0 ? K_SMOOTH0 : K_SMOOTHC, grid_of(B, B.lsweep[l]), blk, s, k_smooth_fused<R>, B.cg,
+                B.lsweep[l], l, first_col, zero ? 1 : 0, src, B.sweep_kz);
+  } else {
+    smooth_pair<R>(B, l, first_col, zero, D, s);
+  }
 }
 
 // Symmetric V-cycle of every active domain: level 0 receives M r.  Levels that
 // precede a domain's tail start run as batched launches; the rest of each
-// domain's cycle runs in its own CTA of the tail kernel.
+// domain's cycle runs in its own CTA of the tail kernel.  With fused sweeps a
+// batched level's iterate alternates between x and x2: after s of its nu1 + nu2
+// sweeps it is in buffer (nu1 + nu2 - s) % 2 (1: x2), so it ends in x.
 template <typename R>
-static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, cudaStream_t s) {
+static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaStream_t s) {
+  const int S = nu1 + nu2;
+  auto cur = [&](int sw) { return B.sweep_kz > 0 ? (S - sw) & 1 : 0; };
   for (int l = 0; l < B.max_first; l++) {
-    if (nu1 == 0) MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l);
-    for (int it = 0; it < nu1; it++) smooth_pair<R>(B, l, 0, it == 0, s);
+    if (nu1 == 0)
+      MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l, D.next(l), cur(0));
+    for (int it = 0; it < nu1; it++) sweep<R>(B, l, 0, it == 0, cur(it), D, s);
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
-                B.lcoarse[l], l);
+                B.lcoarse[l], l, D.next(l), cur(nu1));
   }
   MDBS_LAUNCH(K_TAIL, B.ndom, kTailThreads, s, k_tail_vcycle<R>, B.cg, nu1, nu2, cs);
   for (int l = B.max_first - 1; l >= 0; l--) {
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_of(B, B.lfine[l]), kBlock, s, k_prolong<R>, B.cg, B.lfine[l],
-                l);
-    for (int it = 0; it < nu2; it++) smooth_pair<R>(B, l, 1, false, s);
+                l, D.next(l), cur(nu1));
+    for (int it = 0; it < nu2; it++) sweep<R>(B, l, 1, false, cur(nu1 + it), D, s);
   }
 }
 
@@ -1030,20 +1190,21 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
   MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   MDBS_LAUNCH(K_ZERO, grid_of(B, B.cells), kBlock, s, k_zero_if_b0, B.sd, B.cg, B.cells);
   // one CG iteration, preconditioner first; the last kernels decide whether to continue
+  Dirs D(B.snake);
   auto body = [&](cudaStream_t bs) {
     if (!flexible) {
-      vcycle<double>(B, nu1, nu2, cs, bs);
+      vcycle<double>(B, nu1, nu2, cs, D, bs);
     } else {
-      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_d2f, B.cg, B.cells);
-      vcycle<float>(B, nu1, nu2, cs, bs);
-      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells);
+      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_d2f, B.cg, B.cells, D.next(0));
+      vcycle<float>(B, nu1, nu2, cs, D, bs);
+      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells, D.next(0));
     }
-    MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.rcells, flexible);
+    MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.rcells, flexible, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 3, flexible, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, k_update_d, B.sd, B.cg, B.rcells, flexible);
-    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.rcells);
+    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, k_update_d, B.sd, B.cg, B.rcells, flexible, D.next(0));
+    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.rcells, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 1, 0, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, k_update_xr, B.sd, B.cg, B.rcells);
+    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, k_update_xr, B.sd, B.cg, B.rcells, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 2, 0, tol, max_it);
     MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   };

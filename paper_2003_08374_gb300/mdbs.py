@@ -51,6 +51,22 @@ _D = C.POINTER(C.c_double)
 _lib = None
 
 
+class Tuning(C.Structure):
+    """Schedule of the multigrid kernels (mdbs_tuning); results do not depend on it."""
+    _fields_ = [("smooth_rows", C.c_int32), ("tail_cells", C.c_int32), ("snake", C.c_int32),
+                ("sweep_kz", C.c_int32)]
+
+    def as_dict(self):
+        return {"smooth_rows": self.smooth_rows, "tail_cells": self.tail_cells, "snake": self.snake,
+                "sweep_kz": self.sweep_kz}
+
+
+def _tuning(t):
+    if isinstance(t, Tuning):
+        return t
+    return Tuning(t["smooth_rows"], t["tail_cells"], t["snake"], t["sweep_kz"])
+
+
 class MdbsError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__("mdbs error %d: %s" % (code, msg))
@@ -90,6 +106,11 @@ def lib():
                                               C.c_void_p, C.c_void_p]
         L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
         L.mdbs_debug_array.restype = C.c_int64
+        for nm in ("mdbs_set_tuning", "mdbs_get_tuning", "mdbs_batch_set_tuning", "mdbs_batch_get_tuning"):
+            getattr(L, nm).argtypes = [C.c_void_p, C.POINTER(Tuning)]
+        for nm in ("mdbs_autotune", "mdbs_batch_autotune"):
+            getattr(L, nm).argtypes = [C.c_void_p, C.c_int32, C.POINTER(Tuning), _D, C.c_int32,
+                                       C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -215,6 +236,20 @@ class Simulation:
     def set_stream(self, stream_handle: int):
         self._check(lib().mdbs_set_stream(self.h, C.c_void_p(stream_handle)))
 
+    def set_tuning(self, tuning):
+        self._check(lib().mdbs_set_tuning(self.h, C.byref(_tuning(tuning))))
+
+    def tuning(self):
+        t = Tuning()
+        self._check(lib().mdbs_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, trial_steps=2):
+        """Times real steps under candidate schedules and keeps the fastest; the state is
+        restored, so the simulation continues as if this had not run.  Returns
+        (chosen schedule, [ms per step of each trial])."""
+        return _autotune(lib().mdbs_autotune, self.h, trial_steps, self._check)
+
     def close(self):
         if getattr(self, "h", None):
             lib().mdbs_destroy(self.h)
@@ -225,6 +260,14 @@ class Simulation:
             self.close()
         except Exception:
             pass
+
+
+def _autotune(fn, h, trial_steps, check):
+    chosen = Tuning()
+    ms = np.zeros(32)
+    n = C.c_int32()
+    check(fn(h, int(trial_steps), C.byref(chosen), _ptr(ms), len(ms), C.byref(n)))
+    return chosen.as_dict(), [float(v) for v in ms[: min(n.value, len(ms))]]
 
 
 class Batch:
@@ -247,6 +290,21 @@ class Batch:
 
     def set_stream(self, stream_handle: int):
         lib().mdbs_batch_set_stream(self.h, C.c_void_p(stream_handle))
+
+    def _check(self, rc):
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_batch_last_error(self.h).decode())
+
+    def set_tuning(self, tuning):
+        self._check(lib().mdbs_batch_set_tuning(self.h, C.byref(_tuning(tuning))))
+
+    def tuning(self):
+        t = Tuning()
+        self._check(lib().mdbs_batch_get_tuning(self.h, C.byref(t)))
+        return t.as_dict()
+
+    def autotune(self, trial_steps=1):
+        return _autotune(lib().mdbs_batch_autotune, self.h, trial_steps, self._check)
 
     def close(self):
         if getattr(self, "h", None):

@@ -40,7 +40,7 @@ def test_library_exports_every_declared_function(built):
 def test_binding_struct_layouts_match_header(built):
     from paper_2003_08374_gb300 import mdbs
     structs = {"mdbs_grid": mdbs.Grid, "mdbs_fluids": mdbs.Fluids, "mdbs_closures": mdbs.Closures,
-               "mdbs_options": mdbs.Options, "mdbs_stats": mdbs.Stats}
+               "mdbs_options": mdbs.Options, "mdbs_stats": mdbs.Stats, "mdbs_tuning": mdbs.Tuning}
     prog = '#include <stdio.h>\n#include <stddef.h>\n#include "mdbs.h"\nint main(void){\n'
     for s, cls in structs.items():
         prog += 'printf("%s %%zu\\n", sizeof(%s));\n' % (s, s)

@@ -1,0 +1,123 @@
+"""Execution schedules of the multigrid kernels (mdbs_tuning) and the autotuner.
+A schedule changes only which launches update which cells and in which order the
+CTAs walk them, never a value: fields must be bitwise identical under every
+schedule, and autotuning must leave the simulation exactly where it was."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+SCHEDULES = [
+    {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0},    # default: split half sweeps
+    {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8},    # fused sweeps
+    {"smooth_rows": 2, "tail_cells": 0, "snake": 1, "sweep_kz": 0},       # only the coarsest level in the tail
+    {"smooth_rows": 4, "tail_cells": 512, "snake": 0, "sweep_kz": 4},     # 37 planes: 9 chunks + a ragged one
+    {"smooth_rows": 8, "tail_cells": 0, "snake": 1, "sweep_kz": 32},      # fused down to the 4x3x3 level
+    {"smooth_rows": 8, "tail_cells": 32768, "snake": 1, "sweep_kz": 16},  # all but the finest level in the tail
+]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_08374_gb300.build import build_library
+    build_library()
+
+
+def _case(precision):
+    from paper_2003_08374_gb300 import workloads as W
+    # ragged sizes: levels 61x47x37 -> 31x24x19 -> 16x12x10 -> 8x6x5 -> 4x3x3
+    return W.grf_3d(shape=(61, 47, 37), seed=5, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
+                    precision=precision)
+
+
+def _run(case, schedule, steps=3):
+    from paper_2003_08374_gb300 import mdbs
+    s = mdbs.Simulation(case)
+    if schedule is not None:
+        s.set_tuning(schedule)
+        assert s.tuning() == schedule
+    s.step(steps)
+    out = s.fields(), s.stats()
+    s.close()
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fields_bitwise_identical_under_every_schedule(precision):
+    case = _case(precision)
+    ref_f, ref_s = _run(case, None)
+    assert ref_s["cg_iters_total"] > 0
+    for sch in SCHEDULES:
+        f, st = _run(case, sch)
+        for k in ref_f:
+            assert np.array_equal(ref_f[k], f[k]), (sch, k)
+        assert st["cg_iters"] == ref_s["cg_iters"], sch
+
+
+def test_invalid_schedules_are_rejected():
+    from paper_2003_08374_gb300 import mdbs
+    s = mdbs.Simulation(_case(0))
+    for bad in ({"smooth_rows": 3, "tail_cells": 4096, "snake": 1, "sweep_kz": 8},
+                {"smooth_rows": 8, "tail_cells": 40000, "snake": 1, "sweep_kz": 8},
+                {"smooth_rows": 8, "tail_cells": -1, "snake": 1, "sweep_kz": 8},
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 2, "sweep_kz": 8},
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 6}):
+        with pytest.raises(mdbs.MdbsError) as e:
+            s.set_tuning(bad)
+        assert e.value.code == mdbs.ERR_ARG
+    # still usable with the schedule it had
+    assert s.tuning() == SCHEDULES[0]
+    s.step(1)
+    s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_leaves_the_simulation_where_it_was(precision):
+    from paper_2003_08374_gb300 import mdbs
+    case = _case(precision)
+    a = mdbs.Simulation(case)
+    a.step(1)
+    before = a.stats()
+    chosen, trials = a.autotune(trial_steps=1)
+    assert a.stats() == before
+    assert len(trials) >= 1 + 1 + 4 + 3 and all(t > 0 for t in trials)
+    assert chosen == a.tuning()
+    assert chosen["smooth_rows"] in (1, 2, 4, 8) and chosen["snake"] in (0, 1)
+    a.step(2)
+    b = mdbs.Simulation(case)
+    b.step(3)
+    fa, fb = a.fields(), b.fields()
+    for k in fa:
+        assert np.array_equal(fa[k], fb[k]), k
+    sa, sb = a.stats(), b.stats()
+    for k in ("steps", "time", "cg_iters", "cg_iters_total", "mass"):
+        assert sa[k] == sb[k], k
+    a.close()
+    b.close()
+
+
+def test_batch_schedule_and_autotune_keep_members_identical():
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    cases = [W.darcy_domain((33, 17, 9), seed=21, p_tol=1e-10, max_cg=300),
+             W.darcy_domain((40, 24, 1), seed=22, p_tol=1e-10, max_cg=300),
+             _case(0)]
+    alone = []
+    for c in cases:
+        s = mdbs.Simulation(c)
+        s.step(3)
+        alone.append(s.fields())
+        s.close()
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims)
+    b.set_tuning({"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": 0})
+    b.step(1)
+    chosen, trials = b.autotune(trial_steps=1)
+    assert chosen == b.tuning() and len(trials) >= 5
+    b.step(2)
+    for s, fa in zip(sims, alone):
+        fb = s.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+        assert s.stats()["steps"] == 3
+    b.close()
