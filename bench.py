@@ -313,20 +313,38 @@ def gpu_arm(args):
 
     roof = roofline(prof, case.cells, 8 if args.precision == 0 else 4, fp64=args.precision == 0)
 
-    mixed = None
+    def variant(precision):
+        """The same workload with the FP32 V-cycle (precision 1) or FP32 with BF16 coarse-level
+        coefficients (precision 2) inside FP64 flexible CG."""
+        vcase = case.replace(precision=precision)
+        vsim = mdbs.Simulation(vcase)
+        vsim.set_stream(stream.cuda_stream)
+        vtuning = vsim.tuning() if args.no_autotune else vsim.autotune(trial_steps=2)[0]
+        it0 = vsim.stats()["cg_iters_total"]
+        for _ in range(args.warmup):
+            vsim.step(1)
+        it1 = vsim.stats()["cg_iters_total"]
+        vms, _, _, _, vst = timed(vsim, args.steps, 0)
+        vms = max_over_ranks(vms)
+        vval = case.cells * args.steps * world / (vms / 1e3)
+        out = {"value": vval, "ms_per_step": vms / args.steps, "speedup_vs_fp64": vval / value,
+               "tuning": vtuning, "cg_iters_last_step": vst["cg_iters"],
+               "cg_iters_timed": vst["cg_iters_total"] - it1, "cg_iters_warmup": it1 - it0}
+        vsim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
+        _, vprof, _, _, _ = timed(vsim, args.steps, args.warmup, DOMINANT)
+        out["roofline"] = roofline(vprof, case.cells, 4, fp64=False)
+        vsim.close()
+        return out
+
+    mixed = bf16 = None
     if not args.no_mixed:
-        mcase = case.replace(precision=W.MIXED)
-        msim = mdbs.Simulation(mcase)
-        msim.set_stream(stream.cuda_stream)
-        mtuning = msim.tuning() if args.no_autotune else msim.autotune(trial_steps=2)[0]
-        mms, _, _, _, mst = timed(msim, args.steps, args.warmup)
-        mms = max_over_ranks(mms)
-        mval = case.cells * args.steps * world / (mms / 1e3)
-        msim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
-        _, mprof, _, _, _ = timed(msim, args.steps, args.warmup, DOMINANT)
-        mixed = {"value": mval, "ms_per_step": mms / args.steps, "speedup_vs_fp64": mval / value, "tuning": mtuning,
-                 "cg_iters_last_step": mst["cg_iters"], "roofline": roofline(mprof, case.cells, 4, fp64=False)}
-        msim.close()
+        mixed = variant(W.MIXED)
+        bf16 = variant(W.MIXED_BF16)
+        # BF16 coarse coefficients are kept only while the CG iteration count grows < 10 %
+        growth = bf16["cg_iters_timed"] / max(mixed["cg_iters_timed"], 1) - 1.0
+        bf16["cg_iters_growth_vs_mixed"] = growth
+        bf16["kept"] = growth < 0.10
+        mixed["bf16_coarse"] = bf16
 
     # end to end through the public API with host buffers: each step copies the state in
     # from pinned host memory (mdbs_set_fields), steps, and reads it back (mdbs_get_fields)

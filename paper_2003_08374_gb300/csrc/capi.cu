@@ -558,7 +558,7 @@ size_t mdbs_bytes_required(const mdbs_grid* grid, int32_t precision) {
   if (!grid || grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return 0;
   Layout L = layout_of(grid);
   int n[3] = {grid->nx, grid->ny, grid->nz};
-  return carve(nullptr, L, nullptr) + pressure_bytes(n, precision == 0 ? 0 : 1);
+  return carve(nullptr, L, nullptr) + pressure_bytes(n, precision < 0 || precision > 2 ? 1 : precision);
 }
 
 int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* permeability,

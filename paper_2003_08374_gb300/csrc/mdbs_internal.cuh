@@ -63,13 +63,16 @@ struct Fld {
   double *T[3], *Dd, *diag, *dinv, *b;
 };
 
-// One multigrid level (T is stored per cell for the face towards +axis).
+// One multigrid level (T is stored per cell for the face towards +axis).  In the
+// FP32 hierarchy of MDBS_MIXED_BF16 the coarse levels (l >= 1) keep T as BF16 bit
+// patterns in Tb (T is then NULL); every reader widens them to FP32.
 template <typename R>
 struct Level {
   int n[3];
   int cz[3];  // axis coarsened relative to the finer level
   long long cells;
   R* T[3];
+  uint16_t* Tb[3];
   R* Dd;
   R* diag;
   R* dinv;  // 1 / diag (multiplied in the smoothers instead of dividing)

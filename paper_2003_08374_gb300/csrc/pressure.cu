@@ -6,9 +6,11 @@
 // runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.  Every kernel runs over
 // all domains of a batch (see mdbs_internal.cuh); per-domain CG scalars and
 // convergence flags let converged domains drop out of the remaining iterations.
+#include <cuda_bf16.h>
 #include <math.h>
 
 #include <new>
+#include <type_traits>
 
 #include "mdbs_internal.cuh"
 
@@ -32,6 +34,48 @@ template <>
 __device__ __forceinline__ const Level<double>* levels_of<double>(const CgDom& C) { return C.ld; }
 template <>
 __device__ __forceinline__ const Level<float>* levels_of<float>(const CgDom& C) { return C.lf; }
+
+// ---------------------------------------------------------------- coefficient storage
+// FP32 / FP64 coefficients, or BF16 bit patterns widened exactly to FP32 on load.
+template <typename R>
+struct CoefF {
+  const R* __restrict__ p;
+  __device__ __forceinline__ R operator[](unsigned i) const { return p[i]; }
+};
+struct CoefH {
+  const uint16_t* __restrict__ p;
+  __device__ __forceinline__ float operator[](unsigned i) const { return __uint_as_float((unsigned)p[i] << 16); }
+};
+
+// coefficient d of level L at cell i, whatever its storage
+template <typename R>
+__device__ __forceinline__ R tcoef(const Level<R>& L, int d, unsigned i) {
+  if constexpr (std::is_same<R, float>::value)
+    if (L.Tb[d]) return __uint_as_float((unsigned)L.Tb[d][i] << 16);
+  return L.T[d][i];
+}
+
+// stores coefficient d of level L at cell i (BF16: rounded to nearest even)
+template <typename R>
+__device__ __forceinline__ void tstore(const Level<R>& L, int d, unsigned i, R v) {
+  if constexpr (std::is_same<R, float>::value)
+    if (L.Tb[d]) {
+      L.Tb[d][i] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+      return;
+    }
+  L.T[d][i] = v;
+}
+
+// calls f with the three coefficient readers of level L
+template <typename R, typename F>
+__device__ __forceinline__ void with_coefs(const Level<R>& L, F&& f) {
+  if constexpr (std::is_same<R, float>::value)
+    if (L.Tb[0]) {
+      f(CoefH{L.Tb[0]}, CoefH{L.Tb[1]}, CoefH{L.Tb[2]});
+      return;
+    }
+  f(CoefF<R>{L.T[0]}, CoefF<R>{L.T[1]}, CoefF<R>{L.T[2]});
+}
 
 // CG scalars on the device
 constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6, kRZold = 7, kIt = 8;
@@ -96,7 +140,7 @@ template <typename R>
 __device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], long long c) {
   if (q[d] == 0) return R(0);
   long long o = d == 0 ? 1 : (d == 1 ? (long long)L.n[0] : (long long)L.n[0] * L.n[1]);
-  return L.T[d][c - o];
+  return tcoef(L, d, (unsigned)(c - o));
 }
 
 template <typename R>
@@ -105,7 +149,7 @@ __device__ __forceinline__ void b_diag(const Level<R>& L, long long c) {
   decode3(L.n, c, q[0], q[1], q[2]);
   R dg = R(0);
   for (int d = 0; d < 3; d++) {
-    dg += L.T[d][c];
+    dg += tcoef(L, d, (unsigned)c);
     if (q[d] > 0) dg += coef_lo(L, d, q, c);
   }
   const R dgt = dg + L.Dd[c];
@@ -155,10 +199,9 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
   }
   for (int d = 0; d < 3; d++) {
     if (Q[d] + 1 >= Co.n[d]) {
-      Co.T[d][ci] = R(0);
+      tstore(Co, d, (unsigned)ci, R(0));
       continue;
     }
-    const R* Tf = Fi.T[d];
     int rl[3] = {lo[0], lo[1], lo[2]}, rh[3] = {hi[0], hi[1], hi[2]};
     rl[d] = rh[d] = 0;
     R sum = R(0);
@@ -169,21 +212,21 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
           R inv;
           if (Co.cz[d]) {
             fc[d] = 2 * Q[d] + 1;
-            const R tface = Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+            const R tface = tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
             fc[d] = 2 * Q[d];
-            const R tin_l = Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+            const R tin_l = tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
             inv = R(1) / tface + R(1) / (R(2) * tin_l);
             if (2 * Q[d] + 3 < Fi.n[d]) {
               fc[d] = 2 * Q[d] + 2;
-              inv += R(1) / (R(2) * Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])]);
+              inv += R(1) / (R(2) * tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2])));
             }
           } else {
             fc[d] = Q[d];
-            inv = R(1) / Tf[cell_index(Fi.n, fc[0], fc[1], fc[2])];
+            inv = R(1) / tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
           }
           sum += R(1) / inv;
         }
-    Co.T[d][ci] = sum;
+    tstore(Co, d, (unsigned)ci, sum);
   }
   R dd = R(0);
   for (int z = lo[2]; z <= hi[2]; z++)
@@ -210,8 +253,8 @@ __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restric
   R v = R(0);
   long long o = 1;
   for (int d = 0; d < 3; d++) {
-    if (q[d] > 0) v += L.T[d][c - o] * x[c - o];
-    if (q[d] + 1 < L.n[d]) v += L.T[d][c] * x[c + o];
+    if (q[d] > 0) v += tcoef(L, d, (unsigned)(c - o)) * x[c - o];
+    if (q[d] + 1 < L.n[d]) v += tcoef(L, d, (unsigned)c) * x[c + o];
     o *= L.n[d];
   }
   return v;
@@ -227,12 +270,10 @@ __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(
 // z-, z+; zero: the other colour's x is taken as 0.  The batched sweeps and the
 // tail share this function, so a cell's value does not depend on which of them
 // updates it.
-template <typename R>
+template <typename R, typename CT>
 __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* __restrict__ dinv,
-                                            const R* __restrict__ xr, R* __restrict__ xw,
-                                            const R* __restrict__ Tx, const R* __restrict__ Ty,
-                                            const R* __restrict__ Tz, int n0, int n1, int n2, int i, int j, int k,
-                                            long long c, int zero) {
+                                            const R* __restrict__ xr, R* __restrict__ xw, CT Tx, CT Ty, CT Tz,
+                                            int n0, int n1, int n2, int i, int j, int k, long long c, int zero) {
   if (zero) {
     xw[c] = bb[c] * dinv[c];
     return;
@@ -263,23 +304,22 @@ __global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, in
     const R* __restrict__ bb = Lr.b;
     const R* __restrict__ dinv = Lr.dinv;
     R* __restrict__ x = Lr.x;
-    const R* __restrict__ Tx = Lr.T[0];
-    const R* __restrict__ Ty = Lr.T[1];
-    const R* __restrict__ Tz = Lr.T[2];
     const unsigned half = (n0 + 1) >> 1;
     const unsigned total = half * (unsigned)n1 * (unsigned)n2;
+    with_coefs(Lr, [&](auto Tx, auto Ty, auto Tz) {
 #pragma unroll
-    for (int r = 0; r < REP; r++) {
-      const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
-      if (t >= total) continue;
-      const int ti = (int)(t % half);
-      const unsigned row = t / half;
-      const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
-      const int i = ((j + k + col) & 1) + 2 * ti;
-      if (i >= n0) continue;
-      const long long c = i + (long long)n0 * row;
-      smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
-    }
+      for (int r = 0; r < REP; r++) {
+        const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
+        if (t >= total) continue;
+        const int ti = (int)(t % half);
+        const unsigned row = t / half;
+        const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
+        const int i = ((j + k + col) & 1) + 2 * ti;
+        if (i >= n0) continue;
+        const long long c = i + (long long)n0 * row;
+        smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
+      }
+    });
   }
 }
 
@@ -311,9 +351,6 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
     const R* __restrict__ bb = L.b;
     const R* __restrict__ dinv = L.dinv;
-    const R* __restrict__ Tx = L.T[0];
-    const R* __restrict__ Ty = L.T[1];
-    const R* __restrict__ Tz = L.T[2];
     const R* __restrict__ xin = src ? L.x2 : L.x;
     R* __restrict__ xout = src ? L.x : L.x2;
     const int ntx = (n0 + kSweepTX - 1) / kSweepTX, nty = (n1 + kSweepTY - 1) / kSweepTY;
@@ -332,7 +369,7 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
       if (z0 - 1 >= 0) x0 = xin[col + sz * (unsigned)(z0 - 1)];
       if (z0 - 2 >= 0) xm = xin[col + sz * (unsigned)(z0 - 2)];
     }
-    if (inside && z0 - 2 >= 0) tzm = Tz[col + sz * (unsigned)(z0 - 2)];
+    if (inside && z0 - 2 >= 0) tzm = tcoef(L, 2, col + sz * (unsigned)(z0 - 2));
     for (int k = z0 - 1; k <= z1; k++) {
       const bool plane = k >= 0 && k < n2;
       const unsigned c = col + sz * (unsigned)k;
@@ -340,9 +377,9 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
       if (inside && plane) {
         b0 = bb[c];
         d0 = dinv[c];
-        tx0 = Tx[c];
-        ty0 = Ty[c];
-        tz0 = Tz[c];
+        tx0 = tcoef(L, 0, c);
+        ty0 = tcoef(L, 1, c);
+        tz0 = tcoef(L, 2, c);
       }
       // x_in one plane ahead (also from plane -1 of the first chunk: plane 0)
       if (inside && !zero && k + 1 >= 0 && k + 1 < n2) xp = xin[c + sz];
@@ -354,9 +391,11 @@ __global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
       if (inside && plane && ((i + j + k) & 1) == c1) {
         R v = b0;
         if (!zero) {
-          if (i > 0) v = fma_r(tx > 0 ? txs[m3][ty][tx - 1] : Tx[c - 1], tx > 0 ? xs[ty][tx - 1] : xin[c - 1], v);
+          if (i > 0)
+            v = fma_r(tx > 0 ? txs[m3][ty][tx - 1] : tcoef(L, 0, c - 1), tx > 0 ? xs[ty][tx - 1] : xin[c - 1], v);
           if (i + 1 < n0) v = fma_r(tx0, tx + 1 < kSweepBX ? xs[ty][tx + 1] : xin[c + 1], v);
-          if (j > 0) v = fma_r(ty > 0 ? tys[m3][ty - 1][tx] : Ty[c - sy], ty > 0 ? xs[ty - 1][tx] : xin[c - sy], v);
+          if (j > 0)
+            v = fma_r(ty > 0 ? tys[m3][ty - 1][tx] : tcoef(L, 1, c - sy), ty > 0 ? xs[ty - 1][tx] : xin[c - sy], v);
           if (j + 1 < n1) v = fma_r(ty0, ty + 1 < kSweepBY ? xs[ty + 1][tx] : xin[c + sy], v);
           if (k > 0) v = fma_r(tzm, xm, v);
           if (k + 1 < n2) v = fma_r(tz0, xp, v);
@@ -501,8 +540,8 @@ __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
     int o = 1;
     for (int d = 0; d < 3; d++) {
       if (q[d] + 1 < C.n[d]) {
-        M[c * n + c + o] = -C.T[d][c];
-        M[(c + o) * n + c] = -C.T[d][c];
+        M[c * n + c + o] = -tcoef(C, d, (unsigned)c);
+        M[(c + o) * n + c] = -tcoef(C, d, (unsigned)c);
       }
       o *= C.n[d];
     }
@@ -541,14 +580,16 @@ __device__ void tail_smooth(const Level<R>& L, int col, int zero) {
   const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
   const unsigned half = (n0 + 1) >> 1;
   const unsigned total = half * (unsigned)n1 * (unsigned)n2;
-  for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
-    const unsigned ti = t % half, row = t / half;
-    const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
-    const int i = ((j + k + col) & 1) + 2 * (int)ti;
-    if (i >= n0) continue;
-    const long long c = i + (long long)n0 * row;
-    smooth_cell<R>(L.b, L.dinv, L.x, L.x, L.T[0], L.T[1], L.T[2], n0, n1, n2, i, j, k, c, zero);
-  }
+  with_coefs(L, [&](auto Tx, auto Ty, auto Tz) {
+    for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
+      const unsigned ti = t % half, row = t / half;
+      const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
+      const int i = ((j + k + col) & 1) + 2 * (int)ti;
+      if (i >= n0) continue;
+      const long long c = i + (long long)n0 * row;
+      smooth_cell<R>(L.b, L.dinv, L.x, L.x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
+    }
+  });
   __syncthreads();
 }
 
@@ -986,6 +1027,14 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
         Ld.x2 = (double*)take(nc * 8);
         Ld.b = (double*)take(nc * 8);
       }
+    } else if (precision == 2 && l > 0) {
+      for (int a = 0; a < 3; a++) Lf.Tb[a] = (uint16_t*)take(nc * 2);
+      Lf.Dd = (float*)take(nc * 4);
+      Lf.diag = (float*)take(nc * 4);
+      Lf.dinv = (float*)take(nc * 4);
+      Lf.x = (float*)take(nc * 4);
+      Lf.x2 = (float*)take(nc * 4);
+      Lf.b = (float*)take(nc * 4);
     } else {
       for (int a = 0; a < 3; a++) Lf.T[a] = (float*)take(nc * 4);
       Lf.Dd = (float*)take(nc * 4);
@@ -1011,7 +1060,7 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
     *err = cudaErrorMemoryAllocation;
     return nullptr;
   }
-  ps->precision = precision == 0 ? 0 : 1;
+  ps->precision = precision;
   {
     int dims[kMaxLevels][3], cz[kMaxLevels][3];
     const int nl = plan_levels(P.n, dims, cz);

@@ -67,3 +67,8 @@ def test_bytes_required_is_host_only_and_monotone(built):
     b = mdbs.bytes_required(W.Case(name="b", nx=64, ny=64, nz=64, h=1e-5))
     assert 0 < a < b
     assert b / (64 ** 3) < 1200  # device bytes per cell
+    # mixed precision adds the FP32 hierarchy; BF16 coarse coefficients take 2 bytes, not 4
+    g = W.Case(name="c", nx=64, ny=64, nz=64, h=1e-5)
+    f64, f32, bf = (mdbs.bytes_required(g, precision=p) for p in (0, 1, 2))
+    coarse = sum((64 >> l) ** 3 for l in range(1, 5))  # levels 32^3 .. 4^3
+    assert f64 < f32 and f32 - bf >= 0.99 * 3 * 2 * coarse  # (less 256-byte alignment of the small levels)

@@ -23,7 +23,7 @@ def _cases(precision):
     return cases
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_members_identical_alone_and_batched(precision):
     from paper_2003_08374_gb300 import mdbs
     cases = _cases(precision)

@@ -118,11 +118,13 @@ def test_degenerate_grids(shape):
     check_fields(g, o, TOL64)
 
 
-def test_mixed_precision_matches_fp64_oracle():
-    """FP32 V-cycle inside FP64 flexible CG, solved to 1e-14: within 1e-6 of the FP64 oracle."""
+@pytest.mark.parametrize("precision", [1, 2])
+def test_mixed_precision_matches_fp64_oracle(precision):
+    """FP32 V-cycle (coarse coefficients in BF16 for precision 2) inside FP64 flexible CG,
+    solved to 1e-14: within 1e-6 of the FP64 oracle."""
     from paper_2003_08374_gb300 import workloads as W
     case = W.grf_3d(shape=(24, 20, 16), seed=5, corr_len=4.0, frac_w=4, p_tol=1e-14, max_cg=500,
-                    precision=W.MIXED)
+                    precision=precision)
     g, o = run_both(case, 10)
     check_fields(g, o, TOLMIX)
 

@@ -42,7 +42,7 @@ def _run(case, schedule, steps=3):
     return out
 
 
-@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("precision", [0, 1, 2])
 def test_fields_bitwise_identical_under_every_schedule(precision):
     case = _case(precision)
     ref_f, ref_s = _run(case, None)
