@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
+    ap.add_argument("--schedule", default=None,
+                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8")
     return ap.parse_args()
 
 
@@ -244,6 +246,19 @@ def roofline(prof, cells, word, fp64):
     return out
 
 
+def pick_schedule(obj, args, trial_steps):
+    """The multigrid schedule of a simulation or batch: given (--schedule), default
+    (--no-autotune) or autotuned.  Returns (schedule, per-trial ms per step)."""
+    if args.schedule:
+        kv = dict(item.split("=") for item in args.schedule.split(","))
+        obj.set_tuning({"smooth_rows": int(kv.get("rows", 1)), "tail_cells": int(kv.get("tail", 4096)),
+                        "snake": int(kv.get("snake", 0)), "sweep_kz": int(kv.get("kz", 0))})
+        return obj.tuning(), []
+    if args.no_autotune:
+        return obj.tuning(), []
+    return obj.autotune(trial_steps=trial_steps)
+
+
 def gpu_arm(args):
     import torch
     rank, world, local = dist_info()
@@ -299,7 +314,7 @@ def gpu_arm(args):
     sim = mdbs.Simulation(case)
     sim.set_stream(stream.cuda_stream)
     # schedule of the multigrid kernels picked by timing real steps (state restored after)
-    tuning, tune_ms = (sim.tuning(), []) if args.no_autotune else sim.autotune(trial_steps=2)
+    tuning, tune_ms = pick_schedule(sim, args, trial_steps=2)
     # headline: every step is one CUDA-graph launch (CG loops as device-side WHILE nodes)
     ms, _, clocks, launches, st = timed(sim, args.steps, args.warmup)
     ms = max_over_ranks(ms)
@@ -319,7 +334,7 @@ def gpu_arm(args):
         vcase = case.replace(precision=precision)
         vsim = mdbs.Simulation(vcase)
         vsim.set_stream(stream.cuda_stream)
-        vtuning = vsim.tuning() if args.no_autotune else vsim.autotune(trial_steps=2)[0]
+        vtuning = pick_schedule(vsim, args, trial_steps=2)[0]
         it0 = vsim.stats()["cg_iters_total"]
         for _ in range(args.warmup):
             vsim.step(1)
@@ -418,7 +433,7 @@ def batched_arm(args):
     sims = [mdbs.Simulation(c) for c in cases]
     b = mdbs.Batch(sims)
     b.set_stream(stream.cuda_stream)
-    tuning, tune_ms = (b.tuning(), []) if args.no_autotune else b.autotune(trial_steps=1)
+    tuning, tune_ms = pick_schedule(b, args, trial_steps=1)
     for _ in range(args.warmup):
         b.step(1)
     torch.cuda.synchronize()

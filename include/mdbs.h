@@ -200,10 +200,11 @@ void mdbs_batch_destroy(mdbs_batch* batch);
  *   snake       : 0 or 1; 1 alternates the traversal direction of consecutive
  *                 kernels over one level, so each starts on the cache lines the
  *                 previous one touched last
- *   sweep_kz    : 0, 4, 8, 16 or 32; > 0 runs each red-black sweep pair as ONE fused
- *                 launch over tiles of 30 x 14 columns and chunks of sweep_kz
- *                 planes (every array read once per pair); 0 runs two half sweeps
- *                 (then smooth_rows applies)
+ *   sweep_kz    : 0, 4, 8, 16 or 32; > 0 runs each red-black sweep pair of an FP32
+ *                 level (mixed precisions) as ONE fused launch over tiles of 62 x 14
+ *                 columns and chunks of sweep_kz planes (every array read once per
+ *                 pair); 0, and every FP64 level, runs two half sweeps (then
+ *                 smooth_rows applies)
  * Default: {1, 4096, 0, 0}.  Values outside these sets give MDBS_ERR_ARG.
  */
 typedef struct {
@@ -223,7 +224,8 @@ int mdbs_batch_get_tuning(const mdbs_batch* batch, mdbs_tuning* out);
 /*
  * Picks the fastest schedule for this simulation (or batch) by timing real steps:
  * starting from the current schedule it tries the alternatives of snake, then of
- * smooth_rows, then of tail_cells (coordinate descent), each for one untimed and
+ * sweep_kz (mixed precisions only), then of smooth_rows (when the half sweeps
+ * run), then of tail_cells (coordinate descent), each for one untimed and
  * trial_steps >= 1 timed steps (CUDA events on the simulation's stream), and keeps
  * a change only when it is faster.  The device state (fields, step scalars) is
  * copied aside first and restored after every trial, so the simulation continues

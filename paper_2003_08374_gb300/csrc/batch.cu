@@ -29,6 +29,10 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   // grids cover every work item (one item per block) up to 64 waves of resident
   // blocks; larger spaces loop (grid stride)
   B.grid_cap = sms * (2048 / kBlock) * 64;
+  {
+    cudaError_t e = sweep_kernel_setup();
+    if (e != cudaSuccess) return e;
+  }
   // host block tables: spaces in a fixed order, each ndom + 1 prefix entries
   const int nspace = 5 + 5 * kMaxLevels;
   std::vector<int> tab((size_t)nspace * (ndom + 1), 0);
@@ -58,7 +62,14 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   B.max_first = 0;
   B.max_levels = 0;
   B.any_cfl = 0;
+  B.tail_words = 0;
   for (int d = 0; d < ndom; d++) {
+    long long words = 0;
+    for (int l = cg[d].first; l < cg[d].nlev; l++) {
+      const Level<double>& L = cg[d].ld[l];
+      words += 2LL * L.n[0] * L.n[1] * L.n[2];
+    }
+    B.tail_words = std::max(B.tail_words, words);
     B.max_first = std::max(B.max_first, cg[d].first);
     B.max_levels = std::max(B.max_levels, cg[d].nlev);
     if (sd[d].P.cfl > 0.0) B.any_cfl = 1;
@@ -93,6 +104,8 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   if (e == cudaSuccess) e = cudaMalloc(&B.cg, ndom * sizeof(CgDom));
   if (e == cudaSuccess) e = cudaMemcpy(B.cg, cg, ndom * sizeof(CgDom), cudaMemcpyHostToDevice);
   if (e == cudaSuccess) e = cudaMalloc(&B.any_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B.err_flag, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(B.err_flag, 0, sizeof(int));
   if (e != cudaSuccess) {
     plan_destroy(&B);
     return e;
@@ -126,10 +139,12 @@ void plan_destroy(BatchPlan* B) {
   if (B->sd) cudaFree(B->sd);
   if (B->cg) cudaFree(B->cg);
   if (B->any_flag) cudaFree(B->any_flag);
+  if (B->err_flag) cudaFree(B->err_flag);
   B->table_storage = nullptr;
   B->sd = nullptr;
   B->cg = nullptr;
   B->any_flag = nullptr;
+  B->err_flag = nullptr;
 }
 
 }  // namespace mdbs

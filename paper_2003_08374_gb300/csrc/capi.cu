@@ -384,6 +384,14 @@ cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaSt
 
 const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0};
 
+// whether a kernel of the plan reported a bounded wait that ran out (synchronous read)
+bool plan_failed(const BatchPlan& B) {
+  int h = 0;
+  if (!B.err_flag) return false;
+  if (cudaMemcpy(&h, B.err_flag, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+  return h != 0;
+}
+
 bool valid_tuning(const mdbs_tuning* t) {
   return t && (t->smooth_rows == 1 || t->smooth_rows == 2 || t->smooth_rows == 4 || t->smooth_rows == 8) &&
          t->tail_cells >= 0 && t->tail_cells <= kTailCellsMax && (t->snake == 0 || t->snake == 1) &&
@@ -470,7 +478,7 @@ struct Snapshot {
 template <typename Setup>
 int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_options& opt, Profiler& prof,
                   cudaStream_t stream, mdbs_tuning& tun, Setup setup, int steps, double* trial_ms, int capacity,
-                  int* ntrials, std::string& err) {
+                  int* ntrials, std::string& err, bool fp32_levels) {
   Snapshot snap;
   cudaError_t e = snap.take(sims, stream);
   if (e != cudaSuccess) {
@@ -505,13 +513,15 @@ int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_optio
   mdbs_tuning best = tun;
   double best_ms = 0.0;
   e = trial(best, &best_ms);
-  // axes in order; smooth_rows only matters for split half sweeps (sweep_kz == 0)
+  // axes in order; smooth_rows only matters for split half sweeps (sweep_kz == 0), and
+  // fused sweeps only exist for FP32 levels
   const int snakes[] = {0, 1};
   const int kzs[] = {0, 4, 8, 16, 32};
   const int rows[] = {1, 2, 4, 8};
   const int tails[] = {0, 512, 4096, 32768};
   for (int axis = 0; axis < 4 && e == cudaSuccess; axis++) {
-    if (axis == 2 && best.sweep_kz > 0) continue;
+    if (axis == 2 && best.sweep_kz > 0 && fp32_levels) continue;
+    if (axis == 1 && !fp32_levels) continue;
     const int* vals = axis == 0 ? snakes : axis == 1 ? kzs : axis == 2 ? rows : tails;
     const int nv = axis == 0 ? 2 : axis == 1 ? 5 : 4;
     const mdbs_tuning base = best;
@@ -725,6 +735,7 @@ int mdbs_step(mdbs_sim* s, int32_t n) {
   CK(exec_steps(s->ex, s->opt, s->prof, s->stream, n));
   s->st.steps += n;
   const int rc = refresh_stats(s);
+  if (plan_failed(s->ex.plan)) return fail(s, MDBS_ERR_CUDA, "a device wait for staged data timed out");
   // kernels launched by the graphs: the fixed part of every step plus the CG bodies run
   if (!eager)
     s->prof.launches += (long long)n * s->ex.static_launches +
@@ -871,7 +882,7 @@ int mdbs_autotune(mdbs_sim* s, int32_t trial_steps, mdbs_tuning* chosen, double*
   mdbs_tuning tun = s->tun;
   int nt = 0;
   const int rc = autotune_impl(one, s->ex, s->opt, s->prof, s->stream, tun, setup, trial_steps, trial_ms, capacity,
-                               &nt, s->err);
+                               &nt, s->err, s->precision != 0);
   if (trials) *trials = nt;
   if (rc == MDBS_OK && chosen) *chosen = s->tun;
   return rc;
@@ -896,7 +907,7 @@ int mdbs_batch_autotune(mdbs_batch* b, int32_t trial_steps, mdbs_tuning* chosen,
   mdbs_tuning tun = b->tun;
   int nt = 0;
   const int rc = autotune_impl(b->sims, b->ex, b->opt, b->prof, b->stream, tun, setup, trial_steps, trial_ms,
-                               capacity, &nt, b->err);
+                               capacity, &nt, b->err, b->sims[0]->precision != 0);
   if (trials) *trials = nt;
   if (rc == MDBS_OK && chosen) *chosen = b->tun;
   return rc;
@@ -930,6 +941,10 @@ int mdbs_batch_step(mdbs_batch* b, int32_t n) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
   if (e != cudaSuccess) {
     b->err = std::string("batch step: ") + cudaGetErrorString(e);
+    return MDBS_ERR_CUDA;
+  }
+  if (plan_failed(b->ex.plan)) {
+    b->err = "a device wait for staged data timed out";
     return MDBS_ERR_CUDA;
   }
   int rc = MDBS_OK;

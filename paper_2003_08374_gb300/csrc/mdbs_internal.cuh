@@ -8,6 +8,7 @@
 // (persistent launch).  Per-domain views (StepDom, CgDom) live in device tables
 // so one launch per phase advances every domain of the batch.
 #pragma once
+#include <cuda.h>  // CUtensorMap (type only; the encoder is fetched through the runtime)
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -123,6 +124,10 @@ struct CgDom {
   double* scal;      // CG scalars
   double* cinv_d;    // inverse of the coarsest operator
   float* cinv_f;
+  // TMA descriptors of the FP32 levels (kTmaMaps per level: x, x2, b, 1/diag, T_x, T_y,
+  // T_z); bit l of tma_levels set when level l has them
+  const CUtensorMap* tmaps;
+  unsigned tma_levels;
 };
 
 // ---------------------------------------------------------------- helpers
@@ -177,12 +182,39 @@ void prof_begin(int id, cudaStream_t s);
 void prof_end(int id, cudaStream_t s);
 long long launch_count();  // kernels launched so far by the active simulation
 
-#define MDBS_LAUNCH(ID, GRID, BLOCK, STREAM, KERNEL, ...)   \
-  do {                                                     \
-    ::mdbs::prof_begin((ID), (STREAM));                    \
-    KERNEL<<<(GRID), (BLOCK), 0, (STREAM)>>>(__VA_ARGS__); \
-    ::mdbs::prof_end((ID), (STREAM));                      \
+//
+// Launches are programmatic dependent launches: a kernel may be scheduled while
+// its predecessor in the stream drains, and every kernel begins with
+// MDBS_DEPENDENT_ENTRY(), which waits until the predecessor grid has completed and
+// its memory is visible (griddepcontrol.wait) before touching any data, then lets
+// its own successor start launching (griddepcontrol.launch_dependents).  The
+// order of all memory effects is therefore the plain stream order; only the launch
+// latency between dependent kernels overlaps (also inside captured graphs).
+#define MDBS_DEPENDENT_ENTRY()                                    \
+  do {                                                            \
+    asm volatile("griddepcontrol.wait;\n" ::: "memory");          \
+    asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); \
   } while (0)
+
+#define MDBS_LAUNCH_SMEM(ID, GRID, BLOCK, SMEM, STREAM, KERNEL, ...)                                \
+  do {                                                                                             \
+    ::mdbs::prof_begin((ID), (STREAM));                                                            \
+    cudaLaunchConfig_t cfg_ = {};                                                                  \
+    cfg_.gridDim = dim3(GRID);                                                                     \
+    cfg_.blockDim = dim3(BLOCK);                                                                   \
+    cfg_.dynamicSmemBytes = (SMEM);                                                                \
+    cfg_.stream = (STREAM);                                                                        \
+    cudaLaunchAttribute at_[1];                                                                    \
+    at_[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;                                \
+    at_[0].val.programmaticStreamSerializationAllowed = 1;                                         \
+    cfg_.attrs = at_;                                                                              \
+    cfg_.numAttrs = 1;                                                                             \
+    cudaLaunchKernelEx(&cfg_, KERNEL, __VA_ARGS__);                                                \
+    ::mdbs::prof_end((ID), (STREAM));                                                              \
+  } while (0)
+
+#define MDBS_LAUNCH(ID, GRID, BLOCK, STREAM, KERNEL, ...) \
+  MDBS_LAUNCH_SMEM(ID, GRID, BLOCK, 0, STREAM, KERNEL, __VA_ARGS__)
 
 // ---------------------------------------------------------------- host-side batch plan
 // Block tables of one batch for every iteration space, uploaded once per
@@ -198,15 +230,17 @@ struct BatchPlan {
   Work lcoarse[kMaxLevels];   // level-(l+1) cells of the same domains (restriction)
   Work lsweep[kMaxLevels];    // fused-sweep tiles (kSweepTX x kSweepTY columns x sweep_kz planes) of the same domains
   int max_first;              // largest tail start over the domains
+  long long tail_words;       // largest x + b element count of a domain's tail levels
   int max_levels;             // largest level count over the domains
   int flexible;               // FP32 V-cycle inside flexible CG
   int any_cfl;                // some domain uses the adaptive time step
   int snake;                  // alternate the traversal direction of consecutive level kernels
-  int sweep_kz;               // > 0: fused red-black sweeps over chunks of this many planes; 0: half sweeps
+  int sweep_kz;               // > 0: fused red-black sweeps (FP32 levels) over chunks of this many planes
   StepDom* sd;                // device tables (ndom entries)
   CgDom* cg;
   int* table_storage;         // device memory of every block table
   int* any_flag;              // device: some domain still iterating (CG WHILE condition)
+  int* err_flag;              // device: a kernel's bounded wait ran out (the batch's results are invalid)
 };
 
 inline int grid_of(const BatchPlan& B, const Work& w) {
@@ -251,9 +285,19 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
 
 // batch.cu
 // builds the block tables and device views of a batch of domains
-// Fused red-black sweep tiles: a CTA of kSweepBX x kSweepBY threads owns the interior
-// kSweepTX x kSweepTY columns plus a one-column halo ring.
-constexpr int kSweepBX = 32, kSweepBY = 16, kSweepTX = kSweepBX - 2, kSweepTY = kSweepBY - 2;
+// Fused red-black sweep tiles (FP32 levels): a CTA of kSweepBX x kSweepBY threads,
+// each owning two adjacent cells of a row, covers kSweepCX x kSweepBY cells: the
+// interior kSweepTX x kSweepTY plus a one-cell halo ring.  Every array of a plane
+// is staged as one box of kBoxX x kBoxY cells starting at (i0 - 4, j0 - 2): the
+// tile, one more ring of cells, and x padding so that the box starts on a
+// 16-byte boundary (i0 is a multiple of 4).
+constexpr int kSweepBX = 32, kSweepBY = 8, kSweepCX = 2 * kSweepBX;
+constexpr int kSweepTX = kSweepCX - 4, kSweepTY = kSweepBY - 2;
+constexpr int kBoxX = kSweepCX + 4, kBoxY = kSweepBY + 2;
+constexpr int kSweepDepth = 2;  // planes staged ahead of use
+constexpr int kTmaMaps = 7;
+// opts the fused-sweep and tail kernels into their shared-memory sizes (current device)
+cudaError_t sweep_kernel_setup();
 
 // smooth_rows: kBlock rows per work item of the finest-level half sweeps (1, 2, 4, 8);
 // sweep_kz: planes per fused-sweep chunk (0: half sweeps)

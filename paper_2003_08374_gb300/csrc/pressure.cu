@@ -6,11 +6,14 @@
 // runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.  Every kernel runs over
 // all domains of a batch (see mdbs_internal.cuh); per-domain CG scalars and
 // convergence flags let converged domains drop out of the remaining iterations.
+#include <cudaTypedefs.h>  // PFN_cuTensorMapEncodeTiled
 #include <cuda_bf16.h>
 #include <math.h>
+#include <string.h>
 
 #include <new>
 #include <type_traits>
+#include <vector>
 
 #include "mdbs_internal.cuh"
 
@@ -127,6 +130,7 @@ __device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long
 }
 
 __global__ void k_assemble(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const StepDom& S = D[dm];
     for (int r = 0; r < w.rep; r++) {
@@ -159,6 +163,7 @@ __device__ __forceinline__ void b_diag(const Level<R>& L, long long c) {
 
 template <typename R>
 __global__ void k_diag(const CgDom* __restrict__ C, Work w, int l) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const Level<R>& L = levels_of<R>(C[dm])[l];
     for (int r = 0; r < w.rep; r++) {
@@ -170,6 +175,7 @@ __global__ void k_diag(const CgDom* __restrict__ C, Work w, int l) {
 
 // FP32 copy of the level-0 operator (mixed precision), with its reciprocal diagonal
 __global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const Level<double>& Ld = C[dm].ld[0];
     const Level<float>& Lf = C[dm].lf[0];
@@ -237,6 +243,7 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
 
 template <typename R>
 __global__ void k_coarsen(const CgDom* __restrict__ C, Work w, int l) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const Level<R>* L = levels_of<R>(C[dm]);
     for (int r = 0; r < w.rep; r++) {
@@ -296,6 +303,7 @@ __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* _
 // written and the colour being read are disjoint cells of the same array.
 template <typename R, int REP>
 __global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -323,117 +331,288 @@ __global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, in
   }
 }
 
-// Fused red-black sweep: colour c1 everywhere, then the other colour, in one pass
-// over the level.  A CTA of kSweepBX x kSweepBY threads owns kSweepTX x kSweepTY
-// interior columns (one thread per column, plus a one-column halo ring) and marches
-// over a chunk [z0, z1) of kz planes.  At plane k it computes the first colour on
-// the interior and halo columns (old values of the other colour from x_in), keeps
-// them in shared memory, and computes the second colour on plane k - 1 of the
-// interior columns from those (the in-plane neighbours at the tile edge are the
-// halo values, the z neighbours planes k - 2 and k).  The first colour is therefore
-// computed twice on halo columns and on the chunk's end planes z0 - 1 and z1, with
-// identical inputs and arithmetic.  x_in is read and x_out written once per cell:
-// half the traffic of two half sweeps.  Each cell's arithmetic is smooth_cell's.
-template <typename R>
-__global__ void __launch_bounds__(kSweepBX* kSweepBY, 2)
-    k_smooth_fused(const CgDom* __restrict__ C, Work w, int l, int c1, int zero, int src, int kz) {
-  __shared__ R xs[kSweepBY][kSweepBX];      // x_in of plane k
-  __shared__ R txs[3][kSweepBY][kSweepBX];  // T_x of planes k - 2 .. k (slot plane % 3)
-  __shared__ R tys[3][kSweepBY][kSweepBX];  // T_y
-  __shared__ R s1[3][kSweepBY][kSweepBX];   // new first-colour values
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  for (int b_ = blockIdx.x; b_ < w.total; b_ += gridDim.x) {
+// ------------------------------------------------------------------ fused red-black sweep (FP32)
+// One launch per sweep pair of an FP32 level: colour c1 everywhere, then the other
+// colour.  A CTA owns an extended tile of kSweepCX x kSweepBY cells (the interior
+// kSweepTX x kSweepTY, a one-cell halo ring, and two spare columns); thread
+// (tx, ty) owns the pair of cells 2 tx, 2 tx + 1 of row ty, so in each colour phase
+// every lane of a warp updates exactly one cell (no checkerboard divergence).  The
+// CTA marches over a chunk [z0, z1) of kz planes: at step k it updates the first
+// colour on plane k of the extended tile from the old iterate, and the second
+// colour on plane k - 2 of the interior from first-colour values of planes k - 3
+// .. k - 1, all finished before the step's barrier (in-plane neighbours at the
+// tile edge are the halo values).  One barrier per plane.  The first colour is
+// computed more than once on the halo ring and the chunk's end planes z0 - 1 and
+// z1, with identical inputs and arithmetic.  The iterate is read from one buffer
+// and written to the other (x <-> x2): each array crosses HBM once per pair, half
+// the traffic of two half sweeps, and each cell's arithmetic is smooth_cell's.
+//
+// Planes reach shared memory kSweepDepth planes ahead of use, in a ring of
+// kSweepDepth + 4 stages (planes k - 2 .. k + 1 are read at step k).  A stage is one
+// kBoxX x kBoxY box per array (x, T_x, T_y, T_z, b, 1/diag) starting at cell
+// (i0 - 4, j0 - 2): TMA tiled copies (cp.async.bulk.tensor) issued by one thread
+// and completing on the stage's mbarrier when the level has tensor maps (FP32
+// coefficients, n_x a multiple of 4), else per-element cp.async by every thread.
+// Cells outside the domain or the plane range are zero-filled and never used.
+// FP64 levels use the half sweeps: GB300's FP64 pipe, not HBM, bounds them.
+constexpr int kBoxN = kBoxX * kBoxY;              // cells per box
+constexpr int kBoxS = (kBoxN + 31) / 32 * 32;     // floats between boxes (128-byte aligned)
+constexpr int kSweepThreads = kSweepBX * kSweepBY;
+constexpr int kStage = 6 * kBoxS;                 // floats per stage
+constexpr int kStages = kSweepDepth + 4;
+constexpr int kRing = 4;                          // planes of first-colour values kept
+constexpr unsigned kBoxBytes = kBoxN * 4u;
+enum { kBoxX_ = 0, kBoxTx = 1, kBoxTy = 2, kBoxTz = 3, kBoxB = 4, kBoxD = 5 };
+static_assert(kBoxS * 4 % 128 == 0, "boxes must stay 128-byte aligned in shared memory");
+static_assert(kSweepTX % 4 == 0, "tile origins must be 16-byte aligned for TMA");
+
+__host__ __device__ constexpr size_t sweep_smem_bytes() {
+  // 128 bytes of alignment slack, the stages, the first-colour ring, the mbarriers
+  return 128 + (size_t)kStages * kStage * 4 + (size_t)kRing * kSweepThreads * 4 + (size_t)kStages * 8;
+}
+
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a stage that has not landed in 1 s is an error
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// asynchronous copy of one float into shared memory (zero-filled when !ok)
+__device__ __forceinline__ void cp_async_f32(float* dst, const float* src, bool ok) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(a), "r"(bytes) : "memory");
+}
+// waits for the phase with the given parity; false when it has not completed within kWaitLimitNs
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(a), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(bar);
+  if (mbar_try(a, parity)) return true;  // the usual case: no clock read
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try(a, parity)) return true;
+    if (global_ns() - t0 > kWaitLimitNs) return false;
+  }
+}
+// one TMA tiled copy of the box at (x, y, z) of the tensor into shared memory
+__device__ __forceinline__ void tma_box(float* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const unsigned b = (unsigned)__cvta_generic_to_shared(bar);
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(d),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(b)
+      : "memory");
+}
+
+// one element of an array into a box: asynchronous for FP32 storage, a plain
+// widening copy for BF16 storage (Tb != NULL)
+__device__ __forceinline__ void stage_el(float* dst, const float* T, const uint16_t* Tb, unsigned g, bool ok) {
+  if (Tb) {
+    *dst = ok ? __uint_as_float((unsigned)Tb[g] << 16) : 0.0f;
+    return;
+  }
+  cp_async_f32(dst, T + g, ok);
+}
+
+__global__ void __launch_bounds__(kSweepThreads, 2)
+    k_smooth_fused(const CgDom* __restrict__ C, Work w, int l, int c1, int zero, int src, int kz, int* err) {
+  MDBS_DEPENDENT_ENTRY();
+  extern __shared__ unsigned char sweep_smem_raw[];
+  float* const base =
+      reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(sweep_smem_raw) + 127) & ~(uintptr_t)127);
+  float* const s1 = base + kStages * kStage;  // first-colour values, slot plane % kRing, one per thread
+  uint64_t* const bars = reinterpret_cast<uint64_t*>(s1 + kRing * kSweepThreads);
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * kSweepBX + tx;
+  if (tid == 0) {
+    for (int s = 0; s < kStages; s++) mbar_init(&bars[s], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  __syncthreads();
+  unsigned phases = 0;  // parity of the next wait on each stage's mbarrier
+  bool failed = false;
+  for (int b_ = blockIdx.x; b_ < w.total && !failed; b_ += gridDim.x) {
     const int dm = work_domain(w, b_);
     const int lb = b_ - w.blk[dm];
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;  // the same for the whole block
-    const Level<R>& L = levels_of<R>(G)[l];
+    const Level<float>& L = G.lf[l];
+    // every pointer in registers: the copies' memory clobbers would otherwise reload
+    // them from the domain table after each copy
     const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
-    const R* __restrict__ bb = L.b;
-    const R* __restrict__ dinv = L.dinv;
-    const R* __restrict__ xin = src ? L.x2 : L.x;
-    R* __restrict__ xout = src ? L.x : L.x2;
+    const float* const xin = src ? L.x2 : L.x;
+    float* const xout = src ? L.x : L.x2;
+    const float* const arr[6] = {xin, L.T[0], L.T[1], L.T[2], L.b, L.dinv};
+    const uint16_t* const half[6] = {nullptr, L.Tb[0], L.Tb[1], L.Tb[2], nullptr, nullptr};
+    const bool tma = (G.tma_levels >> l) & 1u;
+    // the level's maps in the order x, x2, b, 1/diag, T_x, T_y, T_z; box a uses map_idx[a]
+    const CUtensorMap* const maps = G.tmaps;
+    const int mb = l * kTmaMaps;
+    const int map_idx[6] = {mb + (src ? 1 : 0), mb + 4, mb + 5, mb + 6, mb + 2, mb + 3};
     const int ntx = (n0 + kSweepTX - 1) / kSweepTX, nty = (n1 + kSweepTY - 1) / kSweepTY;
     const int rr = lb / ntx;
-    const int i = (lb - rr * ntx) * kSweepTX - 1 + tx;
-    const int j = (rr % nty) * kSweepTY - 1 + ty;
+    const int i0 = (lb - rr * ntx) * kSweepTX, j0 = (rr % nty) * kSweepTY;
     const int z0 = (rr / nty) * kz, z1 = min(z0 + kz, n2);
-    const bool inside = i >= 0 && i < n0 && j >= 0 && j < n1;
-    const bool interior = inside && tx >= 1 && tx <= kSweepTX && ty >= 1 && ty <= kSweepTY;
-    // 32-bit cell indices (levels stay below 2^31 cells); plane -1 wraps but is never read
+    const int ia = i0 - 1 + 2 * tx;  // first cell of this thread's pair
+    const int j = j0 - 1 + ty;
+    const bool row_in = j >= 0 && j < n1;
+    const bool row_interior = row_in && ty >= 1 && ty <= kSweepTY;
+    // 32-bit cell indices (levels stay below 2^31 cells)
     const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
-    const unsigned col = inside ? (unsigned)i + sy * (unsigned)j : 0u;  // this column's cell on plane 0
-    // registers: x_in of planes k - 1, k; T_z of planes k - 2, k - 1; b, 1/diag of plane k - 1
-    R xm = R(0), x0 = R(0), tzmm = R(0), tzm = R(0), bm = R(0), dm1 = R(0);
-    if (inside && !zero) {
-      if (z0 - 1 >= 0) x0 = xin[col + sz * (unsigned)(z0 - 1)];
-      if (z0 - 2 >= 0) xm = xin[col + sz * (unsigned)(z0 - 2)];
-    }
-    if (inside && z0 - 2 >= 0) tzm = tcoef(L, 2, col + sz * (unsigned)(z0 - 2));
-    for (int k = z0 - 1; k <= z1; k++) {
-      const bool plane = k >= 0 && k < n2;
-      const unsigned c = col + sz * (unsigned)k;
-      R b0 = R(0), d0 = R(0), tx0 = R(0), ty0 = R(0), tz0 = R(0), xp = R(0);
-      if (inside && plane) {
-        b0 = bb[c];
-        d0 = dinv[c];
-        tx0 = tcoef(L, 0, c);
-        ty0 = tcoef(L, 1, c);
-        tz0 = tcoef(L, 2, c);
-      }
-      // x_in one plane ahead (also from plane -1 of the first chunk: plane 0)
-      if (inside && !zero && k + 1 >= 0 && k + 1 < n2) xp = xin[c + sz];
-      const int m3 = (k + 3) % 3;
-      xs[ty][tx] = x0;
-      txs[m3][ty][tx] = tx0;
-      tys[m3][ty][tx] = ty0;
-      __syncthreads();
-      if (inside && plane && ((i + j + k) & 1) == c1) {
-        R v = b0;
-        if (!zero) {
-          if (i > 0)
-            v = fma_r(tx > 0 ? txs[m3][ty][tx - 1] : tcoef(L, 0, c - 1), tx > 0 ? xs[ty][tx - 1] : xin[c - 1], v);
-          if (i + 1 < n0) v = fma_r(tx0, tx + 1 < kSweepBX ? xs[ty][tx + 1] : xin[c + 1], v);
-          if (j > 0)
-            v = fma_r(ty > 0 ? tys[m3][ty - 1][tx] : tcoef(L, 1, c - sy), ty > 0 ? xs[ty - 1][tx] : xin[c - sy], v);
-          if (j + 1 < n1) v = fma_r(ty0, ty + 1 < kSweepBY ? xs[ty + 1][tx] : xin[c + sy], v);
-          if (k > 0) v = fma_r(tzm, xm, v);
-          if (k + 1 < n2) v = fma_r(tz0, xp, v);
+    const int a0 = zero ? 1 : 0;  // the zero-guess sweep does not read x
+    auto stage_of = [&](int p) { return base + ((p % kStages) + kStages) % kStages * kStage; };
+
+    // stages plane p into stage p mod kStages
+    auto issue = [&](int p) {
+      const int s = ((p % kStages) + kStages) % kStages;
+      float* st = base + s * kStage;
+      if (tma) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+          mbar_expect_tx(&bars[s], (6 - a0) * kBoxBytes);
+#pragma unroll
+          for (int a = 0; a < 6; a++)
+            if (a >= a0) tma_box(st + a * kBoxS, maps + map_idx[a], i0 - 4, j0 - 2, p, &bars[s]);
         }
-        s1[m3][ty][tx] = v * d0;
-      }
-      __syncthreads();
-      const int km = k - 1;
-      if (interior && km >= z0 && km < z1) {
-        const int p3 = (km + 3) % 3;
-        R out;
-        if (((i + j + km) & 1) == c1) {
-          out = s1[p3][ty][tx];
-        } else {
-          R v = bm;
-          if (i > 0) v = fma_r(txs[p3][ty][tx - 1], s1[p3][ty][tx - 1], v);
-          if (i + 1 < n0) v = fma_r(txs[p3][ty][tx], s1[p3][ty][tx + 1], v);
-          if (j > 0) v = fma_r(tys[p3][ty - 1][tx], s1[p3][ty - 1][tx], v);
-          if (j + 1 < n1) v = fma_r(tys[p3][ty][tx], s1[p3][ty + 1][tx], v);
-          if (km > 0) v = fma_r(tzmm, s1[(km + 2) % 3][ty][tx], v);
-          if (km + 1 < n2) v = fma_r(tzm, s1[m3][ty][tx], v);
-          out = v * dm1;
+      } else {
+        const bool pv = p >= 0 && p < n2;
+        for (int e = tid; e < kBoxN; e += kSweepThreads) {
+          const int by = e / kBoxX, bx = e - by * kBoxX;
+          const int ii = i0 - 4 + bx, jj = j0 - 2 + by;
+          const bool ok = pv && ii >= 0 && ii < n0 && jj >= 0 && jj < n1;
+          const unsigned g = ok ? (unsigned)ii + sy * (unsigned)jj + sz * (unsigned)p : 0u;
+#pragma unroll
+          for (int a = 0; a < 6; a++)
+            if (a >= a0) stage_el(st + a * kBoxS + e, arr[a], half[a], g, ok);
         }
-        xout[c - sz] = out;
+        cp_async_commit();
       }
-      bm = b0;
-      dm1 = d0;
-      tzmm = tzm;
-      tzm = tz0;
-      xm = x0;
-      x0 = xp;
+    };
+    // waits until plane p has landed in its stage (TMA path; the copy path waits by group count)
+    auto land = [&](int p) -> bool {
+      const int s = ((p % kStages) + kStages) % kStages;
+      const bool ok = mbar_wait(&bars[s], (phases >> s) & 1u);
+      phases ^= 1u << s;
+      return ok;
+    };
+
+    for (int p = z0 - 2; p <= z0 - 1 + kSweepDepth; p++) issue(p);
+    bool ok = true;
+    if (tma) ok = land(z0 - 2) && land(z0 - 1);
+    float tzmm = 0.0f;  // T_z on plane m - 1 of the cell that is second colour on plane m = k - 2
+    int k = z0 - 1;
+    for (; k <= z1 + 1 && ok; k++) {
+      if (tma)
+        ok = land(k + 1);
+      else
+        cp_async_wait<kSweepDepth - 1>();  // planes up to k + 1 (this thread's copies)
+      // every thread's copies of plane k + 1 and first-colour values of plane k - 1 are
+      // visible; nothing reads stage k - 3 any more
+      if (__syncthreads_or(!ok)) {
+        ok = false;
+        break;
+      }
+      issue(k + kSweepDepth + 1);
+      // first colour on plane k: the member of the pair with (i + j + k) % 2 == c1
+      if (k <= z1) {
+        const float* Sm = stage_of(k - 1);
+        const float* Sk = stage_of(k);
+        const float* Sp = stage_of(k + 1);
+        const int e1 = 2 * tx + (((ia + j + k) & 1) == c1 ? 0 : 1);
+        const int i1 = i0 - 1 + e1;
+        const int h1 = (ty + 1) * kBoxX + e1 + 3;  // the cell in the boxes
+        if (row_in && i1 >= 0 && i1 < n0 && k >= 0 && k < n2) {
+          float v = Sk[kBoxB * kBoxS + h1];
+          if (!zero) {
+            const float* X = Sk;
+            const float* TX = Sk + kBoxTx * kBoxS;
+            const float* TY = Sk + kBoxTy * kBoxS;
+            if (i1 > 0) v = fma_r(TX[h1 - 1], X[h1 - 1], v);
+            if (i1 + 1 < n0) v = fma_r(TX[h1], X[h1 + 1], v);
+            if (j > 0) v = fma_r(TY[h1 - kBoxX], X[h1 - kBoxX], v);
+            if (j + 1 < n1) v = fma_r(TY[h1], X[h1 + kBoxX], v);
+            if (k > 0) v = fma_r(Sm[kBoxTz * kBoxS + h1], Sm[h1], v);
+            if (k + 1 < n2) v = fma_r(Sk[kBoxTz * kBoxS + h1], Sp[h1], v);
+          }
+          s1[((k + kRing) % kRing) * kSweepThreads + tid] = v * Sk[kBoxD * kBoxS + h1];
+        }
+      }
+      // second colour on plane m = k - 2: the member of the pair that is not first colour
+      const int m = k - 2;
+      const int e2 = 2 * tx + (((ia + j + m) & 1) == c1 ? 1 : 0);
+      const float* Sq = stage_of(m);
+      if (row_interior && m >= z0 && m < z1) {
+        const int h2 = (ty + 1) * kBoxX + e2 + 3;
+        const float* q = s1 + ((m + kRing) % kRing) * kSweepThreads;
+        const int io = i0 - 1 + (e2 ^ 1);  // first-colour member of the pair on plane m
+        if (io >= i0 && io < i0 + kSweepTX && io < n0) xout[(unsigned)io + sy * (unsigned)j + sz * (unsigned)m] = q[tid];
+        const int i2 = i0 - 1 + e2;
+        if (i2 >= i0 && i2 < i0 + kSweepTX && i2 < n0) {
+          const float* TX = Sq + kBoxTx * kBoxS;
+          const float* TY = Sq + kBoxTy * kBoxS;
+          const float left = (e2 & 1) ? q[tid] : q[tid - 1];
+          const float right = (e2 & 1) ? q[tid + 1] : q[tid];
+          float v = Sq[kBoxB * kBoxS + h2];
+          if (i2 > 0) v = fma_r(TX[h2 - 1], left, v);
+          if (i2 + 1 < n0) v = fma_r(TX[h2], right, v);
+          if (j > 0) v = fma_r(TY[h2 - kBoxX], q[tid - kSweepBX], v);
+          if (j + 1 < n1) v = fma_r(TY[h2], q[tid + kSweepBX], v);
+          if (m > 0) v = fma_r(tzmm, s1[((m + kRing - 1) % kRing) * kSweepThreads + tid], v);
+          if (m + 1 < n2) v = fma_r(Sq[kBoxTz * kBoxS + h2], s1[((m + 1) % kRing) * kSweepThreads + tid], v);
+          xout[(unsigned)i2 + sy * (unsigned)j + sz * (unsigned)m] = v * Sq[kBoxD * kBoxS + h2];
+        }
+      }
+      // T_z on plane m of the cell that is second colour on plane m + 1 (the next step's;
+      // needed from m + 1 = z0 on, and plane m has landed from m = z0 - 2 on)
+      if (m >= z0 - 1) {
+        const int e2n = 2 * tx + (((ia + j + m + 1) & 1) == c1 ? 1 : 0);
+        tzmm = Sq[kBoxTz * kBoxS + (ty + 1) * kBoxX + e2n + 3];
+      }
     }
-    __syncthreads();  // the next work item reuses the shared planes
+    // planes staged beyond the chunk: let them land before the stages are reused
+    if (tma) {
+      for (int p = k + 1; p <= k + kSweepDepth && ok; p++) ok = land(p);
+    } else {
+      cp_async_wait<0>();
+    }
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) atomicExch(err, 1);
+      failed = true;
+    }
+  }
+  if (failed) {
+    // an mbarrier wait ran out: wait (bounded) for the copies still in flight on every
+    // stage before the block's shared memory is released
+    for (int s = 0; s < kStages; s++) mbar_wait(&bars[s], (phases >> s) & 1u);
   }
 }
 
 template <typename R>
 __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -470,6 +649,7 @@ __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level
 
 template <typename R>
 __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -494,6 +674,7 @@ __device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co
 
 template <typename R>
 __global__ void k_prolong(const CgDom* __restrict__ C, Work w, int l, int rev, int sel) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -524,6 +705,7 @@ __device__ __forceinline__ float* coarse_inverse_of<float>(const CgDom& G) { ret
 // one block per domain
 template <typename R>
 __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
+  MDBS_DEPENDENT_ENTRY();
   const CgDom& G = CG[blockIdx.x];
   const Level<R> C = levels_of<R>(G)[G.nlev - 1];
   R* __restrict__ inv = coarse_inverse_of<R>(G);
@@ -648,13 +830,36 @@ __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co) {
 }
 
 // one CTA per domain: the domain's levels from its tail start down to the
-// coarsest one and back
+// coarsest one and back.  With smem != 0 the iterates and right-hand sides of those
+// levels live in shared memory for the whole cycle (the coefficients, read-only
+// here, stay in L1): b of the first tail level is copied in, its x copied out.
 template <typename R>
-__global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs) {
+__global__ void __launch_bounds__(kTailThreads)
+    k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs, int smem) {
+  MDBS_DEPENDENT_ENTRY();
+  extern __shared__ __align__(16) unsigned char tail_smem_raw[];
   const CgDom& G = CG[blockIdx.x];
   if (G.scal[kCond] == 0.0) return;
-  const Level<R>* lv = levels_of<R>(G);
+  const Level<R>* gl = levels_of<R>(G);
   const int first = G.first, nlev = G.nlev;
+  __shared__ Level<R> lv[kMaxLevels];  // one copy of the level views for the block
+  if (threadIdx.x == 0) {
+    R* p = reinterpret_cast<R*>(tail_smem_raw);
+    for (int l = first; l < nlev; l++) {
+      lv[l] = gl[l];
+      if (smem) {
+        lv[l].x = p;
+        p += lv[l].cells;
+        lv[l].b = p;
+        p += lv[l].cells;
+      }
+    }
+  }
+  __syncthreads();
+  if (smem) {
+    for (unsigned c = threadIdx.x; c < (unsigned)lv[first].cells; c += blockDim.x) lv[first].b[c] = gl[first].b[c];
+    __syncthreads();
+  }
   for (int l = first; l < nlev - 1; l++) {
     if (nu1 == 0) tail_zero(lv[l]);
     for (int it = 0; it < nu1; it++) tail_pair(lv[l], 0, it == 0);
@@ -677,7 +882,12 @@ __global__ void __launch_bounds__(kTailThreads) k_tail_vcycle(const CgDom* __res
     tail_prolong(lv[l], lv[l + 1]);
     for (int it = 0; it < nu2; it++) tail_pair(lv[l], 1, false);
   }
+  if (smem)
+    for (unsigned c = threadIdx.x; c < (unsigned)lv[first].cells; c += blockDim.x) gl[first].x[c] = lv[first].x[c];
 }
+
+// largest shared-memory footprint the tail takes (beyond it, it works in global memory)
+constexpr size_t kTailSmemMax = 200 * 1024;
 
 // ------------------------------------------------------------------ CG kernels (FP64)
 __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const double* __restrict__ x, long long c,
@@ -694,6 +904,7 @@ __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const dou
 
 // r = b - A p; one partial of r.r and b.b per block
 __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const StepDom& S = D[dm];
     const CgDom& G = C[dm];
@@ -719,6 +930,7 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
 
 // q = A d; partial d.q
 __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -756,6 +968,7 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
 
 // p += alpha d; r -= alpha q; partial r.r
 __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -783,6 +996,7 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
 
 // partial r.z and (flexible) z.q
 __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int with_zq, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -809,6 +1023,7 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
 
 // d = z + beta d; the first iteration (counter 0) takes d = z
 __global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int flexible, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -833,6 +1048,7 @@ __global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restric
 // mode 2: rr after the update; counter += 1
 // mode 3: rz_old = rz; rz (and zq when two channels)
 __global__ void k_finalize(const CgDom* __restrict__ C, Work w, int mode, int two, double tol, int max_it) {
+  MDBS_DEPENDENT_ENTRY();
   const CgDom& G = C[blockIdx.x];
   double* scal = G.scal;
   if (mode != 0 && scal[kCond] == 0.0) return;
@@ -875,6 +1091,7 @@ __global__ void k_finalize(const CgDom* __restrict__ C, Work w, int mode, int tw
 // the host reads (eager loop)
 __global__ void k_any(const CgDom* __restrict__ C, int ndom, int* flag, cudaGraphConditionalHandle handle,
                       int use_handle) {
+  MDBS_DEPENDENT_ENTRY();
   int any = 0;
   for (int d = threadIdx.x; d < ndom; d += blockDim.x) any |= C[d].scal[kCond] != 0.0;
   any = __syncthreads_or(any);
@@ -886,6 +1103,7 @@ __global__ void k_any(const CgDom* __restrict__ C, int ndom, int* flag, cudaGrap
 
 // b = 0 has the solution p = 0 whatever the initial guess
 __global__ void k_zero_if_b0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     if (C[dm].scal[kBB] != 0.0) continue;
     for (int r = 0; r < w.rep; r++) {
@@ -897,6 +1115,7 @@ __global__ void k_zero_if_b0(const StepDom* __restrict__ D, const CgDom* __restr
 
 // iterations and relative residual of corrector corr into each domain's step scalars
 __global__ void k_record(const StepDom* __restrict__ D, const CgDom* __restrict__ C, int corr, double tol) {
+  MDBS_DEPENDENT_ENTRY();
   if (threadIdx.x != 0) return;
   const double* scal = C[blockIdx.x].scal;
   double* step = D[blockIdx.x].scal;
@@ -910,6 +1129,7 @@ __global__ void k_record(const StepDom* __restrict__ D, const CgDom* __restrict_
 
 // r -> FP32 right-hand side of the FP32 V-cycle; its result -> z
 __global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -920,6 +1140,7 @@ __global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w, int rev) {
   }
 }
 __global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w, int rev) {
+  MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
@@ -931,6 +1152,16 @@ __global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w, int rev) {
 }
 
 }  // namespace
+
+cudaError_t sweep_kernel_setup() {
+  cudaError_t e =
+      cudaFuncSetAttribute(k_smooth_fused, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sweep_smem_bytes());
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tail_vcycle<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tail_vcycle<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  return e;
+}
 
 // ------------------------------------------------------------------ solver object
 // Device storage of one domain's pressure solver.
@@ -945,6 +1176,8 @@ struct PressureSolver {
   double* scal;
   double* cinv_d;  // inverse of the coarsest operator (FP64 hierarchy)
   float* cinv_f;   // (FP32 hierarchy)
+  CUtensorMap* tmaps;   // device: TMA descriptors of the FP32 levels (mixed precisions)
+  unsigned tma_levels;  // levels that have them
   void* block;     // single device allocation
   size_t bytes;
 };
@@ -995,6 +1228,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
   double* scal = (double*)take(16 * 8);
   double* cinv_d = (double*)take(kCoarseMax * kCoarseMax * 8);
   float* cinv_f = (float*)take(kCoarseMax * kCoarseMax * 4);
+  CUtensorMap* tmaps = precision != 0 ? (CUtensorMap*)take(kMaxLevels * kTmaMaps * sizeof(CUtensorMap)) : nullptr;
   if (ps) {
     ps->nlev = nlev;
     ps->r = r;
@@ -1007,6 +1241,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     ps->scal = scal;
     ps->cinv_d = cinv_d;
     ps->cinv_f = cinv_f;
+    ps->tmaps = tmaps;
   }
   for (int l = 0; l < nlev; l++) {
     const long long nc = (long long)dims[l][0] * dims[l][1] * dims[l][2];
@@ -1054,6 +1289,48 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
 
 size_t pressure_bytes(const int n[3], int precision) { return solver_layout(n, precision, nullptr, nullptr); }
 
+// The tensor-map encoder of the driver, fetched through the runtime (no libcuda link).
+static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static bool tried = false;
+  if (!tried) {
+    tried = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (PFN_cuTensorMapEncodeTiled_v12000)p;
+  }
+  return fn;
+}
+
+// TMA descriptors (3-D tiled, FP32, box kBoxX x kBoxY x 1, zero fill outside) of every
+// FP32 level whose rows are 16-byte multiples and whose coefficients are stored in
+// FP32; the other levels stage their planes with per-element copies.
+static cudaError_t encode_level_maps(PressureSolver* ps) {
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  ps->tma_levels = 0;
+  if (!enc) return cudaSuccess;
+  std::vector<CUtensorMap> maps((size_t)kMaxLevels * kTmaMaps);
+  memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+  for (int l = 0; l < ps->nlev; l++) {
+    const Level<float>& L = ps->lf[l];
+    if (!L.T[0] || L.n[0] % 4 != 0) continue;
+    const cuuint64_t dims[3] = {(cuuint64_t)L.n[0], (cuuint64_t)L.n[1], (cuuint64_t)L.n[2]};
+    const cuuint64_t strides[2] = {(cuuint64_t)L.n[0] * 4, (cuuint64_t)L.n[0] * L.n[1] * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxY, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    float* const arrays[kTmaMaps] = {L.x, L.x2, L.b, L.dinv, L.T[0], L.T[1], L.T[2]};
+    bool ok = true;
+    for (int a = 0; a < kTmaMaps && ok; a++)
+      ok = enc(&maps[(size_t)l * kTmaMaps + a], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, arrays[a], dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+    if (ok) ps->tma_levels |= 1u << l;
+  }
+  return cudaMemcpy(ps->tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice);
+}
+
 PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
   PressureSolver* ps = new (std::nothrow) PressureSolver();
   if (!ps) {
@@ -1079,6 +1356,7 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
   }
   *err = cudaMemset(ps->block, 0, bytes);
   solver_layout(P.n, ps->precision, ps, (char*)ps->block);
+  if (*err == cudaSuccess && ps->tmaps) *err = encode_level_maps(ps);
   return ps;
 }
 
@@ -1123,6 +1401,8 @@ void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom
   G.scal = ps->scal;
   G.cinv_d = ps->cinv_d;
   G.cinv_f = ps->cinv_f;
+  G.tmaps = ps->tmaps;
+  G.tma_levels = ps->tma_levels;
 }
 
 // ------------------------------------------------------------------ batched host sequencing
@@ -1172,14 +1452,20 @@ static void smooth_pair(const BatchPlan& B, int l, int first_col, bool zero_firs
   smooth_half<R>(B, l, 1 - first_col, 0, D, s);
 }
 
+// Fused sweeps run on the FP32 hierarchy when the schedule asks for them.
+template <typename R>
+static bool fused_sweeps(const BatchPlan& B) {
+  return B.sweep_kz > 0 && std::is_same<R, float>::value;
+}
+
 // One pre- (first colour 0) or post-smoothing (first colour 1) sweep pair of level l.
 // Fused: one launch from buffer src into the other one; split: two in-place half sweeps.
 template <typename R>
 static void sweep(const BatchPlan& B, int l, int first_col, bool zero, int src, Dirs& D, cudaStream_t s) {
-  if (B.sweep_kz > 0) {
+  if (fused_sweeps<R>(B)) {
     const dim3 blk(kSweepBX, kSweepBY);
-    MDBS_LAUNCH(l == 0 ? K_SMOOTH0 : K_SMOOTHC, grid_of(B, B.lsweep[l]), blk, s, k_smooth_fused<R>, B.cg,
-                B.lsweep[l], l, first_col, zero ? 1 : 0, src, B.sweep_kz);
+    MDBS_LAUNCH_SMEM(l == 0 ? K_SMOOTH0 : K_SMOOTHC, grid_of(B, B.lsweep[l]), blk, sweep_smem_bytes(), s,
+                     k_smooth_fused, B.cg, B.lsweep[l], l, first_col, zero ? 1 : 0, src, B.sweep_kz, B.err_flag);
   } else {
     smooth_pair<R>(B, l, first_col, zero, D, s);
   }
@@ -1193,7 +1479,7 @@ static void sweep(const BatchPlan& B, int l, int first_col, bool zero, int src, 
 template <typename R>
 static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaStream_t s) {
   const int S = nu1 + nu2;
-  auto cur = [&](int sw) { return B.sweep_kz > 0 ? (S - sw) & 1 : 0; };
+  auto cur = [&](int sw) { return fused_sweeps<R>(B) ? (S - sw) & 1 : 0; };
   for (int l = 0; l < B.max_first; l++) {
     if (nu1 == 0)
       MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l, D.next(l), cur(0));
@@ -1201,7 +1487,10 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
                 B.lcoarse[l], l, D.next(l), cur(nu1));
   }
-  MDBS_LAUNCH(K_TAIL, B.ndom, kTailThreads, s, k_tail_vcycle<R>, B.cg, nu1, nu2, cs);
+  const size_t tail_bytes = (size_t)B.tail_words * sizeof(R);
+  const int tail_smem = tail_bytes <= kTailSmemMax ? 1 : 0;
+  MDBS_LAUNCH_SMEM(K_TAIL, B.ndom, kTailThreads, tail_smem ? tail_bytes : 0, s, k_tail_vcycle<R>, B.cg, nu1, nu2, cs,
+                   tail_smem);
   for (int l = B.max_first - 1; l >= 0; l--) {
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_of(B, B.lfine[l]), kBlock, s, k_prolong<R>, B.cg, B.lfine[l],
                 l, D.next(l), cur(nu1));

@@ -149,6 +149,7 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
 
 // one partial sum of the boundary inflow per block (deterministic)
 __global__ void k_alpha_flux(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -242,6 +243,7 @@ __device__ __forceinline__ void b_alpha_update(const Prm& P, const Fld& F, long 
 // per domain (one block each): scal[slot] += dt * (deterministic sum of the domain's
 // partials, one per block of the space w)
 __global__ void k_finalize_inflow(const StepDom* __restrict__ D, Work w, int slot) {
+  MDBS_DEPENDENT_ENTRY();
   const StepDom& S = D[blockIdx.x];
   const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
   double v = 0.0;
@@ -495,6 +497,7 @@ __device__ __forceinline__ void b_jacobi(const Prm& P, const Fld& F, long long t
 
 // utmp -> u (after an odd number of Jacobi sweeps)
 __global__ void k_copy_faces(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -547,6 +550,7 @@ __device__ __forceinline__ void b_boundary_velocities(const Prm& P, const Fld& F
 // mass, alpha min / max and a non-finite sentinel: one partial per block in four
 // channels of the domain's partials (stride pcap)
 __global__ void k_field_stats(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   __shared__ double smx[32], smn[32];
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
@@ -589,6 +593,7 @@ __global__ void k_field_stats(const StepDom* __restrict__ D, Work w) {
 
 // per domain (one block each): fold the partials of the cells space into the scalars
 __global__ void k_finalize_stats(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   if (threadIdx.x != 0) return;
   const StepDom& S = D[blockIdx.x];
   const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
@@ -608,6 +613,7 @@ __global__ void k_finalize_stats(const StepDom* __restrict__ D, Work w) {
 
 // max over faces of |u_f| / phi_f (CFL time step, section 3.2), one partial per block
 __global__ void k_cfl(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   __shared__ double sm[32];
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
@@ -638,6 +644,7 @@ __global__ void k_cfl(const StepDom* __restrict__ D, Work w) {
 
 // per domain: time += dt; with cfl > 0 the next dt = min(cfl h / max|u/phi|, 1.2 dt, dt_max)
 __global__ void k_finalize_time(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   if (threadIdx.x != 0) return;
   const StepDom& S = D[blockIdx.x];
   double* scal = S.scal;
@@ -684,6 +691,7 @@ __device__ __forceinline__ void b_static_geometry(const Prm& P, const Fld& F, lo
 }
 
 __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -697,6 +705,7 @@ __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
 
 // ------------------------------------------------------------------ batched entry points
 __global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -709,6 +718,7 @@ __global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_alpha_limit(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -721,6 +731,7 @@ __global__ void k_alpha_limit(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_alpha_update(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -733,6 +744,7 @@ __global__ void k_alpha_update(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_properties(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -745,6 +757,7 @@ __global__ void k_properties(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_normals(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -757,6 +770,7 @@ __global__ void k_normals(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -769,6 +783,7 @@ __global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_momentum_assemble(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -781,6 +796,7 @@ __global__ void k_momentum_assemble(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_jacobi(const StepDom* __restrict__ D, Work w, int parity) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -797,6 +813,7 @@ __global__ void k_jacobi(const StepDom* __restrict__ D, Work w, int parity) {
 }
 
 __global__ void k_hbya(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -809,6 +826,7 @@ __global__ void k_hbya(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_correct(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
@@ -821,6 +839,7 @@ __global__ void k_correct(const StepDom* __restrict__ D, Work w) {
 }
 
 __global__ void k_boundary_velocities(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];

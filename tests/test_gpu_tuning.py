@@ -80,7 +80,8 @@ def test_autotune_leaves_the_simulation_where_it_was(precision):
     before = a.stats()
     chosen, trials = a.autotune(trial_steps=1)
     assert a.stats() == before
-    assert len(trials) >= 1 + 1 + 4 + 3 and all(t > 0 for t in trials)
+    # initial, snake, sweep_kz (mixed only), smooth_rows (split sweeps only), tail_cells
+    assert len(trials) >= 1 + 1 + 3 + 3 and all(t > 0 for t in trials)
     assert chosen == a.tuning()
     assert chosen["smooth_rows"] in (1, 2, 4, 8) and chosen["snake"] in (0, 1)
     a.step(2)
@@ -121,3 +122,18 @@ def test_batch_schedule_and_autotune_keep_members_identical():
             assert np.array_equal(fa[k], fb[k]), k
         assert s.stats()["steps"] == 3
     b.close()
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_fused_sweeps_with_tma_staging_are_bitwise_equal(precision):
+    """Levels whose x extent is a multiple of 4 stage their planes with TMA box copies
+    (124 = 2 x 60 + 4: ragged last tile); the fields must equal the split sweeps'."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(124, 52, 20), seed=9, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
+                    precision=precision)
+    ref_f, ref_s = _run(case, {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0})
+    for kz in (4, 8, 32):
+        f, st = _run(case, {"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": kz})
+        for k in ref_f:
+            assert np.array_equal(ref_f[k], f[k]), (kz, k)
+        assert st["cg_iters"] == ref_s["cg_iters"]
