@@ -57,7 +57,7 @@ def parse():
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
     ap.add_argument("--schedule", default=None,
-                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8")
+                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1")
     return ap.parse_args()
 
 
@@ -252,7 +252,8 @@ def pick_schedule(obj, args, trial_steps):
     if args.schedule:
         kv = dict(item.split("=") for item in args.schedule.split(","))
         obj.set_tuning({"smooth_rows": int(kv.get("rows", 1)), "tail_cells": int(kv.get("tail", 4096)),
-                        "snake": int(kv.get("snake", 0)), "sweep_kz": int(kv.get("kz", 0))})
+                        "snake": int(kv.get("snake", 0)), "sweep_kz": int(kv.get("kz", 0)),
+                        "tail_ctas": int(kv.get("ctas", 1))})
         return obj.tuning(), []
     if args.no_autotune:
         return obj.tuning(), []

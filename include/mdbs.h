@@ -194,24 +194,27 @@ void mdbs_batch_destroy(mdbs_batch* batch);
  * under any schedule; only the time per step changes.
  *   smooth_rows : 1, 2, 4 or 8 rows of 256 cells per CTA work item in the
  *                 finest-level red-black sweeps (fewer rows: more CTAs in flight)
- *   tail_cells  : 0 .. 32768; levels with at most this many cells run, with all
- *                 coarser ones, inside one CTA per domain (fewer launches, less
- *                 parallelism)
+ *   tail_cells  : 0 .. 262144; levels with at most this many cells run, with all
+ *                 coarser ones, inside one kernel with tail_ctas CTAs per domain
+ *                 (fewer launches, less parallelism)
+ *   tail_ctas   : 1, 2, 4 or 8; CTAs of 1024 threads per domain in that kernel (more
+ *                 than one: a thread-block cluster synchronised by cluster barriers)
  *   snake       : 0 or 1; 1 alternates the traversal direction of consecutive
  *                 kernels over one level, so each starts on the cache lines the
  *                 previous one touched last
  *   sweep_kz    : 0, 4, 8, 16 or 32; > 0 runs each red-black sweep pair of an FP32
- *                 level (mixed precisions) as ONE fused launch over tiles of 62 x 14
+ *                 level (mixed precisions) as ONE fused launch over tiles of 60 x 6
  *                 columns and chunks of sweep_kz planes (every array read once per
  *                 pair); 0, and every FP64 level, runs two half sweeps (then
  *                 smooth_rows applies)
- * Default: {1, 4096, 0, 0}.  Values outside these sets give MDBS_ERR_ARG.
+ * Default: {1, 4096, 0, 0, 1}.  Values outside these sets give MDBS_ERR_ARG.
  */
 typedef struct {
   int32_t smooth_rows;
   int32_t tail_cells;
   int32_t snake;
   int32_t sweep_kz;
+  int32_t tail_ctas;
 } mdbs_tuning;
 
 /* Sets or reads the schedule of a simulation that is not in a batch (the step
@@ -225,7 +228,7 @@ int mdbs_batch_get_tuning(const mdbs_batch* batch, mdbs_tuning* out);
  * Picks the fastest schedule for this simulation (or batch) by timing real steps:
  * starting from the current schedule it tries the alternatives of snake, then of
  * sweep_kz (mixed precisions only), then of smooth_rows (when the half sweeps
- * run), then of tail_cells (coordinate descent), each for one untimed and
+ * run), then of (tail_cells, tail_ctas) pairs (coordinate descent), each for one untimed and
  * trial_steps >= 1 timed steps (CUDA events on the simulation's stream), and keeps
  * a change only when it is faster.  The device state (fields, step scalars) is
  * copied aside first and restored after every trial, so the simulation continues

@@ -17,12 +17,13 @@ long long faces_total(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P
 }  // namespace
 
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, BatchPlan* out) {
+                        int sweep_kz, int tail_ctas, BatchPlan* out) {
   BatchPlan B{};
   B.ndom = ndom;
   B.flexible = flexible;
   B.snake = snake;
   B.sweep_kz = sweep_kz;
+  B.tail_ctas = tail_ctas;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

@@ -317,7 +317,7 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
 }
 
 cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible, const mdbs_tuning& t) {
-  cudaError_t e = plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, &ex.plan);
+  cudaError_t e = plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, t.tail_ctas, &ex.plan);
   if (e != cudaSuccess) return e;
   ex.planned = true;
   if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
@@ -382,7 +382,7 @@ cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaSt
   return cudaSuccess;
 }
 
-const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0};
+const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0, 1};
 
 // whether a kernel of the plan reported a bounded wait that ran out (synchronous read)
 bool plan_failed(const BatchPlan& B) {
@@ -395,7 +395,8 @@ bool plan_failed(const BatchPlan& B) {
 bool valid_tuning(const mdbs_tuning* t) {
   return t && (t->smooth_rows == 1 || t->smooth_rows == 2 || t->smooth_rows == 4 || t->smooth_rows == 8) &&
          t->tail_cells >= 0 && t->tail_cells <= kTailCellsMax && (t->snake == 0 || t->snake == 1) &&
-         (t->sweep_kz == 0 || t->sweep_kz == 4 || t->sweep_kz == 8 || t->sweep_kz == 16 || t->sweep_kz == 32);
+         (t->sweep_kz == 0 || t->sweep_kz == 4 || t->sweep_kz == 8 || t->sweep_kz == 16 || t->sweep_kz == 32) &&
+         (t->tail_ctas == 1 || t->tail_ctas == 2 || t->tail_ctas == 4 || t->tail_ctas == 8);
 }
 
 // (re)builds the batch-of-one plan of a simulation for its schedule
@@ -518,18 +519,25 @@ int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_optio
   const int snakes[] = {0, 1};
   const int kzs[] = {0, 4, 8, 16, 32};
   const int rows[] = {1, 2, 4, 8};
-  const int tails[] = {0, 512, 4096, 32768};
+  // (tail_cells, tail_ctas): larger tails want more CTAs
+  const int tails[][2] = {{0, 1}, {512, 1}, {4096, 1}, {4096, 4}, {32768, 4}, {32768, 8}, {262144, 8}};
   for (int axis = 0; axis < 4 && e == cudaSuccess; axis++) {
     if (axis == 2 && best.sweep_kz > 0 && fp32_levels) continue;
     if (axis == 1 && !fp32_levels) continue;
-    const int* vals = axis == 0 ? snakes : axis == 1 ? kzs : axis == 2 ? rows : tails;
-    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : 4;
+    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : axis == 2 ? 4 : 7;
     const mdbs_tuning base = best;
     for (int v = 0; v < nv && e == cudaSuccess; v++) {
       mdbs_tuning t = base;
-      int* field = axis == 0 ? &t.snake : axis == 1 ? &t.sweep_kz : axis == 2 ? &t.smooth_rows : &t.tail_cells;
-      if (*field == vals[v]) continue;
-      *field = vals[v];
+      if (axis == 0) t.snake = snakes[v];
+      if (axis == 1) t.sweep_kz = kzs[v];
+      if (axis == 2) t.smooth_rows = rows[v];
+      if (axis == 3) {
+        t.tail_cells = tails[v][0];
+        t.tail_ctas = tails[v][1];
+      }
+      if (t.snake == base.snake && t.sweep_kz == base.sweep_kz && t.smooth_rows == base.smooth_rows &&
+          t.tail_cells == base.tail_cells && t.tail_ctas == base.tail_ctas)
+        continue;
       double ms = 0.0;
       e = trial(t, &ms);
       if (e == cudaSuccess && ms < best_ms) {

@@ -167,6 +167,28 @@ __device__ __forceinline__ double block_sum(double v) {
   return v;
 }
 
+// warp + block minimum / maximum (order-independent); result valid in thread 0
+template <bool MAX>
+__device__ __forceinline__ double block_minmax(double v) {
+  __shared__ double warp_part[32];
+  for (int o = 16; o > 0; o >>= 1) {
+    const double u = __shfl_down_sync(0xffffffffu, v, o);
+    v = MAX ? fmax(v, u) : fmin(v, u);
+  }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) warp_part[w] = v;
+  __syncthreads();
+  int nw = (blockDim.x + 31) >> 5;
+  v = (threadIdx.x < nw) ? warp_part[threadIdx.x] : (MAX ? -INFINITY : INFINITY);
+  if (w == 0)
+    for (int o = 16; o > 0; o >>= 1) {
+      const double u = __shfl_down_sync(0xffffffffu, v, o);
+      v = MAX ? fmax(v, u) : fmin(v, u);
+    }
+  return v;
+}
+
 // ---------------------------------------------------------------- launch accounting
 // Every kernel launch goes through MDBS_LAUNCH: it counts the launch for the
 // active simulation and, when profiling is on, brackets it with CUDA events on
@@ -231,6 +253,7 @@ struct BatchPlan {
   Work lsweep[kMaxLevels];    // fused-sweep tiles (kSweepTX x kSweepTY columns x sweep_kz planes) of the same domains
   int max_first;              // largest tail start over the domains
   long long tail_words;       // largest x + b element count of a domain's tail levels
+  int tail_ctas;              // CTAs (one cluster) per domain in the tail kernel
   int max_levels;             // largest level count over the domains
   int flexible;               // FP32 V-cycle inside flexible CG
   int any_cfl;                // some domain uses the adaptive time step
@@ -270,7 +293,7 @@ size_t pressure_bytes(const int n[3], int precision);
 void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom* out);
 // the solver's single device allocation
 void pressure_storage(const PressureSolver* ps, void** ptr, size_t* bytes);
-constexpr int kTailCellsMax = 32768;
+constexpr int kTailCellsMax = 262144;
 int pressure_precision(const PressureSolver* ps);
 void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s);
 // Enqueues the solve of A p = b for every domain of the batch by GMG-preconditioned
@@ -300,9 +323,10 @@ constexpr int kTmaMaps = 7;
 cudaError_t sweep_kernel_setup();
 
 // smooth_rows: kBlock rows per work item of the finest-level half sweeps (1, 2, 4, 8);
-// sweep_kz: planes per fused-sweep chunk (0: half sweeps)
+// sweep_kz: planes per fused-sweep chunk (0: half sweeps); tail_ctas: CTAs per domain
+// in the tail kernel (1, 2, 4, 8: one cluster)
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, BatchPlan* out);
+                        int sweep_kz, int tail_ctas, BatchPlan* out);
 void plan_destroy(BatchPlan* B);
 
 }  // namespace mdbs

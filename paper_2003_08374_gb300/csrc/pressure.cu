@@ -752,18 +752,36 @@ __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
 }
 
 // ------------------------------------------------------------------ tail V-cycle
-// The small levels (and the coarsest solve) of a V-cycle in one CTA: the same
-// per-cell arithmetic, in the same order, as the per-level kernels above, with
-// __syncthreads() between phases instead of kernel boundaries.
+// The small levels (and the coarsest solve) of a V-cycle in one CTA, or in one
+// thread-block cluster of up to 8 CTAs, per domain: the same per-cell arithmetic,
+// in the same order, as the per-level kernels above, with a block or cluster
+// barrier between phases instead of kernel boundaries.  The cluster barrier
+// (release / acquire at cluster scope) orders the phases' global-memory writes.
 constexpr int kTailThreads = 1024;
+constexpr int kTailCtasMax = 8;
+
+// this CTA's share of a phase: items rank * blockDim.x + threadIdx.x, step size * blockDim.x
+struct TailPart {
+  unsigned first, step;
+  int size;
+};
+
+__device__ __forceinline__ void tail_barrier(const TailPart& tp) {
+  if (tp.size > 1) {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n" ::: "memory");
+    asm volatile("barrier.cluster.wait.acquire.aligned;\n" ::: "memory");
+  } else {
+    __syncthreads();
+  }
+}
 
 template <typename R>
-__device__ void tail_smooth(const Level<R>& L, int col, int zero) {
+__device__ void tail_smooth(const Level<R>& L, int col, int zero, const TailPart& tp) {
   const int n0 = L.n[0], n1 = L.n[1], n2 = L.n[2];
   const unsigned half = (n0 + 1) >> 1;
   const unsigned total = half * (unsigned)n1 * (unsigned)n2;
   with_coefs(L, [&](auto Tx, auto Ty, auto Tz) {
-    for (unsigned t = threadIdx.x; t < total; t += blockDim.x) {
+    for (unsigned t = tp.first; t < total; t += tp.step) {
       const unsigned ti = t % half, row = t / half;
       const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
       const int i = ((j + k + col) & 1) + 2 * (int)ti;
@@ -772,24 +790,24 @@ __device__ void tail_smooth(const Level<R>& L, int col, int zero) {
       smooth_cell<R>(L.b, L.dinv, L.x, L.x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
     }
   });
-  __syncthreads();
+  tail_barrier(tp);
 }
 
 template <typename R>
-__device__ void tail_pair(const Level<R>& L, int first_col, bool zero_first) {
-  tail_smooth(L, first_col, zero_first ? 1 : 0);
-  tail_smooth(L, 1 - first_col, 0);
+__device__ void tail_pair(const Level<R>& L, int first_col, bool zero_first, const TailPart& tp) {
+  tail_smooth(L, first_col, zero_first ? 1 : 0, tp);
+  tail_smooth(L, 1 - first_col, 0, tp);
 }
 
 template <typename R>
-__device__ void tail_zero(const Level<R>& L) {
-  for (unsigned c = threadIdx.x; c < (unsigned)L.cells; c += blockDim.x) L.x[c] = R(0);
-  __syncthreads();
+__device__ void tail_zero(const Level<R>& L, const TailPart& tp) {
+  for (unsigned c = tp.first; c < (unsigned)L.cells; c += tp.step) L.x[c] = R(0);
+  tail_barrier(tp);
 }
 
 template <typename R>
-__device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co) {
-  for (unsigned ci = threadIdx.x; ci < (unsigned)Co.cells; ci += blockDim.x) {
+__device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
+  for (unsigned ci = tp.first; ci < (unsigned)Co.cells; ci += tp.step) {
     int Q[3];
     Q[0] = (int)(ci % (unsigned)Co.n[0]);
     const unsigned r = ci / (unsigned)Co.n[0];
@@ -811,12 +829,12 @@ __device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co) {
         }
     Co.b[ci] = s;
   }
-  __syncthreads();
+  tail_barrier(tp);
 }
 
 template <typename R>
-__device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co) {
-  for (unsigned c = threadIdx.x; c < (unsigned)Fi.cells; c += blockDim.x) {
+__device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
+  for (unsigned c = tp.first; c < (unsigned)Fi.cells; c += tp.step) {
     int q[3];
     q[0] = (int)(c % (unsigned)Fi.n[0]);
     const unsigned r = c / (unsigned)Fi.n[0];
@@ -826,23 +844,26 @@ __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co) {
     for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
     Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
   }
-  __syncthreads();
+  tail_barrier(tp);
 }
 
-// one CTA per domain: the domain's levels from its tail start down to the
-// coarsest one and back.  With smem != 0 the iterates and right-hand sides of those
-// levels live in shared memory for the whole cycle (the coefficients, read-only
-// here, stay in L1): b of the first tail level is copied in, its x copied out.
+// One CTA or cluster of ctas CTAs per domain (domain = blockIdx.x / ctas): the
+// domain's levels from its tail start down to the coarsest one and back.  With
+// smem != 0 (single CTA only) the iterates and right-hand sides of those levels
+// live in shared memory for the whole cycle (the coefficients, read-only here, stay
+// in L1): b of the first tail level is copied in, its x copied out.
 template <typename R>
 __global__ void __launch_bounds__(kTailThreads)
-    k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs, int smem) {
+    k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs, int smem, int ctas) {
   MDBS_DEPENDENT_ENTRY();
   extern __shared__ __align__(16) unsigned char tail_smem_raw[];
-  const CgDom& G = CG[blockIdx.x];
-  if (G.scal[kCond] == 0.0) return;
+  const CgDom& G = CG[blockIdx.x / ctas];
+  if (G.scal[kCond] == 0.0) return;  // the same for the whole cluster
+  const int rank = blockIdx.x % ctas;
+  const TailPart tp{(unsigned)(rank * blockDim.x + threadIdx.x), (unsigned)(ctas * blockDim.x), ctas};
   const Level<R>* gl = levels_of<R>(G);
   const int first = G.first, nlev = G.nlev;
-  __shared__ Level<R> lv[kMaxLevels];  // one copy of the level views for the block
+  __shared__ Level<R> lv[kMaxLevels];  // one copy of the level views per block
   if (threadIdx.x == 0) {
     R* p = reinterpret_cast<R*>(tail_smem_raw);
     for (int l = first; l < nlev; l++) {
@@ -861,26 +882,26 @@ __global__ void __launch_bounds__(kTailThreads)
     __syncthreads();
   }
   for (int l = first; l < nlev - 1; l++) {
-    if (nu1 == 0) tail_zero(lv[l]);
-    for (int it = 0; it < nu1; it++) tail_pair(lv[l], 0, it == 0);
-    tail_restrict(lv[l], lv[l + 1]);
+    if (nu1 == 0) tail_zero(lv[l], tp);
+    for (int it = 0; it < nu1; it++) tail_pair(lv[l], 0, it == 0, tp);
+    tail_restrict(lv[l], lv[l + 1], tp);
   }
   const Level<R>& C = lv[nlev - 1];
   if (cs == 0) {
     const R* cinv = coarse_inverse_of<R>(G);
     const int n = (int)C.cells;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int i = (int)tp.first; i < n; i += (int)tp.step) {
       R v = R(0);
       for (int j = 0; j < n; j++) v += cinv[i * n + j] * C.b[j];
       C.x[i] = v;
     }
-    __syncthreads();
+    tail_barrier(tp);
   }
-  for (int it = 0; it < cs; it++) tail_pair(C, 0, it == 0);
-  for (int it = 0; it < cs; it++) tail_pair(C, 1, false);
+  for (int it = 0; it < cs; it++) tail_pair(C, 0, it == 0, tp);
+  for (int it = 0; it < cs; it++) tail_pair(C, 1, false, tp);
   for (int l = nlev - 2; l >= first; l--) {
-    tail_prolong(lv[l], lv[l + 1]);
-    for (int it = 0; it < nu2; it++) tail_pair(lv[l], 1, false);
+    tail_prolong(lv[l], lv[l + 1], tp);
+    for (int it = 0; it < nu2; it++) tail_pair(lv[l], 1, false, tp);
   }
   if (smem)
     for (unsigned c = threadIdx.x; c < (unsigned)lv[first].cells; c += blockDim.x) gl[first].x[c] = lv[first].x[c];
@@ -903,14 +924,16 @@ __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const dou
 }
 
 // r = b - A p; one partial of r.r and b.b per block
+template <int REP>
 __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const StepDom& S = D[dm];
     const CgDom& G = C[dm];
     double rr = 0.0, bb = 0.0;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+    #pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < S.P.cells) {
         int q[3];
         decode3(S.P.n, c, q[0], q[1], q[2]);
@@ -929,6 +952,7 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
 }
 
 // q = A d; partial d.q
+template <int REP>
 __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
@@ -944,8 +968,9 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
     const double* __restrict__ Tx = S.F.T[0];
     const double* __restrict__ Ty = S.F.T[1];
     const double* __restrict__ Tz = S.F.T[2];
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+    #pragma unroll 1
+    for (int r = 0; r < REP; r++) {
+      const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         int i, j, k;
         decode3(S.P.n, c, i, j, k);
@@ -967,6 +992,7 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
 }
 
 // p += alpha d; r -= alpha q; partial r.r
+template <int REP>
 __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
@@ -980,8 +1006,9 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
     double* __restrict__ rv = G.r;
     const double* __restrict__ dv = G.dv;
     const double* __restrict__ qv = G.q;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+    #pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         p[c] += al * dv[c];
         const double rc = rv[c] - al * qv[c];
@@ -995,6 +1022,7 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
 }
 
 // partial r.z and (flexible) z.q
+template <int REP>
 __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int with_zq, int rev) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
@@ -1005,8 +1033,9 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
     const double* __restrict__ rv = G.r;
     const double* __restrict__ z = G.z;
     const double* __restrict__ qv = G.q;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+    #pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         rz += rv[c] * z[c];
         if (with_zq) zq += z[c] * qv[c];
@@ -1022,6 +1051,7 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
 }
 
 // d = z + beta d; the first iteration (counter 0) takes d = z
+template <int REP>
 __global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int flexible, int rev) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
@@ -1034,8 +1064,9 @@ __global__ void k_update_d(const StepDom* __restrict__ D, const CgDom* __restric
     const long long n = D[dm].P.cells;
     const double* __restrict__ z = G.z;
     double* __restrict__ dv = G.dv;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+    #pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) dv[c] = first ? z[c] : z[c] + be * dv[c];
     }
   }
@@ -1487,10 +1518,28 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
                 B.lcoarse[l], l, D.next(l), cur(nu1));
   }
+  const int ctas = B.tail_ctas;
   const size_t tail_bytes = (size_t)B.tail_words * sizeof(R);
-  const int tail_smem = tail_bytes <= kTailSmemMax ? 1 : 0;
-  MDBS_LAUNCH_SMEM(K_TAIL, B.ndom, kTailThreads, tail_smem ? tail_bytes : 0, s, k_tail_vcycle<R>, B.cg, nu1, nu2, cs,
-                   tail_smem);
+  const int tail_smem = ctas == 1 && tail_bytes <= kTailSmemMax ? 1 : 0;
+  {
+    prof_begin(K_TAIL, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B.ndom * ctas);
+    cfg.blockDim = dim3(kTailThreads);
+    cfg.dynamicSmemBytes = tail_smem ? tail_bytes : 0;
+    cfg.stream = s;
+    cudaLaunchAttribute at[2];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    at[1].id = cudaLaunchAttributeClusterDimension;
+    at[1].val.clusterDim.x = ctas;
+    at[1].val.clusterDim.y = 1;
+    at[1].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 2;
+    cudaLaunchKernelEx(&cfg, k_tail_vcycle<R>, B.cg, nu1, nu2, cs, tail_smem, ctas);
+    prof_end(K_TAIL, s);
+  }
   for (int l = B.max_first - 1; l >= 0; l--) {
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_of(B, B.lfine[l]), kBlock, s, k_prolong<R>, B.cg, B.lfine[l],
                 l, D.next(l), cur(nu1));
@@ -1523,7 +1572,7 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
   }
   const int use = capture ? 1 : 0;
   // initial residual and loop condition
-  MDBS_LAUNCH(K_RESID0, grid_of(B, B.rcells), kBlock, s, k_resid0, B.sd, B.cg, B.rcells);
+  MDBS_LAUNCH(K_RESID0, grid_of(B, B.rcells), kBlock, s, (k_resid0<kRepBig>), B.sd, B.cg, B.rcells);
   MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize, B.cg, B.rcells, 0, 1, tol, max_it);
   MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   MDBS_LAUNCH(K_ZERO, grid_of(B, B.cells), kBlock, s, k_zero_if_b0, B.sd, B.cg, B.cells);
@@ -1537,12 +1586,12 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
       vcycle<float>(B, nu1, nu2, cs, D, bs);
       MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells, D.next(0));
     }
-    MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, k_dots_rz, B.sd, B.cg, B.rcells, flexible, D.next(0));
+    MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, (k_dots_rz<kRepBig>), B.sd, B.cg, B.rcells, flexible, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 3, flexible, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, k_update_d, B.sd, B.cg, B.rcells, flexible, D.next(0));
-    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, k_spmv_dot, B.sd, B.cg, B.rcells, D.next(0));
+    MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, (k_update_d<kRepBig>), B.sd, B.cg, B.rcells, flexible, D.next(0));
+    MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, (k_spmv_dot<kRepBig>), B.sd, B.cg, B.rcells, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 1, 0, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, k_update_xr, B.sd, B.cg, B.rcells, D.next(0));
+    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, (k_update_xr<kRepBig>), B.sd, B.cg, B.rcells, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 2, 0, tol, max_it);
     MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   };

@@ -594,21 +594,28 @@ __global__ void k_field_stats(const StepDom* __restrict__ D, Work w) {
 // per domain (one block each): fold the partials of the cells space into the scalars
 __global__ void k_finalize_stats(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
-  if (threadIdx.x != 0) return;
+  // one block per domain; each thread folds a fixed stride of the partials and the
+  // block combines them in a fixed tree (deterministic sums)
   const StepDom& S = D[blockIdx.x];
   const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
   const long long pc = S.pcap;
   double mass = 0.0, amin = INFINITY, amax = -INFINITY, bad = 0.0;
-  for (int b = 0; b < nb; b++) {
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
     mass += S.partials[b];
     amin = fmin(amin, S.partials[pc + b]);
     amax = fmax(amax, S.partials[2 * pc + b]);
     bad += S.partials[3 * pc + b];
   }
-  S.scal[kSlotMass] = mass;
-  S.scal[kSlotAmin] = amin;
-  S.scal[kSlotAmax] = amax;
-  S.scal[kSlotBad] = bad;
+  mass = block_sum(mass);
+  bad = block_sum(bad);
+  amin = block_minmax<false>(amin);
+  amax = block_minmax<true>(amax);
+  if (threadIdx.x == 0) {
+    S.scal[kSlotMass] = mass;
+    S.scal[kSlotAmin] = amin;
+    S.scal[kSlotAmax] = amax;
+    S.scal[kSlotBad] = bad;
+  }
 }
 
 // max over faces of |u_f| / phi_f (CFL time step, section 3.2), one partial per block
@@ -645,15 +652,19 @@ __global__ void k_cfl(const StepDom* __restrict__ D, Work w) {
 // per domain: time += dt; with cfl > 0 the next dt = min(cfl h / max|u/phi|, 1.2 dt, dt_max)
 __global__ void k_finalize_time(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
-  if (threadIdx.x != 0) return;
   const StepDom& S = D[blockIdx.x];
   double* scal = S.scal;
   const double dt = scal[kSlotDt];
-  scal[kSlotTime] += dt;
-  if (!(S.P.cfl > 0.0)) return;
+  if (!(S.P.cfl > 0.0)) {
+    if (threadIdx.x == 0) scal[kSlotTime] += dt;
+    return;
+  }
   const int nb = w.blk[blockIdx.x + 1] - w.blk[blockIdx.x];
   double a = 0.0;
-  for (int b = 0; b < nb; b++) a = fmax(a, S.partials[b]);
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) a = fmax(a, S.partials[b]);
+  a = block_minmax<true>(a);
+  if (threadIdx.x != 0) return;
+  scal[kSlotTime] += dt;
   scal[kSlotUmax] = a;
   double dtn = a > 0.0 ? S.P.cfl * S.P.h / a : S.P.dt_max;
   dtn = fmin(dtn, 1.2 * dt);
@@ -891,12 +902,12 @@ void launch_set_boundary_velocities(const BatchPlan& B, cudaStream_t s) {
 
 void launch_field_stats(const BatchPlan& B, cudaStream_t s) {
   BATCH_LAUNCH(K_STATS, rcells, k_field_stats);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_stats, B.sd, B.rcells);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_stats, B.sd, B.rcells);
 }
 
 void launch_time_advance(const BatchPlan& B, cudaStream_t s) {
   if (B.any_cfl) BATCH_LAUNCH(K_CFL, rfaces, k_cfl);
-  MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_finalize_time, B.sd, B.rfaces);
+  MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_time, B.sd, B.rfaces);
 }
 
 void launch_static_geometry(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_STATIC, cells, k_static_geometry); }

@@ -8,12 +8,13 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 SCHEDULES = [
-    {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0},    # default: split half sweeps
-    {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8},    # fused sweeps
-    {"smooth_rows": 2, "tail_cells": 0, "snake": 1, "sweep_kz": 0},       # only the coarsest level in the tail
-    {"smooth_rows": 4, "tail_cells": 512, "snake": 0, "sweep_kz": 4},     # 37 planes: 9 chunks + a ragged one
-    {"smooth_rows": 8, "tail_cells": 0, "snake": 1, "sweep_kz": 32},      # fused down to the 4x3x3 level
-    {"smooth_rows": 8, "tail_cells": 32768, "snake": 1, "sweep_kz": 16},  # all but the finest level in the tail
+    {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0, "tail_ctas": 1},    # default
+    {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 1},    # fused sweeps
+    {"smooth_rows": 2, "tail_cells": 0, "snake": 1, "sweep_kz": 0, "tail_ctas": 2},       # coarsest only, 2 CTAs
+    {"smooth_rows": 4, "tail_cells": 512, "snake": 0, "sweep_kz": 4, "tail_ctas": 4},     # 37 planes: ragged chunks
+    {"smooth_rows": 8, "tail_cells": 0, "snake": 1, "sweep_kz": 32, "tail_ctas": 1},      # fused down to 4x3x3
+    {"smooth_rows": 8, "tail_cells": 32768, "snake": 1, "sweep_kz": 16, "tail_ctas": 1},  # all but level 0, one CTA
+    {"smooth_rows": 1, "tail_cells": 262144, "snake": 0, "sweep_kz": 0, "tail_ctas": 8},  # all but level 0, cluster
 ]
 
 
@@ -58,10 +59,12 @@ def test_invalid_schedules_are_rejected():
     from paper_2003_08374_gb300 import mdbs
     s = mdbs.Simulation(_case(0))
     for bad in ({"smooth_rows": 3, "tail_cells": 4096, "snake": 1, "sweep_kz": 8},
-                {"smooth_rows": 8, "tail_cells": 40000, "snake": 1, "sweep_kz": 8},
+                {"smooth_rows": 8, "tail_cells": 300000, "snake": 1, "sweep_kz": 8},
                 {"smooth_rows": 8, "tail_cells": -1, "snake": 1, "sweep_kz": 8},
                 {"smooth_rows": 8, "tail_cells": 4096, "snake": 2, "sweep_kz": 8},
-                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 6}):
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 6},
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 3},
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 16}):
         with pytest.raises(mdbs.MdbsError) as e:
             s.set_tuning(bad)
         assert e.value.code == mdbs.ERR_ARG
@@ -111,7 +114,7 @@ def test_batch_schedule_and_autotune_keep_members_identical():
         s.close()
     sims = [mdbs.Simulation(c) for c in cases]
     b = mdbs.Batch(sims)
-    b.set_tuning({"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": 0})
+    b.set_tuning({"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": 0, "tail_ctas": 1})
     b.step(1)
     chosen, trials = b.autotune(trial_steps=1)
     assert chosen == b.tuning() and len(trials) >= 5
@@ -131,9 +134,9 @@ def test_fused_sweeps_with_tma_staging_are_bitwise_equal(precision):
     from paper_2003_08374_gb300 import workloads as W
     case = W.grf_3d(shape=(124, 52, 20), seed=9, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
                     precision=precision)
-    ref_f, ref_s = _run(case, {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0})
+    ref_f, ref_s = _run(case, {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0, "tail_ctas": 1})
     for kz in (4, 8, 32):
-        f, st = _run(case, {"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": kz})
+        f, st = _run(case, {"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": kz, "tail_ctas": 1})
         for k in ref_f:
             assert np.array_equal(ref_f[k], f[k]), (kz, k)
         assert st["cg_iters"] == ref_s["cg_iters"]
