@@ -100,6 +100,22 @@ def dist_info():
     return rank, world, local
 
 
+def max_over_ranks(x, world, device):
+    """The maximum of x over the ranks of the process group (x itself on one rank)."""
+    if world == 1:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(cells, steps, world, ms):
+    """Whole-job cell-steps/s of `world` independent replicas of a `cells`-cell workload
+    that all finished `steps` steps within `ms` milliseconds (the slowest rank's time)."""
+    return cells * steps * world / (ms / 1e3)
+
+
 def reference_arm(args):
     rank, world, _ = dist_info()
     if rank != 0:
@@ -278,12 +294,8 @@ def gpu_arm(args):
         if world > 1:
             torch.distributed.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        return float(t.item())
+    def rank_max(x):
+        return max_over_ranks(x, world, "cuda")
 
     def timed(sim, steps, warmup, profile_kernel=None):
         for _ in range(warmup):
@@ -318,8 +330,8 @@ def gpu_arm(args):
     tuning, tune_ms = pick_schedule(sim, args, trial_steps=2)
     # headline: every step is one CUDA-graph launch (CG loops as device-side WHILE nodes)
     ms, _, clocks, launches, st = timed(sim, args.steps, args.warmup)
-    ms = max_over_ranks(ms)
-    value = case.cells * args.steps * world / (ms / 1e3)
+    ms = rank_max(ms)
+    value = replicas_value(case.cells, args.steps, world, ms)
     cg_iters = st["cg_iters"]
     # the same number of steps again with CUDA events around each launch of the dominant
     # kernel (event timing needs individually launched kernels, so this pass runs eagerly)
@@ -341,8 +353,8 @@ def gpu_arm(args):
             vsim.step(1)
         it1 = vsim.stats()["cg_iters_total"]
         vms, _, _, _, vst = timed(vsim, args.steps, 0)
-        vms = max_over_ranks(vms)
-        vval = case.cells * args.steps * world / (vms / 1e3)
+        vms = rank_max(vms)
+        vval = replicas_value(case.cells, args.steps, world, vms)
         out = {"value": vval, "ms_per_step": vms / args.steps, "speedup_vs_fp64": vval / value,
                "tuning": vtuning, "cg_iters_last_step": vst["cg_iters"],
                "cg_iters_timed": vst["cg_iters_total"] - it1, "cg_iters_warmup": it1 - it0}
@@ -385,8 +397,8 @@ def gpu_arm(args):
     e1.record(stream)
     torch.cuda.synchronize()
     barrier()
-    ems = max_over_ranks(e0.elapsed_time(e1))
-    e2e = {"value": case.cells * args.steps * world / (ems / 1e3), "unit": UNIT,
+    ems = rank_max(e0.elapsed_time(e1))
+    e2e = {"value": replicas_value(case.cells, args.steps, world, ems), "unit": UNIT,
            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes}
     sim.close()
 

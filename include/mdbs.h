@@ -283,6 +283,17 @@ int mdbs_profile_read(const mdbs_sim* sim, int32_t id, const char** name, double
  */
 int64_t mdbs_debug_array(const mdbs_sim* sim, const char* name, double* out, int64_t capacity);
 
+/*
+ * Self-test of the bounded device waits (no counterpart in the paper).  Kernels that
+ * wait on asynchronous copies (the fused sweeps' mbarriers) give up after one second,
+ * record the failure (the step then returns MDBS_ERR_CUDA) and return, so a lost
+ * copy never hangs the GPU.  This call runs one such wait on an mbarrier that
+ * nothing completes: MDBS_OK when the wait gave up as designed and the device still
+ * runs work afterwards; *waited_s receives the device-measured wait (about 1 s).
+ * Error text via mdbs_last_error(NULL).
+ */
+int mdbs_check_bounded_wait(double* waited_s);
+
 /* ---------------- allocation-free helper ---------------- */
 
 /* Capacity of the file-scope scratch array used by mdbs_field_stats_static:

@@ -1017,6 +1017,15 @@ int mdbs_profile_read(const mdbs_sim* s, int32_t id, const char** name, double* 
   return MDBS_OK;
 }
 
+int mdbs_check_bounded_wait(double* waited_s) {
+  if (!waited_s) return fail(nullptr, MDBS_ERR_ARG, "waited_s is NULL");
+  int status = 0;
+  cudaError_t e = bounded_wait_selftest(&status, waited_s);
+  if (e != cudaSuccess) return fail(nullptr, MDBS_ERR_CUDA, std::string("bounded wait: ") + cudaGetErrorString(e));
+  if (status != 1) return fail(nullptr, MDBS_ERR_CUDA, "the bounded wait did not give up as designed");
+  return MDBS_OK;
+}
+
 int64_t mdbs_debug_array(const mdbs_sim* cs, const char* name, double* out, int64_t capacity) {
   mdbs_sim* s = const_cast<mdbs_sim*>(cs);
   if (!s || !name) return MDBS_ERR_ARG;

@@ -321,6 +321,8 @@ constexpr int kSweepDepth = 2;  // planes staged ahead of use
 constexpr int kTmaMaps = 7;
 // opts the fused-sweep and tail kernels into their shared-memory sizes (current device)
 cudaError_t sweep_kernel_setup();
+// runs one bounded mbarrier wait that cannot complete; *status 1: it gave up as designed
+cudaError_t bounded_wait_selftest(int* status, double* waited_s);
 
 // smooth_rows: kBlock rows per work item of the finest-level half sweeps (1, 2, 4, 8);
 // sweep_kz: planes per fused-sweep chunk (0: half sweeps); tail_ctas: CTAs per domain

@@ -302,7 +302,8 @@ __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* _
 // work item so that the REP rows of an item overlap their loads: the colour being
 // written and the colour being read are disjoint cells of the same array.
 template <typename R, int REP>
-__global__ void k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
+__global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
+    k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
@@ -1183,6 +1184,45 @@ __global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w, int rev) {
 }
 
 }  // namespace
+
+namespace {
+// One thread waits, through the same bounded wait the fused sweep uses, on an
+// mbarrier that nothing ever completes: the wait must give up after kWaitLimitNs
+// and the kernel return normally.
+__global__ void k_wait_selftest(int* status, unsigned long long* waited_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  const unsigned long long t0 = global_ns();
+  const bool landed = mbar_wait(&bar, 0);
+  *waited_ns = global_ns() - t0;
+  *status = landed ? 2 : 1;
+}
+}  // namespace
+
+cudaError_t bounded_wait_selftest(int* status, double* waited_s) {
+  int* d_status = nullptr;
+  unsigned long long* d_ns = nullptr;
+  cudaError_t e = cudaMalloc(&d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&d_ns, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+  if (e == cudaSuccess) {
+    k_wait_selftest<<<1, 32>>>(d_status, d_ns);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  unsigned long long ns = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(status, d_status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(&ns, d_ns, sizeof(ns), cudaMemcpyDeviceToHost);
+  // the context must still run work after the timed-out wait
+  if (e == cudaSuccess) e = cudaMemset(d_status, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (d_status) cudaFree(d_status);
+  if (d_ns) cudaFree(d_ns);
+  *waited_s = (double)ns * 1e-9;
+  return e;
+}
 
 cudaError_t sweep_kernel_setup() {
   cudaError_t e =

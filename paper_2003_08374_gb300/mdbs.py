@@ -106,6 +106,7 @@ def lib():
                                               C.c_void_p, C.c_void_p]
         L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
         L.mdbs_debug_array.restype = C.c_int64
+        L.mdbs_check_bounded_wait.argtypes = [_D]
         for nm in ("mdbs_set_tuning", "mdbs_get_tuning", "mdbs_batch_set_tuning", "mdbs_batch_get_tuning"):
             getattr(L, nm).argtypes = [C.c_void_p, C.POINTER(Tuning)]
         for nm in ("mdbs_autotune", "mdbs_batch_autotune"):
@@ -147,6 +148,15 @@ def field_stats_static(cells, cell_volume, porosity_ptr, alpha_ptr, p_ptr, out_p
 def bytes_required(case, precision=None):
     g = Grid(case.nx, case.ny, case.nz, case.h)
     return int(lib().mdbs_bytes_required(C.byref(g), case.precision if precision is None else precision))
+
+
+def check_bounded_wait():
+    """Runs the bounded-wait self-test; returns the device-measured wait in seconds."""
+    w = C.c_double()
+    rc = lib().mdbs_check_bounded_wait(C.byref(w))
+    if rc != OK:
+        raise MdbsError(rc, lib().mdbs_last_error(None).decode())
+    return w.value
 
 
 def kernel_names():

@@ -140,3 +140,15 @@ def test_fused_sweeps_with_tma_staging_are_bitwise_equal(precision):
         for k in ref_f:
             assert np.array_equal(ref_f[k], f[k]), (kz, k)
         assert st["cg_iters"] == ref_s["cg_iters"]
+
+
+def test_bounded_wait_gives_up_and_the_device_stays_usable():
+    """The fused sweeps' mbarrier waits have a time limit: a wait that nothing completes
+    returns after about a second with an error status, and work runs afterwards."""
+    from paper_2003_08374_gb300 import mdbs
+    waited = mdbs.check_bounded_wait()
+    assert 0.9 <= waited <= 5.0
+    s = mdbs.Simulation(_case(1))
+    s.step(1)
+    assert s.stats()["steps"] == 1
+    s.close()
