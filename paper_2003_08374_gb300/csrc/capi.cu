@@ -1059,7 +1059,20 @@ int64_t mdbs_debug_array(const mdbs_sim* cs, const char* name, double* out, int6
       n = 0;
     if (out && capacity > 0) {
       long long m = n < capacity ? n : capacity;
-      if (m > 0) {
+      // the pressure system (T, D, b) is stored x-split: even cells of each row, then
+      // odd ones; the copy returns natural x-fastest order
+      const bool xsplit = e.a == F.T[0] || e.a == F.T[1] || e.a == F.T[2] || e.a == F.Dd || e.a == F.b;
+      if (m > 0 && xsplit) {
+        std::vector<double> dev((size_t)n);
+        cudaError_t er = cudaMemcpyAsync(dev.data(), e.a, n * 8, cudaMemcpyDeviceToHost, s->stream);
+        if (er == cudaSuccess) er = cudaStreamSynchronize(s->stream);
+        if (er != cudaSuccess) return cuda_fail(s, er, "debug copy");
+        const long long n0 = s->P.n[0], he = (n0 + 1) / 2;
+        for (long long c = 0; c < m; c++) {
+          const long long row = c / n0, i = c - row * n0;
+          out[c] = dev[(size_t)(row * n0 + ((i & 1) ? he + i / 2 : i / 2))];
+        }
+      } else if (m > 0) {
         cudaError_t er = cudaMemcpyAsync(out, e.a, m * 8, cudaMemcpyDeviceToHost, s->stream);
         if (er == cudaSuccess) er = cudaStreamSynchronize(s->stream);
         if (er != cudaSuccess) return cuda_fail(s, er, "debug copy");

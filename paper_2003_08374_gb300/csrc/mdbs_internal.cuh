@@ -310,14 +310,15 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
 // builds the block tables and device views of a batch of domains
 // Fused red-black sweep tiles (FP32 levels): a CTA of kSweepBX x kSweepBY threads,
 // each owning two adjacent cells of a row, covers kSweepCX x kSweepBY cells: the
-// interior kSweepTX x kSweepTY plus a one-cell halo ring.  Every array of a plane
-// is staged as one box of kBoxX x kBoxY cells starting at (i0 - 4, j0 - 2): the
-// tile, one more ring of cells, and x padding so that the box starts on a
-// 16-byte boundary (i0 is a multiple of 4).
+// interior kSweepTX x kSweepTY plus a one-cell halo ring and spare columns.  Every
+// array of a plane is staged as the natural x range [i0 - 8, i0 + 64) of kBoxY
+// rows from j0 - 2: in the x-split storage that is one box of kBoxHX even cells
+// and one of kBoxHX odd cells per row (i0 a multiple of 8 keeps both box starts
+// on 16-byte boundaries when n_x is a multiple of 8).
 constexpr int kSweepBX = 32, kSweepBY = 8, kSweepCX = 2 * kSweepBX;
-constexpr int kSweepTX = kSweepCX - 4, kSweepTY = kSweepBY - 2;
-constexpr int kBoxX = kSweepCX + 4, kBoxY = kSweepBY + 2;
-constexpr int kSweepDepth = 2;  // planes staged ahead of use
+constexpr int kSweepTX = kSweepCX - 8, kSweepTY = kSweepBY - 2;
+constexpr int kBoxHX = (kSweepCX + 8) / 2, kBoxY = kSweepBY + 2;
+constexpr int kSweepDepth = 1;  // planes staged ahead of use
 constexpr int kTmaMaps = 7;
 // opts the fused-sweep and tail kernels into their shared-memory sizes (current device)
 cudaError_t sweep_kernel_setup();

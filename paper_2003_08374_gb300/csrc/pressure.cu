@@ -22,12 +22,35 @@ namespace mdbs {
 namespace {
 
 
-__device__ __forceinline__ void decode3(const int n[3], long long c, int& i, int& j, int& k) {
-  const unsigned uc = (unsigned)c;  // arrays stay below 2^31 entries
-  i = (int)(uc % (unsigned)n[0]);
-  const unsigned r = uc / (unsigned)n[0];
-  j = (int)(r % (unsigned)n[1]);
-  k = (int)(r / (unsigned)n[1]);
+
+// ------------------------------------------------------------------ x-split storage
+// Every array of the pressure system (the assembled coefficients and right-hand
+// side, the CG vectors and every multigrid level) stores each x-row with its even
+// cells first and its odd cells after them: cell (i, j, k) sits at
+// n0 (j + n1 k) + (i even ? i / 2 : he + i / 2), he = ceil(n0 / 2).  One colour of a
+// red-black sweep and all its neighbours are then contiguous runs (a natural
+// layout makes every sweep read stride-2, wasting half of each sector).  The
+// pressure field p keeps the natural x-fastest order.
+__device__ __forceinline__ unsigned xs_px(unsigned he, int i) {
+  return (i & 1) ? he + (unsigned)(i >> 1) : (unsigned)(i >> 1);
+}
+__device__ __forceinline__ unsigned lpos(const int n[3], int i, int j, int k) {
+  return (unsigned)n[0] * ((unsigned)j + (unsigned)n[1] * (unsigned)k) + xs_px((unsigned)(n[0] + 1) >> 1, i);
+}
+// storage position -> cell
+__device__ __forceinline__ void decode_pos(const int n[3], long long c, int& i, int& j, int& k) {
+  const unsigned uc = (unsigned)c, n0 = (unsigned)n[0];
+  const unsigned row = uc / n0, r = uc - row * n0, he = (n0 + 1) >> 1;
+  i = (int)(r < he ? 2 * r : 2 * (r - he) + 1);
+  j = (int)(row % (unsigned)n[1]);
+  k = (int)(row / (unsigned)n[1]);
+}
+// position of the neighbour of cell q (at position c) one cell down / up along d
+__device__ __forceinline__ unsigned lo_pos(const int n[3], const int q[3], unsigned c, int d) {
+  return d == 0 ? lpos(n, q[0] - 1, q[1], q[2]) : (d == 1 ? c - (unsigned)n[0] : c - (unsigned)n[0] * (unsigned)n[1]);
+}
+__device__ __forceinline__ unsigned hi_pos(const int n[3], const int q[3], unsigned c, int d) {
+  return d == 0 ? lpos(n, q[0] + 1, q[1], q[2]) : (d == 1 ? c + (unsigned)n[0] : c + (unsigned)n[0] * (unsigned)n[1]);
 }
 
 // the FP64 or FP32 hierarchy of a domain
@@ -104,7 +127,7 @@ constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6
 // unknown faces and the fixed velocity on wall / inlet faces.
 __device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long c) {
   int q[3];
-  decode3(P.n, c, q[0], q[1], q[2]);
+  decode_pos(P.n, c, q[0], q[1], q[2]);  // c: storage position of the cell
   const double A = P.A, A2 = P.A * P.A;
   double div = 0.0, Dd = 0.0;
   for (int d = 0; d < 3; d++) {
@@ -143,14 +166,13 @@ __global__ void k_assemble(const StepDom* __restrict__ D, Work w) {
 template <typename R>
 __device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], long long c) {
   if (q[d] == 0) return R(0);
-  long long o = d == 0 ? 1 : (d == 1 ? (long long)L.n[0] : (long long)L.n[0] * L.n[1]);
-  return tcoef(L, d, (unsigned)(c - o));
+  return tcoef(L, d, lo_pos(L.n, q, (unsigned)c, d));
 }
 
 template <typename R>
 __device__ __forceinline__ void b_diag(const Level<R>& L, long long c) {
   int q[3];
-  decode3(L.n, c, q[0], q[1], q[2]);
+  decode_pos(L.n, c, q[0], q[1], q[2]);
   R dg = R(0);
   for (int d = 0; d < 3; d++) {
     dg += tcoef(L, d, (unsigned)c);
@@ -197,7 +219,7 @@ __global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
 template <typename R>
 __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
-  decode3(Co.n, ci, Q[0], Q[1], Q[2]);
+  decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
   for (int a = 0; a < 3; a++) {
     lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -218,17 +240,17 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
           R inv;
           if (Co.cz[d]) {
             fc[d] = 2 * Q[d] + 1;
-            const R tface = tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
+            const R tface = tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
             fc[d] = 2 * Q[d];
-            const R tin_l = tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
+            const R tin_l = tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
             inv = R(1) / tface + R(1) / (R(2) * tin_l);
             if (2 * Q[d] + 3 < Fi.n[d]) {
               fc[d] = 2 * Q[d] + 2;
-              inv += R(1) / (R(2) * tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2])));
+              inv += R(1) / (R(2) * tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2])));
             }
           } else {
             fc[d] = Q[d];
-            inv = R(1) / tcoef(Fi, d, (unsigned)cell_index(Fi.n, fc[0], fc[1], fc[2]));
+            inv = R(1) / tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
           }
           sum += R(1) / inv;
         }
@@ -237,7 +259,7 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
   R dd = R(0);
   for (int z = lo[2]; z <= hi[2]; z++)
     for (int y = lo[1]; y <= hi[1]; y++)
-      for (int x = lo[0]; x <= hi[0]; x++) dd += R(0.5) * Fi.Dd[cell_index(Fi.n, x, y, z)];
+      for (int x = lo[0]; x <= hi[0]; x++) dd += R(0.5) * Fi.Dd[lpos(Fi.n, x, y, z)];
   Co.Dd[ci] = dd;
 }
 
@@ -258,11 +280,12 @@ template <typename R>
 __device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restrict__ x, const int q[3],
                                            long long c) {
   R v = R(0);
-  long long o = 1;
   for (int d = 0; d < 3; d++) {
-    if (q[d] > 0) v += tcoef(L, d, (unsigned)(c - o)) * x[c - o];
-    if (q[d] + 1 < L.n[d]) v += tcoef(L, d, (unsigned)c) * x[c + o];
-    o *= L.n[d];
+    if (q[d] > 0) {
+      const unsigned cl = lo_pos(L.n, q, (unsigned)c, d);
+      v += tcoef(L, d, cl) * x[cl];
+    }
+    if (q[d] + 1 < L.n[d]) v += tcoef(L, d, (unsigned)c) * x[hi_pos(L.n, q, (unsigned)c, d)];
   }
   return v;
 }
@@ -277,18 +300,20 @@ __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(
 // z-, z+; zero: the other colour's x is taken as 0.  The batched sweeps and the
 // tail share this function, so a cell's value does not depend on which of them
 // updates it.
+// c, cm, cp: storage positions of the cell and of its x neighbours i - 1, i + 1
 template <typename R, typename CT>
 __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* __restrict__ dinv,
                                             const R* __restrict__ xr, R* __restrict__ xw, CT Tx, CT Ty, CT Tz,
-                                            int n0, int n1, int n2, int i, int j, int k, long long c, int zero) {
+                                            int n0, int n1, int n2, int i, int j, int k, long long c, long long cm,
+                                            long long cp, int zero) {
   if (zero) {
     xw[c] = bb[c] * dinv[c];
     return;
   }
   const long long sy = n0, sz = (long long)n0 * n1;
   R v = bb[c];
-  if (i > 0) v = fma_r(Tx[c - 1], xr[c - 1], v);
-  if (i + 1 < n0) v = fma_r(Tx[c], xr[c + 1], v);
+  if (i > 0) v = fma_r(Tx[cm], xr[cm], v);
+  if (i + 1 < n0) v = fma_r(Tx[c], xr[cp], v);
   if (j > 0) v = fma_r(Ty[c - sy], xr[c - sy], v);
   if (j + 1 < n1) v = fma_r(Ty[c], xr[c + sy], v);
   if (k > 0) v = fma_r(Tz[c - sz], xr[c - sz], v);
@@ -323,10 +348,12 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
         const int ti = (int)(t % half);
         const unsigned row = t / half;
         const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
-        const int i = ((j + k + col) & 1) + 2 * ti;
+        const int sh = (j + k + col) & 1, i = sh + 2 * ti;
         if (i >= n0) continue;
-        const long long c = i + (long long)n0 * row;
-        smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
+        // x-split positions: this colour's run, and the other colour's run for i -/+ 1
+        const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
+        const unsigned cm = sh ? rb + ti : rb + half + ti - 1, cp = sh ? rb + ti + 1 : rb + half + ti;
+        smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
       }
     });
   }
@@ -335,7 +362,7 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
 // ------------------------------------------------------------------ fused red-black sweep (FP32)
 // One launch per sweep pair of an FP32 level: colour c1 everywhere, then the other
 // colour.  A CTA owns an extended tile of kSweepCX x kSweepBY cells (the interior
-// kSweepTX x kSweepTY, a one-cell halo ring, and two spare columns); thread
+// kSweepTX x kSweepTY, a one-cell halo ring, and spare columns); thread
 // (tx, ty) owns the pair of cells 2 tx, 2 tx + 1 of row ty, so in each colour phase
 // every lane of a warp updates exactly one cell (no checkerboard divergence).  The
 // CTA marches over a chunk [z0, z1) of kz planes: at step k it updates the first
@@ -349,23 +376,31 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
 // the traffic of two half sweeps, and each cell's arithmetic is smooth_cell's.
 //
 // Planes reach shared memory kSweepDepth planes ahead of use, in a ring of
-// kSweepDepth + 4 stages (planes k - 2 .. k + 1 are read at step k).  A stage is one
-// kBoxX x kBoxY box per array (x, T_x, T_y, T_z, b, 1/diag) starting at cell
-// (i0 - 4, j0 - 2): TMA tiled copies (cp.async.bulk.tensor) issued by one thread
+// kSweepDepth + 4 stages (planes k - 2 .. k + 1 are read at step k).  A stage holds,
+// per array (x, T_x, T_y, T_z, b, 1/diag), the natural x range [i0 - 8, i0 + 64) of
+// kBoxY rows from j0 - 2, as two kBoxHX x kBoxY boxes of the x-split storage (even
+// cells, odd cells): TMA tiled copies (cp.async.bulk.tensor) issued by one thread
 // and completing on the stage's mbarrier when the level has tensor maps (FP32
-// coefficients, n_x a multiple of 4), else per-element cp.async by every thread.
+// coefficients, n_x a multiple of 8), else per-element cp.async by every thread.
 // Cells outside the domain or the plane range are zero-filled and never used.
 // FP64 levels use the half sweeps: GB300's FP64 pipe, not HBM, bounds them.
-constexpr int kBoxN = kBoxX * kBoxY;              // cells per box
-constexpr int kBoxS = (kBoxN + 31) / 32 * 32;     // floats between boxes (128-byte aligned)
+constexpr int kBoxHalf = kBoxHX * kBoxY;               // cells per box (even or odd cells)
+constexpr int kBoxHalfS = (kBoxHalf + 31) / 32 * 32;   // floats per box slot (128-byte aligned)
+constexpr int kBoxN = 2 * kBoxHalf;                    // cells per staged array
+constexpr int kBoxS = 2 * kBoxHalfS;                   // floats per staged array: even box, odd box
 constexpr int kSweepThreads = kSweepBX * kSweepBY;
 constexpr int kStage = 6 * kBoxS;                 // floats per stage
 constexpr int kStages = kSweepDepth + 4;
 constexpr int kRing = 4;                          // planes of first-colour values kept
-constexpr unsigned kBoxBytes = kBoxN * 4u;
+constexpr unsigned kBoxBytes = kBoxHalf * 4u;  // one TMA box (even or odd cells)
 enum { kBoxX_ = 0, kBoxTx = 1, kBoxTy = 2, kBoxTz = 3, kBoxB = 4, kBoxD = 5 };
 static_assert(kBoxS * 4 % 128 == 0, "boxes must stay 128-byte aligned in shared memory");
-static_assert(kSweepTX % 4 == 0, "tile origins must be 16-byte aligned for TMA");
+static_assert(kSweepTX % 8 == 0, "tile origins must keep the box starts 16-byte aligned for TMA");
+
+// index in a staged array of the cell at natural offset bx = i - (i0 - 8), row by
+__device__ __forceinline__ int box_idx(int bx, int by) {
+  return (bx & 1) * kBoxHalfS + by * kBoxHX + (bx >> 1);
+}
 
 __host__ __device__ constexpr size_t sweep_smem_bytes() {
   // 128 bytes of alignment slack, the stages, the first-colour ring, the mbarriers
@@ -482,7 +517,7 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
     const bool row_in = j >= 0 && j < n1;
     const bool row_interior = row_in && ty >= 1 && ty <= kSweepTY;
     // 32-bit cell indices (levels stay below 2^31 cells)
-    const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
+    const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1, he = (unsigned)(n0 + 1) >> 1;
     const int a0 = zero ? 1 : 0;  // the zero-guess sweep does not read x
     auto stage_of = [&](int p) { return base + ((p % kStages) + kStages) % kStages * kStage; };
 
@@ -493,21 +528,28 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
       if (tma) {
         if (tid == 0) {
           asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-          mbar_expect_tx(&bars[s], (6 - a0) * kBoxBytes);
+          mbar_expect_tx(&bars[s], (6 - a0) * 2 * kBoxBytes);
 #pragma unroll
           for (int a = 0; a < 6; a++)
-            if (a >= a0) tma_box(st + a * kBoxS, maps + map_idx[a], i0 - 4, j0 - 2, p, &bars[s]);
+            if (a >= a0) {
+              tma_box(st + a * kBoxS, maps + map_idx[a], i0 / 2 - 4, j0 - 2, p, &bars[s]);  // even cells
+              tma_box(st + a * kBoxS + kBoxHalfS, maps + map_idx[a], (int)he + i0 / 2 - 4, j0 - 2, p,
+                      &bars[s]);  // odd cells
+            }
         }
       } else {
         const bool pv = p >= 0 && p < n2;
         for (int e = tid; e < kBoxN; e += kSweepThreads) {
-          const int by = e / kBoxX, bx = e - by * kBoxX;
-          const int ii = i0 - 4 + bx, jj = j0 - 2 + by;
+          const int par = e / kBoxHalf, rem = e - par * kBoxHalf;
+          const int by = rem / kBoxHX, hx = rem - by * kBoxHX;
+          const int ii = i0 - 8 + 2 * hx + par, jj = j0 - 2 + by;
           const bool ok = pv && ii >= 0 && ii < n0 && jj >= 0 && jj < n1;
-          const unsigned g = ok ? (unsigned)ii + sy * (unsigned)jj + sz * (unsigned)p : 0u;
+          // the box holds cells in natural x order, gathered from x-split storage
+          const unsigned g = ok ? xs_px(he, ii) + sy * (unsigned)jj + sz * (unsigned)p : 0u;
+          const int slot = par * kBoxHalfS + rem;
 #pragma unroll
           for (int a = 0; a < 6; a++)
-            if (a >= a0) stage_el(st + a * kBoxS + e, arr[a], half[a], g, ok);
+            if (a >= a0) stage_el(st + a * kBoxS + slot, arr[a], half[a], g, ok);
         }
         cp_async_commit();
       }
@@ -544,17 +586,19 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
         const float* Sp = stage_of(k + 1);
         const int e1 = 2 * tx + (((ia + j + k) & 1) == c1 ? 0 : 1);
         const int i1 = i0 - 1 + e1;
-        const int h1 = (ty + 1) * kBoxX + e1 + 3;  // the cell in the boxes
+        const int b1 = e1 + 7;                 // natural offset of the cell from i0 - 8
+        const int h1 = box_idx(b1, ty + 1);  // the cell in the staged arrays
+        const int h1m = box_idx(b1 - 1, ty + 1), h1p = box_idx(b1 + 1, ty + 1);
         if (row_in && i1 >= 0 && i1 < n0 && k >= 0 && k < n2) {
           float v = Sk[kBoxB * kBoxS + h1];
           if (!zero) {
             const float* X = Sk;
             const float* TX = Sk + kBoxTx * kBoxS;
             const float* TY = Sk + kBoxTy * kBoxS;
-            if (i1 > 0) v = fma_r(TX[h1 - 1], X[h1 - 1], v);
-            if (i1 + 1 < n0) v = fma_r(TX[h1], X[h1 + 1], v);
-            if (j > 0) v = fma_r(TY[h1 - kBoxX], X[h1 - kBoxX], v);
-            if (j + 1 < n1) v = fma_r(TY[h1], X[h1 + kBoxX], v);
+            if (i1 > 0) v = fma_r(TX[h1m], X[h1m], v);
+            if (i1 + 1 < n0) v = fma_r(TX[h1], X[h1p], v);
+            if (j > 0) v = fma_r(TY[h1 - kBoxHX], X[h1 - kBoxHX], v);
+            if (j + 1 < n1) v = fma_r(TY[h1], X[h1 + kBoxHX], v);
             if (k > 0) v = fma_r(Sm[kBoxTz * kBoxS + h1], Sm[h1], v);
             if (k + 1 < n2) v = fma_r(Sk[kBoxTz * kBoxS + h1], Sp[h1], v);
           }
@@ -566,10 +610,10 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
       const int e2 = 2 * tx + (((ia + j + m) & 1) == c1 ? 1 : 0);
       const float* Sq = stage_of(m);
       if (row_interior && m >= z0 && m < z1) {
-        const int h2 = (ty + 1) * kBoxX + e2 + 3;
+        const int h2 = box_idx(e2 + 7, ty + 1), h2m = box_idx(e2 + 6, ty + 1);
         const float* q = s1 + ((m + kRing) % kRing) * kSweepThreads;
         const int io = i0 - 1 + (e2 ^ 1);  // first-colour member of the pair on plane m
-        if (io >= i0 && io < i0 + kSweepTX && io < n0) xout[(unsigned)io + sy * (unsigned)j + sz * (unsigned)m] = q[tid];
+        if (io >= i0 && io < i0 + kSweepTX && io < n0) xout[xs_px(he, io) + sy * (unsigned)j + sz * (unsigned)m] = q[tid];
         const int i2 = i0 - 1 + e2;
         if (i2 >= i0 && i2 < i0 + kSweepTX && i2 < n0) {
           const float* TX = Sq + kBoxTx * kBoxS;
@@ -577,20 +621,20 @@ __global__ void __launch_bounds__(kSweepThreads, 2)
           const float left = (e2 & 1) ? q[tid] : q[tid - 1];
           const float right = (e2 & 1) ? q[tid + 1] : q[tid];
           float v = Sq[kBoxB * kBoxS + h2];
-          if (i2 > 0) v = fma_r(TX[h2 - 1], left, v);
+          if (i2 > 0) v = fma_r(TX[h2m], left, v);
           if (i2 + 1 < n0) v = fma_r(TX[h2], right, v);
-          if (j > 0) v = fma_r(TY[h2 - kBoxX], q[tid - kSweepBX], v);
+          if (j > 0) v = fma_r(TY[h2 - kBoxHX], q[tid - kSweepBX], v);
           if (j + 1 < n1) v = fma_r(TY[h2], q[tid + kSweepBX], v);
           if (m > 0) v = fma_r(tzmm, s1[((m + kRing - 1) % kRing) * kSweepThreads + tid], v);
           if (m + 1 < n2) v = fma_r(Sq[kBoxTz * kBoxS + h2], s1[((m + 1) % kRing) * kSweepThreads + tid], v);
-          xout[(unsigned)i2 + sy * (unsigned)j + sz * (unsigned)m] = v * Sq[kBoxD * kBoxS + h2];
+          xout[xs_px(he, i2) + sy * (unsigned)j + sz * (unsigned)m] = v * Sq[kBoxD * kBoxS + h2];
         }
       }
       // T_z on plane m of the cell that is second colour on plane m + 1 (the next step's;
       // needed from m + 1 = z0 on, and plane m has landed from m = z0 - 2 on)
       if (m >= z0 - 1) {
         const int e2n = 2 * tx + (((ia + j + m + 1) & 1) == c1 ? 1 : 0);
-        tzmm = Sq[kBoxTz * kBoxS + (ty + 1) * kBoxX + e2n + 3];
+        tzmm = Sq[kBoxTz * kBoxS + box_idx(e2n + 7, ty + 1)];
       }
     }
     // planes staged beyond the chunk: let them land before the stages are reused
@@ -630,7 +674,7 @@ __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int 
 template <typename R>
 __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
-  decode3(Co.n, ci, Q[0], Q[1], Q[2]);
+  decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
   for (int a = 0; a < 3; a++) {
     lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -641,7 +685,7 @@ __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level
     for (int y = lo[1]; y <= hi[1]; y++)
       for (int x = lo[0]; x <= hi[0]; x++) {
         const int q[3] = {x, y, z};
-        const long long c = cell_index(Fi.n, x, y, z);
+        const long long c = lpos(Fi.n, x, y, z);
         const R ax = Fi.diag[c] * Fi.x[c] - neighbour_sum(Fi, Fi.x, q, c);
         s += Fi.b[c] - ax;
       }
@@ -667,10 +711,10 @@ __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int
 template <typename R>
 __device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co, long long c) {
   int q[3];
-  decode3(Fi.n, c, q[0], q[1], q[2]);
+  decode_pos(Fi.n, c, q[0], q[1], q[2]);
   int Q[3];
   for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
-  Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
+  Fi.x[c] += Co.x[lpos(Co.n, Q[0], Q[1], Q[2])];
 }
 
 template <typename R>
@@ -714,19 +758,16 @@ __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
   const int n = (int)C.cells;
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) M[e] = R(0);
   __syncthreads();
-  for (int c = threadIdx.x; c < n; c += blockDim.x) {
+  for (int c = threadIdx.x; c < n; c += blockDim.x) {  // rows and columns in storage order
     int q[3];
-    q[0] = c % C.n[0];
-    q[1] = (c / C.n[0]) % C.n[1];
-    q[2] = c / (C.n[0] * C.n[1]);
+    decode_pos(C.n, c, q[0], q[1], q[2]);
     M[c * n + c] = C.diag[c];
-    int o = 1;
     for (int d = 0; d < 3; d++) {
       if (q[d] + 1 < C.n[d]) {
-        M[c * n + c + o] = -tcoef(C, d, (unsigned)c);
-        M[(c + o) * n + c] = -tcoef(C, d, (unsigned)c);
+        const int u = (int)hi_pos(C.n, q, (unsigned)c, d);
+        M[c * n + u] = -tcoef(C, d, (unsigned)c);
+        M[u * n + c] = -tcoef(C, d, (unsigned)c);
       }
-      o *= C.n[d];
     }
   }
   __syncthreads();
@@ -785,10 +826,11 @@ __device__ void tail_smooth(const Level<R>& L, int col, int zero, const TailPart
     for (unsigned t = tp.first; t < total; t += tp.step) {
       const unsigned ti = t % half, row = t / half;
       const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
-      const int i = ((j + k + col) & 1) + 2 * (int)ti;
+      const int sh = (j + k + col) & 1, i = sh + 2 * (int)ti;
       if (i >= n0) continue;
-      const long long c = i + (long long)n0 * row;
-      smooth_cell<R>(L.b, L.dinv, L.x, L.x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, zero);
+      const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
+      const unsigned cm = sh ? rb + ti : rb + half + ti - 1, cp = sh ? rb + ti + 1 : rb + half + ti;
+      smooth_cell<R>(L.b, L.dinv, L.x, L.x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
     }
   });
   tail_barrier(tp);
@@ -810,10 +852,7 @@ template <typename R>
 __device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
   for (unsigned ci = tp.first; ci < (unsigned)Co.cells; ci += tp.step) {
     int Q[3];
-    Q[0] = (int)(ci % (unsigned)Co.n[0]);
-    const unsigned r = ci / (unsigned)Co.n[0];
-    Q[1] = (int)(r % (unsigned)Co.n[1]);
-    Q[2] = (int)(r / (unsigned)Co.n[1]);
+    decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) {
       lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -824,7 +863,7 @@ __device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co, const Tail
       for (int y = lo[1]; y <= hi[1]; y++)
         for (int x = lo[0]; x <= hi[0]; x++) {
           const int q[3] = {x, y, z};
-          const long long c = cell_index(Fi.n, x, y, z);
+          const long long c = lpos(Fi.n, x, y, z);
           const R ax = Fi.diag[c] * Fi.x[c] - neighbour_sum(Fi, Fi.x, q, c);
           s += Fi.b[c] - ax;
         }
@@ -837,13 +876,10 @@ template <typename R>
 __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
   for (unsigned c = tp.first; c < (unsigned)Fi.cells; c += tp.step) {
     int q[3];
-    q[0] = (int)(c % (unsigned)Fi.n[0]);
-    const unsigned r = c / (unsigned)Fi.n[0];
-    q[1] = (int)(r % (unsigned)Fi.n[1]);
-    q[2] = (int)(r / (unsigned)Fi.n[1]);
+    decode_pos(Fi.n, c, q[0], q[1], q[2]);
     int Q[3];
     for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
-    Fi.x[c] += Co.x[cell_index(Co.n, Q[0], Q[1], Q[2])];
+    Fi.x[c] += Co.x[lpos(Co.n, Q[0], Q[1], Q[2])];
   }
   tail_barrier(tp);
 }
@@ -912,14 +948,16 @@ __global__ void __launch_bounds__(kTailThreads)
 constexpr size_t kTailSmemMax = 200 * 1024;
 
 // ------------------------------------------------------------------ CG kernels (FP64)
-__device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const double* __restrict__ x, long long c,
+// (A p) at the cell q stored at position c; p is in natural order
+__device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const double* __restrict__ p, unsigned c,
                                            const int q[3]) {
-  double v = F.diag[c] * x[c];
-  long long o = 1;
+  const unsigned nc = (unsigned)q[0] + (unsigned)P.n[0] * ((unsigned)q[1] + (unsigned)P.n[1] * (unsigned)q[2]);
+  double v = F.diag[c] * p[nc];
+  unsigned o = 1;
   for (int d = 0; d < 3; d++) {
-    if (q[d] > 0) v -= F.T[d][c - o] * x[c - o];
-    if (q[d] + 1 < P.n[d]) v -= F.T[d][c] * x[c + o];
-    o *= P.n[d];
+    if (q[d] > 0) v -= F.T[d][lo_pos(P.n, q, c, d)] * p[nc - o];
+    if (q[d] + 1 < P.n[d]) v -= F.T[d][c] * p[nc + o];
+    o *= (unsigned)P.n[d];
   }
   return v;
 }
@@ -937,9 +975,9 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < S.P.cells) {
         int q[3];
-        decode3(S.P.n, c, q[0], q[1], q[2]);
+        decode_pos(S.P.n, c, q[0], q[1], q[2]);
         const double bc = S.F.b[c];
-        const double rc = bc - apply_A0(S.F, S.P, S.F.p, c, q);
+        const double rc = bc - apply_A0(S.F, S.P, S.F.p, (unsigned)c, q);
         G.r[c] = rc;
         rr += rc * rc;
         bb += bc * bc;
@@ -974,11 +1012,13 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         int i, j, k;
-        decode3(S.P.n, c, i, j, k);
+        decode_pos(S.P.n, c, i, j, k);
+        const unsigned rb = (unsigned)n0 * ((unsigned)j + (unsigned)n1 * (unsigned)k), he = (unsigned)(n0 + 1) >> 1;
+        const unsigned cm = rb + xs_px(he, i - 1), cp = rb + xs_px(he, i + 1);
         const double dc = dv[c];
         double v = dg[c] * dc;
-        if (i > 0) v -= Tx[c - 1] * dv[c - 1];
-        if (i + 1 < n0) v -= Tx[c] * dv[c + 1];
+        if (i > 0) v -= Tx[cm] * dv[cm];
+        if (i + 1 < n0) v -= Tx[c] * dv[cp];
         if (j > 0) v -= Ty[c - sy] * dv[c - sy];
         if (j + 1 < n1) v -= Ty[c] * dv[c + sy];
         if (k > 0) v -= Tz[c - sz] * dv[c - sz];
@@ -1003,6 +1043,7 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
     const double al = G.scal[kAlpha];
     double s = 0.0;
     const long long n = S.P.cells;
+    const unsigned n0 = (unsigned)S.P.n[0], he = (n0 + 1) >> 1;
     double* __restrict__ p = S.F.p;
     double* __restrict__ rv = G.r;
     const double* __restrict__ dv = G.dv;
@@ -1011,7 +1052,9 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
     for (int r = 0; r < REP; r++) {
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
-        p[c] += al * dv[c];
+        // p is in natural order: the cell at x-split position c
+        const unsigned row = (unsigned)c / n0, x = (unsigned)c - row * n0;
+        p[row * n0 + (x < he ? 2 * x : 2 * (x - he) + 1)] += al * dv[c];
         const double rc = rv[c] - al * qv[c];
         rv[c] = rc;
         s += rc * rc;
@@ -1375,9 +1418,10 @@ static PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
   return fn;
 }
 
-// TMA descriptors (3-D tiled, FP32, box kBoxX x kBoxY x 1, zero fill outside) of every
-// FP32 level whose rows are 16-byte multiples and whose coefficients are stored in
-// FP32; the other levels stage their planes with per-element copies.
+// TMA descriptors (3-D tiled over the x-split storage, FP32, box kBoxHX x kBoxY x 1,
+// zero fill outside) of every FP32 level whose x extent is a multiple of 8 (so the
+// odd cells of a row start on a 16-byte boundary) and whose coefficients are stored
+// in FP32; the other levels stage their planes with per-element copies.
 static cudaError_t encode_level_maps(PressureSolver* ps) {
   PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
   ps->tma_levels = 0;
@@ -1386,10 +1430,10 @@ static cudaError_t encode_level_maps(PressureSolver* ps) {
   memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
   for (int l = 0; l < ps->nlev; l++) {
     const Level<float>& L = ps->lf[l];
-    if (!L.T[0] || L.n[0] % 4 != 0) continue;
+    if (!L.T[0] || L.n[0] % 8 != 0) continue;
     const cuuint64_t dims[3] = {(cuuint64_t)L.n[0], (cuuint64_t)L.n[1], (cuuint64_t)L.n[2]};
     const cuuint64_t strides[2] = {(cuuint64_t)L.n[0] * 4, (cuuint64_t)L.n[0] * L.n[1] * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)kBoxX, (cuuint32_t)kBoxY, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)kBoxHX, (cuuint32_t)kBoxY, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     float* const arrays[kTmaMaps] = {L.x, L.x2, L.b, L.dinv, L.T[0], L.T[1], L.T[2]};
     bool ok = true;

@@ -129,10 +129,11 @@ def test_batch_schedule_and_autotune_keep_members_identical():
 
 @pytest.mark.parametrize("precision", [1, 2])
 def test_fused_sweeps_with_tma_staging_are_bitwise_equal(precision):
-    """Levels whose x extent is a multiple of 4 stage their planes with TMA box copies
-    (124 = 2 x 60 + 4: ragged last tile); the fields must equal the split sweeps'."""
+    """Levels whose x extent is a multiple of 8 stage their planes with TMA box copies of
+    the even and the odd cells (120 = 2 x 56 + 8: a ragged last tile; the 60- and
+    30-cell levels use per-element copies); the fields must equal the split sweeps'."""
     from paper_2003_08374_gb300 import workloads as W
-    case = W.grf_3d(shape=(124, 52, 20), seed=9, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
+    case = W.grf_3d(shape=(120, 52, 20), seed=9, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
                     precision=precision)
     ref_f, ref_s = _run(case, {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0, "tail_ctas": 1})
     for kz in (4, 8, 32):
