@@ -964,7 +964,7 @@ __device__ __forceinline__ double apply_A0(const Fld& F, const Prm& P, const dou
 
 // r = b - A p; one partial of r.r and b.b per block
 template <int REP>
-__global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w) {
+__global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int narrow) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const StepDom& S = D[dm];
@@ -979,6 +979,7 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
         const double bc = S.F.b[c];
         const double rc = bc - apply_A0(S.F, S.P, S.F.p, (unsigned)c, q);
         G.r[c] = rc;
+        if (narrow) G.lf[0].b[c] = (float)rc;  // the first FP32 V-cycle's right-hand side
         rr += rc * rc;
         bb += bc * bc;
       }
@@ -1034,7 +1035,7 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
 
 // p += alpha d; r -= alpha q; partial r.r
 template <int REP>
-__global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev) {
+__global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restrict__ C, Work w, int rev, int narrow) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
@@ -1057,6 +1058,7 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
         p[row * n0 + (x < he ? 2 * x : 2 * (x - he) + 1)] += al * dv[c];
         const double rc = rv[c] - al * qv[c];
         rv[c] = rc;
+        if (narrow) G.lf[0].b[c] = (float)rc;  // the next FP32 V-cycle's right-hand side
         s += rc * rc;
       }
     }
@@ -1075,14 +1077,23 @@ __global__ void k_dots_rz(const StepDom* __restrict__ D, const CgDom* __restrict
     double rz = 0.0, zq = 0.0;
     const long long n = D[dm].P.cells;
     const double* __restrict__ rv = G.r;
-    const double* __restrict__ z = G.z;
+    double* __restrict__ z = G.z;
     const double* __restrict__ qv = G.q;
+    const float* __restrict__ zf = G.lf[0].x;
     #pragma unroll
     for (int r = 0; r < REP; r++) {
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
-        rz += rv[c] * z[c];
-        if (with_zq) zq += z[c] * qv[c];
+        // flexible CG: z is the FP32 V-cycle's result, widened here (no separate pass)
+        double zc;
+        if (with_zq) {
+          zc = (double)zf[c];
+          z[c] = zc;
+        } else {
+          zc = z[c];
+        }
+        rz += rv[c] * zc;
+        if (with_zq) zq += zc * qv[c];
       }
     }
     rz = block_sum(rz);
@@ -1200,30 +1211,6 @@ __global__ void k_record(const StepDom* __restrict__ D, const CgDom* __restrict_
   step[kSlotResid + corr] = res;
   step[kSlotItersTotal] += scal[kIt];
   if (!(res <= tol)) step[kSlotNotConverged] += 1.0;
-}
-
-// r -> FP32 right-hand side of the FP32 V-cycle; its result -> z
-__global__ void k_copy_d2f(const CgDom* __restrict__ C, Work w, int rev) {
-  MDBS_DEPENDENT_ENTRY();
-  FOR_WORK_DIR(w, rev)
-    const CgDom& G = C[dm];
-    if (G.scal[kCond] == 0.0) continue;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < G.lf[0].cells) G.lf[0].b[c] = (float)G.r[c];
-    }
-  }
-}
-__global__ void k_copy_f2d(const CgDom* __restrict__ C, Work w, int rev) {
-  MDBS_DEPENDENT_ENTRY();
-  FOR_WORK_DIR(w, rev)
-    const CgDom& G = C[dm];
-    if (G.scal[kCond] == 0.0) continue;
-    for (int r = 0; r < w.rep; r++) {
-      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < G.lf[0].cells) G.z[c] = (double)G.lf[0].x[c];
-    }
-  }
 }
 
 }  // namespace
@@ -1532,7 +1519,7 @@ static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
     MDBS_LAUNCH(K_COARSEN, grid_of(B, B.lcells[l]), kBlock, s, k_coarsen<R>, B.cg, B.lcells[l], l);
     MDBS_LAUNCH(K_DIAG, grid_of(B, B.lcells[l]), kBlock, s, k_diag<R>, B.cg, B.lcells[l], l);
   }
-  if (direct) MDBS_LAUNCH(K_COARSEN, B.ndom, 256, s, k_coarse_inverse<R>, B.cg);
+  if (direct) MDBS_LAUNCH(K_COARSEN, B.ndom, 1024, s, k_coarse_inverse<R>, B.cg);
 }
 
 // Traversal direction of the next kernel over each level; flips at every launch
@@ -1656,7 +1643,7 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
   }
   const int use = capture ? 1 : 0;
   // initial residual and loop condition
-  MDBS_LAUNCH(K_RESID0, grid_of(B, B.rcells), kBlock, s, (k_resid0<kRepBig>), B.sd, B.cg, B.rcells);
+  MDBS_LAUNCH(K_RESID0, grid_of(B, B.rcells), kBlock, s, (k_resid0<kRepBig>), B.sd, B.cg, B.rcells, flexible);
   MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize, B.cg, B.rcells, 0, 1, tol, max_it);
   MDBS_LAUNCH(K_FINALIZE, 1, 1024, s, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   MDBS_LAUNCH(K_ZERO, grid_of(B, B.cells), kBlock, s, k_zero_if_b0, B.sd, B.cg, B.cells);
@@ -1666,16 +1653,17 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
     if (!flexible) {
       vcycle<double>(B, nu1, nu2, cs, D, bs);
     } else {
-      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_d2f, B.cg, B.cells, D.next(0));
+      // the FP32 right-hand side was narrowed by the residual update; the result is
+      // widened by the dot products
       vcycle<float>(B, nu1, nu2, cs, D, bs);
-      MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, bs, k_copy_f2d, B.cg, B.cells, D.next(0));
     }
     MDBS_LAUNCH(K_DOTS, grid_of(B, B.rcells), kBlock, bs, (k_dots_rz<kRepBig>), B.sd, B.cg, B.rcells, flexible, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 3, flexible, tol, max_it);
     MDBS_LAUNCH(K_UPDATE_D, grid_of(B, B.rcells), kBlock, bs, (k_update_d<kRepBig>), B.sd, B.cg, B.rcells, flexible, D.next(0));
     MDBS_LAUNCH(K_SPMV_DOT, grid_of(B, B.rcells), kBlock, bs, (k_spmv_dot<kRepBig>), B.sd, B.cg, B.rcells, D.next(0));
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 1, 0, tol, max_it);
-    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, (k_update_xr<kRepBig>), B.sd, B.cg, B.rcells, D.next(0));
+    MDBS_LAUNCH(K_UPDATE_XR, grid_of(B, B.rcells), kBlock, bs, (k_update_xr<kRepBig>), B.sd, B.cg, B.rcells, D.next(0),
+                flexible);
     MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, bs, k_finalize, B.cg, B.rcells, 2, 0, tol, max_it);
     MDBS_LAUNCH(K_FINALIZE, 1, 1024, bs, k_any, B.cg, B.ndom, B.any_flag, handle, use);
   };
