@@ -64,6 +64,24 @@ struct Fld {
   double *T[3], *Dd, *diag, *dinv, *b;
 };
 
+// Division by a divisor fixed for a level, without a hardware divide: for
+// 0 <= t < 2^31, t / d == (t * m) >> s with s = 31 + ceil(log2 d) and
+// m = ceil(2^s / d) < 2^32 (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994).
+struct FastDiv {
+  unsigned m;
+  unsigned s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) l++;
+  const unsigned long long num = 1ull << (31 + l);
+  return FastDiv{(unsigned)((num + d - 1) / d), 31 + l};
+}
+__device__ __forceinline__ unsigned fastdiv(unsigned t, FastDiv f) {
+  return (unsigned)(((unsigned long long)t * f.m) >> f.s);
+}
+
 // One multigrid level (T is stored per cell for the face towards +axis).  In the
 // FP32 hierarchy of MDBS_MIXED_BF16 the coarse levels (l >= 1) keep T as BF16 bit
 // patterns in Tb (T is then NULL); every reader widens them to FP32.
@@ -72,6 +90,7 @@ struct Level {
   int n[3];
   int cz[3];  // axis coarsened relative to the finer level
   long long cells;
+  FastDiv dhalf, dn1;  // division by ceil(n[0] / 2) and by n[1]
   R* T[3];
   uint16_t* Tb[3];
   R* Dd;

@@ -340,14 +340,16 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
     R* __restrict__ x = Lr.x;
     const unsigned half = (n0 + 1) >> 1;
     const unsigned total = half * (unsigned)n1 * (unsigned)n2;
+    const FastDiv dh = Lr.dhalf, dn = Lr.dn1;
     with_coefs(Lr, [&](auto Tx, auto Ty, auto Tz) {
 #pragma unroll
       for (int r = 0; r < REP; r++) {
         const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
         if (t >= total) continue;
-        const int ti = (int)(t % half);
-        const unsigned row = t / half;
-        const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
+        const unsigned row = fastdiv(t, dh);
+        const int ti = (int)(t - row * half);
+        const unsigned kk = fastdiv(row, dn);
+        const int j = (int)(row - kk * (unsigned)n1), k = (int)kk;
         const int sh = (j + k + col) & 1, i = sh + 2 * ti;
         if (i >= n0) continue;
         // x-split positions: this colour's run, and the other colour's run for i -/+ 1
@@ -824,8 +826,9 @@ __device__ void tail_smooth(const Level<R>& L, int col, int zero, const TailPart
   const unsigned total = half * (unsigned)n1 * (unsigned)n2;
   with_coefs(L, [&](auto Tx, auto Ty, auto Tz) {
     for (unsigned t = tp.first; t < total; t += tp.step) {
-      const unsigned ti = t % half, row = t / half;
-      const int j = (int)(row % (unsigned)n1), k = (int)(row / (unsigned)n1);
+      const unsigned row = fastdiv(t, L.dhalf), ti = t - row * half;
+      const unsigned kk = fastdiv(row, L.dn1);
+      const int j = (int)(row - kk * (unsigned)n1), k = (int)kk;
       const int sh = (j + k + col) & 1, i = sh + 2 * (int)ti;
       if (i >= n0) continue;
       const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
@@ -1353,6 +1356,8 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
       Ld.cz[a] = Lf.cz[a] = cz[l][a];
     }
     Ld.cells = Lf.cells = nc;
+    Ld.dhalf = Lf.dhalf = make_fastdiv((unsigned)(dims[l][0] + 1) / 2);
+    Ld.dn1 = Lf.dn1 = make_fastdiv((unsigned)dims[l][1]);
     if (precision == 0) {
       if (l > 0) {
         for (int a = 0; a < 3; a++) Ld.T[a] = (double*)take(nc * 8);
