@@ -620,6 +620,10 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.n[2] = grid->nz;
   Layout L = layout_of(grid);
   P.dim = L.dim;
+  P.dn0 = make_fastdiv((unsigned)grid->nx);
+  P.dn1 = make_fastdiv((unsigned)grid->ny);
+  P.dn0p = make_fastdiv((unsigned)grid->nx + 1);
+  P.dn1p = make_fastdiv((unsigned)grid->ny + 1);
   P.cells = L.cells;
   for (int d = 0; d < 3; d++) P.nf[d] = L.nf[d];
   P.h = grid->h;

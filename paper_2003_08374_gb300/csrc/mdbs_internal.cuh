@@ -24,6 +24,24 @@ constexpr int kSlotMass = 0, kSlotAmin = 1, kSlotAmax = 2, kSlotBad = 3, kSlotUm
               kSlotDt = 6, kSlotTime = 7, kSlotIters = 8 /* 8 correctors */, kSlotResid = 16 /* 8 */,
               kSlotItersTotal = 24, kSlotNotConverged = 25, kNumSlots = 32;
 
+// Division by a divisor fixed for a level, without a hardware divide: for
+// 0 <= t < 2^31, t / d == (t * m) >> s with s = 31 + ceil(log2 d) and
+// m = ceil(2^s / d) < 2^32 (Granlund and Montgomery, "Division by invariant
+// integers using multiplication", 1994).
+struct FastDiv {
+  unsigned m;
+  unsigned s;
+};
+inline FastDiv make_fastdiv(unsigned d) {
+  unsigned l = 0;
+  while ((1ull << l) < d) l++;
+  const unsigned long long num = 1ull << (31 + l);
+  return FastDiv{(unsigned)((num + d - 1) / d), 31 + l};
+}
+__device__ __forceinline__ unsigned fastdiv(unsigned t, FastDiv f) {
+  return (unsigned)(((unsigned long long)t * f.m) >> f.s);
+}
+
 // Geometry and physical parameters of one domain.
 struct Prm {
   int n[3];  // cells per axis
@@ -41,6 +59,8 @@ struct Prm {
   double inv_h, half_inv_h;  // 1/h and 1/(2h)
   int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
   double cfl, dt_max;        // adaptive time step (cfl > 0)
+  FastDiv dn0, dn1;          // division by n[0] and by n[1]
+  FastDiv dn0p, dn1p;        // division by n[0] + 1 and by n[1] + 1 (face arrays)
 };
 
 // Device arrays of one domain.
@@ -64,24 +84,6 @@ struct Fld {
   double *T[3], *Dd, *diag, *dinv, *b;
 };
 
-// Division by a divisor fixed for a level, without a hardware divide: for
-// 0 <= t < 2^31, t / d == (t * m) >> s with s = 31 + ceil(log2 d) and
-// m = ceil(2^s / d) < 2^32 (Granlund and Montgomery, "Division by invariant
-// integers using multiplication", 1994).
-struct FastDiv {
-  unsigned m;
-  unsigned s;
-};
-inline FastDiv make_fastdiv(unsigned d) {
-  unsigned l = 0;
-  while ((1ull << l) < d) l++;
-  const unsigned long long num = 1ull << (31 + l);
-  return FastDiv{(unsigned)((num + d - 1) / d), 31 + l};
-}
-__device__ __forceinline__ unsigned fastdiv(unsigned t, FastDiv f) {
-  return (unsigned)(((unsigned long long)t * f.m) >> f.s);
-}
-
 // One multigrid level (T is stored per cell for the face towards +axis).  In the
 // FP32 hierarchy of MDBS_MIXED_BF16 the coarse levels (l >= 1) keep T as BF16 bit
 // patterns in Tb (T is then NULL); every reader widens them to FP32.
@@ -90,7 +92,7 @@ struct Level {
   int n[3];
   int cz[3];  // axis coarsened relative to the finer level
   long long cells;
-  FastDiv dhalf, dn1;  // division by ceil(n[0] / 2) and by n[1]
+  FastDiv dhalf, dn0, dn1;  // division by ceil(n[0] / 2), by n[0] and by n[1]
   R* T[3];
   uint16_t* Tb[3];
   R* Dd;

@@ -37,7 +37,23 @@ __device__ __forceinline__ unsigned xs_px(unsigned he, int i) {
 __device__ __forceinline__ unsigned lpos(const int n[3], int i, int j, int k) {
   return (unsigned)n[0] * ((unsigned)j + (unsigned)n[1] * (unsigned)k) + xs_px((unsigned)(n[0] + 1) >> 1, i);
 }
-// storage position -> cell
+// storage position -> cell, with the divisions by n[0] and n[1] done by multiplication
+__device__ __forceinline__ void decode_pos(const int n[3], FastDiv dn0, FastDiv dn1, long long c, int& i, int& j,
+                                           int& k) {
+  const unsigned uc = (unsigned)c, n0 = (unsigned)n[0];
+  const unsigned row = fastdiv(uc, dn0), r = uc - row * n0, he = (n0 + 1) >> 1;
+  i = (int)(r < he ? 2 * r : 2 * (r - he) + 1);
+  const unsigned kk = fastdiv(row, dn1);
+  j = (int)(row - kk * (unsigned)n[1]);
+  k = (int)kk;
+}
+template <typename R>
+__device__ __forceinline__ void decode_pos(const Level<R>& L, long long c, int& i, int& j, int& k) {
+  decode_pos(L.n, L.dn0, L.dn1, c, i, j, k);
+}
+__device__ __forceinline__ void decode_pos(const Prm& P, long long c, int& i, int& j, int& k) {
+  decode_pos(P.n, P.dn0, P.dn1, c, i, j, k);
+}
 __device__ __forceinline__ void decode_pos(const int n[3], long long c, int& i, int& j, int& k) {
   const unsigned uc = (unsigned)c, n0 = (unsigned)n[0];
   const unsigned row = uc / n0, r = uc - row * n0, he = (n0 + 1) >> 1;
@@ -127,7 +143,7 @@ constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6
 // unknown faces and the fixed velocity on wall / inlet faces.
 __device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long c) {
   int q[3];
-  decode_pos(P.n, c, q[0], q[1], q[2]);  // c: storage position of the cell
+  decode_pos(P, c, q[0], q[1], q[2]);  // c: storage position of the cell
   const double A = P.A, A2 = P.A * P.A;
   double div = 0.0, Dd = 0.0;
   for (int d = 0; d < 3; d++) {
@@ -172,7 +188,7 @@ __device__ __forceinline__ R coef_lo(const Level<R>& L, int d, const int q[3], l
 template <typename R>
 __device__ __forceinline__ void b_diag(const Level<R>& L, long long c) {
   int q[3];
-  decode_pos(L.n, c, q[0], q[1], q[2]);
+  decode_pos(L, c, q[0], q[1], q[2]);
   R dg = R(0);
   for (int d = 0; d < 3; d++) {
     dg += tcoef(L, d, (unsigned)c);
@@ -219,7 +235,7 @@ __global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
 template <typename R>
 __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
-  decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
+  decode_pos(Co, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
   for (int a = 0; a < 3; a++) {
     lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -676,7 +692,7 @@ __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int 
 template <typename R>
 __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
-  decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
+  decode_pos(Co, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
   for (int a = 0; a < 3; a++) {
     lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -713,7 +729,7 @@ __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int
 template <typename R>
 __device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co, long long c) {
   int q[3];
-  decode_pos(Fi.n, c, q[0], q[1], q[2]);
+  decode_pos(Fi, c, q[0], q[1], q[2]);
   int Q[3];
   for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
   Fi.x[c] += Co.x[lpos(Co.n, Q[0], Q[1], Q[2])];
@@ -855,7 +871,7 @@ template <typename R>
 __device__ void tail_restrict(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
   for (unsigned ci = tp.first; ci < (unsigned)Co.cells; ci += tp.step) {
     int Q[3];
-    decode_pos(Co.n, ci, Q[0], Q[1], Q[2]);
+    decode_pos(Co, ci, Q[0], Q[1], Q[2]);
     int lo[3], hi[3];
     for (int a = 0; a < 3; a++) {
       lo[a] = Co.cz[a] ? 2 * Q[a] : Q[a];
@@ -879,7 +895,7 @@ template <typename R>
 __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co, const TailPart& tp) {
   for (unsigned c = tp.first; c < (unsigned)Fi.cells; c += tp.step) {
     int q[3];
-    decode_pos(Fi.n, c, q[0], q[1], q[2]);
+    decode_pos(Fi, c, q[0], q[1], q[2]);
     int Q[3];
     for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
     Fi.x[c] += Co.x[lpos(Co.n, Q[0], Q[1], Q[2])];
@@ -978,7 +994,7 @@ __global__ void k_resid0(const StepDom* __restrict__ D, const CgDom* __restrict_
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < S.P.cells) {
         int q[3];
-        decode_pos(S.P.n, c, q[0], q[1], q[2]);
+        decode_pos(S.P, c, q[0], q[1], q[2]);
         const double bc = S.F.b[c];
         const double rc = bc - apply_A0(S.F, S.P, S.F.p, (unsigned)c, q);
         G.r[c] = rc;
@@ -1016,7 +1032,7 @@ __global__ void k_spmv_dot(const StepDom* __restrict__ D, const CgDom* __restric
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         int i, j, k;
-        decode_pos(S.P.n, c, i, j, k);
+        decode_pos(S.P, c, i, j, k);
         const unsigned rb = (unsigned)n0 * ((unsigned)j + (unsigned)n1 * (unsigned)k), he = (unsigned)(n0 + 1) >> 1;
         const unsigned cm = rb + xs_px(he, i - 1), cp = rb + xs_px(he, i + 1);
         const double dc = dv[c];
@@ -1057,7 +1073,7 @@ __global__ void k_update_xr(const StepDom* __restrict__ D, const CgDom* __restri
       const long long c = ((long long)lb * REP + r) * blockDim.x + threadIdx.x;
       if (c < n) {
         // p is in natural order: the cell at x-split position c
-        const unsigned row = (unsigned)c / n0, x = (unsigned)c - row * n0;
+        const unsigned row = fastdiv((unsigned)c, S.P.dn0), x = (unsigned)c - row * n0;
         p[row * n0 + (x < he ? 2 * x : 2 * (x - he) + 1)] += al * dv[c];
         const double rc = rv[c] - al * qv[c];
         rv[c] = rc;
@@ -1357,6 +1373,7 @@ static size_t solver_layout(const int n[3], int precision, PressureSolver* ps, c
     }
     Ld.cells = Lf.cells = nc;
     Ld.dhalf = Lf.dhalf = make_fastdiv((unsigned)(dims[l][0] + 1) / 2);
+    Ld.dn0 = Lf.dn0 = make_fastdiv((unsigned)dims[l][0]);
     Ld.dn1 = Lf.dn1 = make_fastdiv((unsigned)dims[l][1]);
     if (precision == 0) {
       if (l > 0) {

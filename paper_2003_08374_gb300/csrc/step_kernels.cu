@@ -27,12 +27,14 @@ __device__ __forceinline__ bool decode_face(const Prm& P, long long t, int& d, i
     return false;
   }
   // 32-bit decode: mdbs_create limits every array to fewer than 2^31 entries
+  // (divisions by multiplication with the domain's invariant-divisor constants)
   const unsigned fx = P.n[0] + (d == 0), fy = P.n[1] + (d == 1);
   const unsigned uf = (unsigned)f;
-  i = (int)(uf % fx);
-  const unsigned r = uf / fx;
-  j = (int)(r % fy);
-  k = (int)(r / fy);
+  const unsigned r = fastdiv(uf, d == 0 ? P.dn0p : P.dn0);
+  i = (int)(uf - r * fx);
+  const unsigned kk = fastdiv(r, d == 1 ? P.dn1p : P.dn1);
+  j = (int)(r - kk * fy);
+  k = (int)kk;
   return true;
 }
 
@@ -42,10 +44,11 @@ __device__ __forceinline__ long long total_faces(const Prm& P) {
 
 __device__ __forceinline__ void decode_cell(const Prm& P, long long c, int& i, int& j, int& k) {
   const unsigned uc = (unsigned)c;
-  i = (int)(uc % (unsigned)P.n[0]);
-  const unsigned r = uc / (unsigned)P.n[0];
-  j = (int)(r % (unsigned)P.n[1]);
-  k = (int)(r / (unsigned)P.n[1]);
+  const unsigned r = fastdiv(uc, P.dn0);
+  i = (int)(uc - r * (unsigned)P.n[0]);
+  const unsigned kk = fastdiv(r, P.dn1);
+  j = (int)(r - kk * (unsigned)P.n[1]);
+  k = (int)kk;
 }
 
 // central difference of a cell field along e at (i,j,k), zero-gradient ghosts
