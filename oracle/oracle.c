@@ -76,6 +76,26 @@ static double cval(const orc_state* s, const double* a, const int c[3]) {
   for (int e = 0; e < 3; e++) q[e] = clampi(c[e], 0, s->n[e] - 1);
   return a[cidv(s, q)];
 }
+/* Van Leer limited face value (section 3.1): the upwind value plus half the
+ * limited difference toward the downwind cell, psi(r) = (r + |r|)/(1 + |r|)
+ * with r the ratio of the upwind to the face difference; psi -> 2 as r -> +inf
+ * (a face difference too small for the ratio to be finite). */
+static double van_leer(double aU, double aD, double aUU) {
+  double den = aD - aU;
+  if (den == 0.0) return aU;
+  double r = (aU - aUU) / den;
+  double psi = isinf(r) ? (r > 0.0 ? 2.0 : 0.0) : (r + fabs(r)) / (1.0 + fabs(r));
+  return aU + 0.5 * psi * den;
+}
+/* liquid fractional flow M_l / M of the cell at c (clamped into the grid like
+ * cval); a cell without mobilities (solid-free) gives its saturation */
+static double frac_flow(const orc_state* s, const int c[3]) {
+  int q[3];
+  for (int e = 0; e < 3; e++) q[e] = clampi(c[e], 0, s->n[e] - 1);
+  long i = cidv(s, q);
+  double M = s->Ml[i] + s->Mg[i];
+  return M > 0.0 ? s->Ml[i] / M : s->alpha[i];
+}
 static void cpy3(int dst[3], const int src[3]) { dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; }
 static void coords_of(const int n[3], long idx, int c[3]) {
   c[0] = (int)(idx % n[0]);
@@ -273,15 +293,7 @@ static void alpha_step(orc_state* s, double dt) {
             }
             aUU = cval(s, s->alpha, UU);
             double flo = Q * aU; /* upwind (low order) flux */
-            /* Van Leer limited face value (section 3.1) */
-            double den = aD - aU, avl;
-            if (den == 0.0) {
-              avl = aU;
-            } else {
-              double rr = (aU - aUU) / den;
-              double psi = (rr + fabs(rr)) / (1.0 + fabs(rr));
-              avl = aU + 0.5 * psi * den;
-            }
+            double avl = van_leer(aU, aD, aUU);
             double Rf = 0.0;
             if (s->is_free[l] && s->is_free[r]) {
               /* compression relative velocity in solid-free faces, Eq. 22
@@ -301,17 +313,26 @@ static void alpha_step(orc_state* s, double dt) {
               else
                 Rf = w * s->alpha[r] * (1.0 - s->alpha[l]);
             } else if (!s->is_free[l] && !s->is_free[r]) {
-              /* porous relative flux phi a_l a_g v_r, Eq. 34 multiplied
-               * through by a_l a_g so that it stays regular at a -> 0, 1 */
-              double af = 0.5 * (s->alpha[l] + s->alpha[r]), agf = 1.0 - af;
-              double Mlf = 0.5 * (s->Ml[l] + s->Ml[r]), Mgf = 0.5 * (s->Mg[l] + s->Mg[r]);
-              double pcf = 0.5 * (s->pc[l] + s->pc[r]);
-              double dp = (s->p[r] - s->p[l]) / h;
-              double dpc = (s->pc[r] - s->pc[l]) / h;
-              double da = (s->alpha[r] - s->alpha[l]) / h;
-              double cm = agf * Mlf - af * Mgf;
-              Rf = A * (-cm * dp + (agf * P->rho_l * Mlf - af * P->rho_g * Mgf) * P->g[d] +
-                        (Mlf * agf * agf + Mgf * af * af) * dpc - cm * pcf * da);
+              /* porous relative flux phi a_l a_g v_r (Eq. 34).  With the
+               * single-field velocity v = v_l + v_g (section 2.2), the liquid
+               * Darcy flux a_l v + phi a_l a_g v_r of Eq. 34 equals
+               * f v + lambda [(rho_l - rho_g) g + grad pc],
+               * f = M_l / M, lambda = M_l M_g / M; Eq. 34 rewritten that way is
+               * discretised with the face flux Q itself: f by the same Van Leer
+               * limited upwind value as alpha (section 3.1), lambda by phase
+               * upwinding along the gravity-capillary drive.  The relative flux is
+               * that liquid flux minus the convective part Q * avl. */
+              int Ucell[3], Dcell[3];
+              cpy3(Ucell, Q >= 0.0 ? L : R);
+              cpy3(Dcell, Q >= 0.0 ? R : L);
+              double fU = frac_flow(s, Ucell), fD = frac_flow(s, Dcell), fUU = frac_flow(s, UU);
+              double fvl = van_leer(fU, fD, fUU);
+              double drive = (P->rho_l - P->rho_g) * P->g[d] + (s->pc[r] - s->pc[l]) / h;
+              /* liquid from the cell the drive pushes it out of, gas from the other */
+              double mlw = drive >= 0.0 ? s->Ml[l] : s->Ml[r];
+              double mgw = drive >= 0.0 ? s->Mg[r] : s->Mg[l];
+              double lam = (mlw + mgw) > 0.0 ? mlw * mgw / (mlw + mgw) : 0.0;
+              Rf = Q * (fvl - avl) + A * lam * drive;
             }
             s->FLO[d][f] = flo;
             s->AF[d][f] = (Q * avl + Rf) - flo; /* anti-diffusive flux */

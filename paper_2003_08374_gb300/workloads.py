@@ -16,6 +16,8 @@ identical arrays.  Recipes:
   and a solitary-wave free surface (stand-in for section 5.1).
 * ``darcy_domain`` -- porous-only domain with a random porosity field mapped
   into [0.1, 0.9] and uniform initial saturation (batched / served domains).
+* ``buckley_leverett`` -- the Darcy-scale 1-D column of sections 4.1.1-4.1.2
+  (water injected into air or oil, optional gravity along the flow).
 
 Every array is x-fastest: cell c = i + nx*(j + ny*k).  Face arrays hold
 (nx+1)*ny*nz x-faces, nx*(ny+1)*nz y-faces and nx*ny*(nz+1) z-faces; a 2-D
@@ -226,6 +228,38 @@ def darcy_domain(shape, seed, corr_len=4.0, sat=None, inlet_u=1e-4, **kw) -> Cas
     c.alpha = np.full(nx * ny * nz, s0)
     _zero_fields(c)
     _plug_flow(c, c.inlet_u)
+    return c
+
+
+DISPLACED = {"air": (1.0, 1.76e-5), "oil": (800.0, 0.1)}  # Table 1: (density, viscosity)
+
+
+def buckley_leverett(nx=2000, length=4.0, displaced="air", kr_model=BROOKS_COREY, kr_m=None,
+                     gravity=False, phi=0.5, k0=1e-11, u=1e-5, cfl=None, **kw) -> Case:
+    """Darcy-scale 1-D column of section 4.1.1 (4 m, 2000 cells, porosity 0.5, k0 = 1e-11 m^2):
+    water (1000, 1e-3) injected at u = 1e-5 m/s through x- into a column saturated with air or
+    oil (Table 1), outlet at p = 0 on x+, no capillary pressure.  Relative permeability by
+    Brooks-Corey (m = 3) or Van Genuchten (m = 0.5), Table 2.  ``gravity`` adds g = 9.81 m/s^2
+    along the injection direction (section 4.1.2).  The time step follows the CFL number on
+    the face velocity; the default keeps the saturation Courant number below about 0.3 for
+    these fluids (the fractional-flow wave speeds reach about 3 u / phi)."""
+    rho_g, mu_g = DISPLACED[displaced]
+    if kr_m is None:
+        kr_m = 3.0 if kr_model == BROOKS_COREY else 0.5
+    if cfl is None:
+        cfl = 0.02 if gravity else 0.05
+    h = length / nx
+    name = "buckley_leverett_%s_%s%s_%d" % (displaced, "bc" if kr_model == BROOKS_COREY else "vg",
+                                            "_gravity" if gravity else "", nx)
+    c = Case(name=name, nx=nx, ny=1, nz=1, h=h, rho_l=1000.0, mu_l=1e-3, rho_g=rho_g, mu_g=mu_g,
+             sigma=0.0, pc0=0.0, kr_model=kr_model, kr_m=kr_m, g=(9.81 if gravity else 0.0, 0.0, 0.0),
+             cfl=cfl, dt=cfl * h / u, dt_max=1e9, inlet_u=u, inlet_alpha=1.0, p_tol=1e-12, max_cg=300)
+    c = c.replace(**kw)
+    c.porosity = np.full(nx, float(phi))
+    c.permeability = np.full(nx, float(k0))
+    c.alpha = np.zeros(nx)
+    _zero_fields(c)
+    _plug_flow(c, u)
     return c
 
 
