@@ -72,10 +72,28 @@ __device__ __forceinline__ double warp_reduce_max(double v) {
 
 
 // ------------------------------------------------------------------ saturation
+// Van Leer limited face value (section 3.1): aU + (1/2) psi(r) (aD - aU) with
+// psi(r) = (r+|r|)/(1+|r|), r = (aU-aUU)/(aD-aU), evaluated without the ratio
+// as aU + ab/(a+b) when ab > 0 (a = aU - aUU, b = aD - aU).
+__device__ __forceinline__ double van_leer(double aU, double aD, double aUU) {
+  const double ga = aU - aUU, gb = aD - aU;
+  return (ga * gb > 0.0) ? aU + ga * gb / (ga + gb) : aU;
+}
+
+// liquid fractional flow M_l / M of a cell; a cell without mobilities gives alpha
+__device__ __forceinline__ double frac_flow(const Fld& F, long long c) {
+  const double ml = F.Ml[c], M = ml + F.Mg[c];
+  return M > 0.0 ? ml / M : F.alpha[c];
+}
+
 // Face fluxes of the saturation equation (Eq. 15): upwind (low-order) flux,
 // Van Leer high-order flux (section 3.1) plus the relative-velocity flux --
-// compression in solid-free faces (Eq. 22 oriented as Eq. 41) or the porous
-// phase-flux difference (Eq. 34 times a_l a_g).  AF = high - low order.
+// compression in solid-free faces (Eq. 22 oriented as Eq. 41), or in porous faces
+// the relative flux phi a_l a_g v_r of Eq. 34 in total-velocity form: with
+// v = v_l + v_g the liquid Darcy flux is f v + lambda [(rho_l - rho_g) g + grad pc]
+// (f = M_l / M, lambda = M_l M_g / M), taken with the face flux Q, f Van Leer
+// limited like alpha and lambda phase-upwinded along the gravity-capillary drive;
+// the relative flux is that minus Q * avl.  AF = high - low order.
 // returns the boundary inflow of face t (0 for interior faces)
 __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long long t) {
   double inflow = 0.0;
@@ -92,21 +110,15 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
       const long long l = cell_index(P.n, i - di, j - dj, k - dk);
       const long long r = cell_index(P.n, i, j, k);
       const double al = F.alpha[l], ar = F.alpha[r];
-      double aU, aD, aUU;
-      if (Q >= 0.0) {
-        aU = al;
-        aD = ar;
-        aUU = ghost_read(F.alpha, P.n, i - 2 * di, j - 2 * dj, k - 2 * dk);
-      } else {
-        aU = ar;
-        aD = al;
-        aUU = ghost_read(F.alpha, P.n, i + di, j + dj, k + dk);
-      }
+      // upwind, downwind and second-upwind cells (the last clamped into the grid)
+      const bool pos = Q >= 0.0;
+      const long long uc = pos ? l : r, dc = pos ? r : l;
+      const int s2 = pos ? -2 : 1;
+      const long long uu = cell_index(P.n, clampi(i + s2 * di, 0, P.n[0] - 1), clampi(j + s2 * dj, 0, P.n[1] - 1),
+                                      clampi(k + s2 * dk, 0, P.n[2] - 1));
+      const double aU = pos ? al : ar, aD = pos ? ar : al, aUU = F.alpha[uu];
       const double flo = Q * aU;
-      // Van Leer: aU + (1/2) psi(r) (aD - aU), psi(r) = (r+|r|)/(1+|r|), r = (aU-aUU)/(aD-aU),
-      // evaluated without the ratio: aU + ab/(a+b) when ab > 0.
-      const double ga = aU - aUU, gb = aD - aU;
-      const double avl = (ga * gb > 0.0) ? aU + ga * gb / (ga + gb) : aU;
+      const double avl = van_leer(aU, aD, aUU);
       double rel = 0.0;
       const bool fl = F.is_free[l], fr = F.is_free[r];
       if (fl && fr) {
@@ -118,16 +130,13 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
         const double w = P.c_alpha * fabs(uf) * nfc * P.A;
         rel = (w >= 0.0) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
       } else if (!fl && !fr) {
-        const double af = 0.5 * (al + ar), agf = 1.0 - af;
-        const double Mlf = 0.5 * (F.Ml[l] + F.Ml[r]), Mgf = 0.5 * (F.Mg[l] + F.Mg[r]);
-        const double pcl = F.pc[l], pcr = F.pc[r];
-        const double pcf = 0.5 * (pcl + pcr);
-        const double dp = (F.p[r] - F.p[l]) * inv_h;
-        const double dpc = (pcr - pcl) * inv_h;
-        const double da = (ar - al) * inv_h;
-        const double cm = agf * Mlf - af * Mgf;
-        rel = P.A * (-cm * dp + (agf * P.rho_l * Mlf - af * P.rho_g * Mgf) * P.g[d] +
-                     (Mlf * agf * agf + Mgf * af * af) * dpc - cm * pcf * da);
+        const double fvl = van_leer(frac_flow(F, uc), frac_flow(F, dc), frac_flow(F, uu));
+        const double drive = (P.rho_l - P.rho_g) * P.g[d] + (F.pc[r] - F.pc[l]) * inv_h;
+        // liquid from the cell the drive pushes it out of, gas from the other
+        const bool fwd = drive >= 0.0;
+        const double mlw = fwd ? F.Ml[l] : F.Ml[r], mgw = fwd ? F.Mg[r] : F.Mg[l];
+        const double lam = (mlw + mgw) > 0.0 ? mlw * mgw / (mlw + mgw) : 0.0;
+        rel = Q * (fvl - avl) + P.A * lam * drive;
       }
       F.FLO[d][f] = flo;
       F.AF[d][f] = (Q * avl + rel) - flo;

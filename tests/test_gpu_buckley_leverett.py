@@ -1,0 +1,118 @@
+"""The Darcy-scale 1-D column of sections 4.1.1-4.1.2 on the CUDA path.
+
+* Parity with the oracle over hundreds of steps, element by element, for water
+  into oil (Brooks-Corey), water into air with gravity (Van Genuchten) and a
+  ragged column length, in FP64 and in mixed precision.
+* The paper's own size (4 m, 2000 cells) run to a front near 1.6 m: the first
+  steps against the oracle, the end against the semi-analytic Welge profile.
+* A batch of columns steps exactly like the columns alone."""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-9
+TOLMIX = 1e-6
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_08374_gb300.build import build_library
+    from oracle.build import build_oracle
+    build_library()
+    build_oracle()
+
+
+def rel(a, b):
+    nb = np.linalg.norm(b)
+    return float(np.linalg.norm(a - b) / nb) if nb > 0 else float(np.linalg.norm(a))
+
+
+def _cases(precision):
+    from paper_2003_08374_gb300 import workloads as W
+    return [
+        W.buckley_leverett(nx=300, displaced="oil", p_tol=1e-14, precision=precision),
+        W.buckley_leverett(nx=200, length=0.5, displaced="air", kr_model=W.VAN_GENUCHTEN, gravity=True,
+                           p_tol=1e-14, precision=precision),
+        W.buckley_leverett(nx=257, displaced="air", kr_model=W.BROOKS_COREY, p_tol=1e-14,
+                           precision=precision),
+    ]
+
+
+@pytest.mark.parametrize("precision,tol", [(0, TOL64), (1, TOLMIX)])
+def test_columns_match_oracle_over_many_steps(precision, tol):
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    for case in _cases(precision):
+        g, o = mdbs.Simulation(case), OracleSim(case)
+        for _ in range(4):
+            g.step(100)
+            o.step(100)
+            fg, fo = g.fields(), o.fields()
+            errs = {k: rel(fg[k], fo[k]) for k in ("alpha", "p", "ux")}
+            assert all(e <= tol for e in errs.values()), (case.name, errs)
+        sg, so = g.stats(), o.stats()
+        assert sg["steps"] == so["steps"] == 400
+        assert abs(sg["time"] - so["time"]) <= 1e-12 * so["time"]
+        assert abs(sg["mass"] - so["mass"]) <= 1e-9 * so["mass"]
+        assert 0.0 < fg["alpha"].max() <= 1.0 + 1e-12 and fg["alpha"].min() >= -1e-12
+        g.close()
+        o.close()
+
+
+def _welge(x, t, mu_g, m, u=1e-5, phi=0.5, mu_l=1e-3):
+    """Brooks-Corey semi-analytic profile (S = 1 injected into S = 0)."""
+    S = np.linspace(0.0, 1.0, 400001)[1:]
+    f = S ** m / mu_l / (S ** m / mu_l + (1.0 - S) ** m / mu_g)
+    df = np.gradient(f, S)
+    i = int(np.argmax(f / S))
+    xf = u * t * f[i] / S[i] / phi
+    out = np.zeros_like(x)
+    xs = u * t * df[i:] / phi
+    behind = x <= xf
+    out[behind] = np.interp(x[behind], xs[::-1], S[i:][::-1])
+    return out, xf
+
+
+def test_paper_column_against_oracle_and_welge():
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.buckley_leverett(nx=2000, displaced="oil")  # 4 m, 2000 cells, phi 0.5, k0 1e-11
+    g, o = mdbs.Simulation(case), OracleSim(case)
+    g.step(300)
+    o.step(300)
+    fg, fo = g.fields(), o.fields()
+    assert rel(fg["alpha"], fo["alpha"]) <= TOL64
+    o.close()
+    _, xf1 = _welge(np.zeros(1), 1.0, 0.1, 3.0)
+    t_end = 1.6 / xf1
+    while g.stats()["time"] < t_end:
+        g.step(50)
+    st = g.stats()
+    a = g.fields()["alpha"]
+    x = (np.arange(case.nx) + 0.5) * case.h
+    ex, xf = _welge(x, st["time"], 0.1, 3.0)
+    err = float(np.abs(a - ex).sum() / np.abs(ex).sum())
+    assert err <= 2.5e-3, err
+    assert abs(st["mass"] - st["boundary_in"]) <= 1e-12 * st["mass"]
+    g.close()
+
+
+def test_batch_of_columns_equals_columns_alone():
+    from paper_2003_08374_gb300 import mdbs
+    cases = _cases(0)
+    alone = []
+    for c in cases:
+        s = mdbs.Simulation(c)
+        s.step(200)
+        alone.append(s.fields())
+        s.close()
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims)
+    b.step(200)
+    for s, fa in zip(sims, alone):
+        fb = s.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+    b.close()
