@@ -48,7 +48,8 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched", "serving"])
+    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched", "serving", "buckley_leverett"])
+    ap.add_argument("--columns", type=int, default=512, help="buckley_leverett: columns in the batch")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window [s]")
     ap.add_argument("--max-side", type=int, default=96, help="serving: largest cube side")
@@ -472,6 +473,99 @@ def batched_arm(args):
     return 0
 
 
+def bl_columns(count, nx=2000):
+    """Darcy-scale columns of sections 4.1.1-4.1.2 (4 m, 2000 cells), cycling through water
+    into oil / air, Brooks-Corey / Van Genuchten and gravity off / on."""
+    from paper_2003_08374_gb300 import workloads as W
+    kinds = [(d, m, g) for g in (False, True) for m in (W.BROOKS_COREY, W.VAN_GENUCHTEN) for d in ("oil", "air")]
+    return [W.buckley_leverett(nx=nx, displaced=kinds[i % 8][0], kr_model=kinds[i % 8][1], gravity=kinds[i % 8][2])
+            for i in range(count)]
+
+
+def bl_arm(args):
+    """The 1-D Buckley-Leverett column: one column alone (latency of a step: a 2000-cell
+    step is bound by launch and dependency latency, not by memory) and a batch of
+    columns advanced together (the whole-job number)."""
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2003_08374_gb300.build import build_library
+    build_library()
+    from paper_2003_08374_gb300 import mdbs
+    stream = torch.cuda.current_stream()
+
+    def run(obj, steps, warmup):
+        for _ in range(warmup):
+            obj.step(1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            obj.step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    def single(precision):
+        """One column alone, autotuned: graph steps, then an eager pass with events per kernel."""
+        c = bl_columns(1)[0].replace(precision=precision)
+        one = mdbs.Simulation(c)
+        one.set_stream(stream.cuda_stream)
+        tun = pick_schedule(one, args, trial_steps=2)[0]
+        l0 = one.stats()["kernel_launches"]
+        ms1 = run(one, args.steps, args.warmup)
+        st1 = one.stats()
+        out = {"precision": "fp64" if precision == 0 else "mixed", "ms_per_step": ms1 / args.steps,
+               "cell_steps_per_s": c.cells * args.steps / (ms1 / 1e3),
+               "gpu_launches_per_step": (st1["kernel_launches"] - l0) / (args.steps + args.warmup),
+               "cg_iters_last_step": st1["cg_iters"], "tuning": tun}
+        one.profile(True, only=None)
+        run(one, args.steps, 0)
+        prof = one.profile_read()
+        one.profile(False)
+        one.close()
+        out["kernel_ms_per_step"] = {k: round(v[0] / args.steps, 4)
+                                     for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
+        return out, prof
+
+    case = bl_columns(1)[0]
+    single64, prof = single(0)
+    single32, _ = single(1)
+    top, (top_ms, top_n) = max(prof.items(), key=lambda kv: kv[1][0])
+
+    cases = bl_columns(args.columns)
+    cells = sum(c.cells for c in cases)
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims)
+    b.set_stream(stream.cuda_stream)
+    tuning, tune_ms = pick_schedule(b, args, trial_steps=1)
+    with ClockSampler(local) as clk:
+        ms = run(b, args.steps, args.warmup)
+    iters = [s.stats()["cg_iters"] for s in sims]
+    b.close()
+
+    cpu = None
+    if not args.no_cpu_baseline:
+        cval, csec = time_oracle(case, 200, 0)
+        cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": "200 oracle steps of one 2000-cell column (water into oil, Brooks-Corey), %.1f s" % csec}
+    pk = peaks()
+    hbm_peak = pk["hbm_gbs"] if pk else 6800.0
+    line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "buckley_leverett_%d_columns_2000_cells" % len(cases), "cells": cells,
+                       "cg_iters_max": max(max(i) for i in iters), "tuning": tuning,
+                       "l2": "inputs smaller than L2 (a latency-bound workload)"},
+            "single_column": single64, "single_column_mixed": single32,
+            "roofline": {"bound": "hbm", "kernel": top, "avg_us": top_ms / top_n * 1e3,
+                         "achieved": None, "peak": hbm_peak, "unit": "GB/s", "frac": None, "traffic": None,
+                         "note": "a 2000-cell step moves about 1 MB: latency-bound, no memory roofline applies"},
+            "cpu_baseline": cpu, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def serving_arm(args):
     """Continuous batching of a seeded Poisson trace of fractured-porous requests (sides
     log-uniform in [32, max_side], capillary number log-uniform in [1e-5, 1e-2])."""
@@ -512,6 +606,8 @@ def main():
         return reference_arm(args)
     if args.workload == "batched":
         return batched_arm(args)
+    if args.workload == "buckley_leverett":
+        return bl_arm(args)
     return gpu_arm(args)
 
 

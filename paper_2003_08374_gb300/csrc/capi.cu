@@ -194,6 +194,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   F.p = cd();
   F.Ml = cd();
   F.Mg = cd();
+  F.fw = cd();
   F.pc = cd();
   F.cf = cd();
   F.rho = cd();

@@ -75,16 +75,19 @@ __device__ __forceinline__ double warp_reduce_max(double v) {
 // Van Leer limited face value (section 3.1): aU + (1/2) psi(r) (aD - aU) with
 // psi(r) = (r+|r|)/(1+|r|), r = (aU-aUU)/(aD-aU), evaluated without the ratio
 // as aU + ab/(a+b) when ab > 0 (a = aU - aUU, b = aD - aU).
+// (FP64 division is the costliest operation of the face flux: it is branched
+// around, not selected, where the limiter is zero.)
 __device__ __forceinline__ double van_leer(double aU, double aD, double aUU) {
   const double ga = aU - aUU, gb = aD - aU;
-  return (ga * gb > 0.0) ? aU + ga * gb / (ga + gb) : aU;
+  const double ab = ga * gb;
+  double v = aU;
+  if (ab > 0.0) v = aU + ab / (ga + gb);
+  return v;
 }
 
-// liquid fractional flow M_l / M of a cell; a cell without mobilities gives alpha
-__device__ __forceinline__ double frac_flow(const Fld& F, long long c) {
-  const double ml = F.Ml[c], M = ml + F.Mg[c];
-  return M > 0.0 ? ml / M : F.alpha[c];
-}
+// liquid fractional flow M_l / M of a cell, stored by the closures (alpha in a
+// solid-free cell, which has no mobilities)
+__device__ __forceinline__ double frac_flow(const Fld& F, long long c) { return F.fw[c]; }
 
 // Face fluxes of the saturation equation (Eq. 15): upwind (low-order) flux,
 // Van Leer high-order flux (section 3.1) plus the relative-velocity flux --
@@ -93,7 +96,8 @@ __device__ __forceinline__ double frac_flow(const Fld& F, long long c) {
 // v = v_l + v_g the liquid Darcy flux is f v + lambda [(rho_l - rho_g) g + grad pc]
 // (f = M_l / M, lambda = M_l M_g / M), taken with the face flux Q, f Van Leer
 // limited like alpha and lambda phase-upwinded along the gravity-capillary drive;
-// the relative flux is that minus Q * avl.  AF = high - low order.
+// the relative flux is that minus Q * avl.  AF = high - low order.  Mixed
+// solid-free / porous faces carry no relative flux.
 // returns the boundary inflow of face t (0 for interior faces)
 __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long long t) {
   double inflow = 0.0;
@@ -118,28 +122,36 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
                                       clampi(k + s2 * dk, 0, P.n[2] - 1));
       const double aU = pos ? al : ar, aD = pos ? ar : al, aUU = F.alpha[uu];
       const double flo = Q * aU;
-      const double avl = van_leer(aU, aD, aUU);
-      double rel = 0.0;
       const bool fl = F.is_free[l], fr = F.is_free[r];
-      if (fl && fr) {
-        double gf[3] = {0.0, 0.0, 0.0};
-        for (int e = 0; e < P.dim; e++)
-          gf[e] = 0.5 * (cgrad(F.alpha, P, e, i - di, j - dj, k - dk) + cgrad(F.alpha, P, e, i, j, k));
-        const double mag = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
-        const double nfc = gf[d] / (mag + 1e-8 * inv_h);
-        const double w = P.c_alpha * fabs(uf) * nfc * P.A;
-        rel = (w >= 0.0) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
-      } else if (!fl && !fr) {
+      double hi;  // high-order liquid flux of the face
+      if (!fl && !fr) {
+        // Q avl + (relative flux) = Q f_vl + A lambda drive: the Van Leer value of
+        // alpha cancels, so porous faces do not form it
         const double fvl = van_leer(frac_flow(F, uc), frac_flow(F, dc), frac_flow(F, uu));
         const double drive = (P.rho_l - P.rho_g) * P.g[d] + (F.pc[r] - F.pc[l]) * inv_h;
-        // liquid from the cell the drive pushes it out of, gas from the other
-        const bool fwd = drive >= 0.0;
-        const double mlw = fwd ? F.Ml[l] : F.Ml[r], mgw = fwd ? F.Mg[r] : F.Mg[l];
-        const double lam = (mlw + mgw) > 0.0 ? mlw * mgw / (mlw + mgw) : 0.0;
-        rel = Q * (fvl - avl) + P.A * lam * drive;
+        hi = Q * fvl;
+        if (drive != 0.0) {
+          // liquid from the cell the drive pushes it out of, gas from the other
+          const bool fwd = drive >= 0.0;
+          const double mlw = fwd ? F.Ml[l] : F.Ml[r], mgw = fwd ? F.Mg[r] : F.Mg[l];
+          const double msum = mlw + mgw;
+          if (msum > 0.0) hi += P.A * (mlw * mgw / msum) * drive;
+        }
+      } else {
+        double rel = 0.0;
+        if (fl && fr) {
+          double gf[3] = {0.0, 0.0, 0.0};
+          for (int e = 0; e < P.dim; e++)
+            gf[e] = 0.5 * (cgrad(F.alpha, P, e, i - di, j - dj, k - dk) + cgrad(F.alpha, P, e, i, j, k));
+          const double mag = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
+          const double nfc = gf[d] / (mag + 1e-8 * inv_h);
+          const double w = P.c_alpha * fabs(uf) * nfc * P.A;
+          rel = (w >= 0.0) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
+        }
+        hi = Q * van_leer(aU, aD, aUU) + rel;
       }
       F.FLO[d][f] = flo;
-      F.AF[d][f] = (Q * avl + rel) - flo;
+      F.AF[d][f] = hi - flo;
     } else {
       const bool high = cd != 0;
       const int side = 2 * d + (high ? 1 : 0);
@@ -273,6 +285,7 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
   if (F.is_free[c]) {
     F.Ml[c] = 0.0;
     F.Mg[c] = 0.0;
+    F.fw[c] = a;
     F.drag[c] = 0.0;
     F.pc[c] = 0.0;
     F.cf[c] = 0.0;
@@ -312,6 +325,7 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
     pc = P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
   F.Ml[c] = Ml;
   F.Mg[c] = Mg;
+  F.fw[c] = Ml / M;  // M > 0 in porous cells: k0 > 0 and k_rl + k_rg > 0
   const double inv_M = 1.0 / M;
   F.drag[c] = inv_M;
   F.rho[c] = (P.rho_l * Ml + P.rho_g * Mg) * inv_M;
