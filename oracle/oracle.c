@@ -48,7 +48,7 @@ struct orc_state {
   double* nw[3];
   double *alpha, *p, *u[3];
   /* properties */
-  double *Ml, *Mg, *pc, *cf, *rho, *rho_old, *mu, *drag, *m[3], *kappa;
+  double *Ml, *Mg, *pc, *cf, *rho, *mu, *drag, *m[3], *kappa;
   /* alpha step */
   double *FLO[3], *AF[3], *aL, *Rp, *Rm;
   /* momentum */
@@ -462,7 +462,6 @@ static void momentum_assemble(orc_state* s, double dt) {
           L[d] -= 1;
           double phif = 0.5 * (cval(s, s->phi, L) + cval(s, s->phi, R));
           double rhof = 0.5 * (cval(s, s->rho, L) + cval(s, s->rho, R));
-          double rhoo = 0.5 * (cval(s, s->rho_old, L) + cval(s, s->rho_old, R));
           double Df = 0.5 * (cval(s, s->drag, L) + cval(s, s->drag, R));
           /* face body force: gravity rho g (Eq. 45 density) and capillary F_c */
           double G = rhof * P->g[d];
@@ -480,9 +479,14 @@ static void momentum_assemble(orc_state* s, double dt) {
             }
           }
           s->B[d][f] = G + F;
-          /* Euler implicit inertia with the 1/phi factors of Eq. 21 */
+          /* Euler implicit inertia with the 1/phi factors of Eq. 21, in
+           * advective form rho^{k+1} (v^{k+1} - v^k) / dt: with the upwind
+           * advective convection below it is the same equation as the
+           * conservative form, which would need momentum fluxes consistent
+           * with the saturation fluxes (a water/air interface leaving a face
+           * otherwise hands water momentum to air) */
           double at = V * rhof / (phif * dt);
-          double S = V * rhoo * s->u[d][f] / (phif * dt);
+          double S = at * s->u[d][f];
           double cconv = V * rhof / (phif * phif * h);
           double ap = at + V * Df; /* Darcy drag K_fs, Eq. 46 */
           double TT = 0.0;        /* explicit div(mu grad(v)^T) */
@@ -1093,7 +1097,6 @@ orc_state* orc_create(const orc_params* prm, const double* porosity, const doubl
   s->pc = CA(nc);
   s->cf = CA(nc);
   s->rho = CA(nc);
-  s->rho_old = CA(nc);
   s->mu = CA(nc);
   s->drag = CA(nc);
   s->kappa = CA(nc);
@@ -1176,10 +1179,7 @@ int orc_step(orc_state* s, int nsteps) {
     double dt = s->dt;
     /* 1. saturation */
     alpha_step(s, dt);
-    /* 3. properties at alpha^{k+1}; rho^k kept for the inertia source */
-    double* t = s->rho_old;
-    s->rho_old = s->rho;
-    s->rho = t;
+    /* 3. properties at alpha^{k+1} */
     update_props(s);
     normals_curvature(s);
     /* 4. momentum predictor */
@@ -1241,7 +1241,7 @@ long orc_get_array(const orc_state* s, const char* name, double* out) {
     const double* a;
     long n;
   } tab[] = {
-      {"rho", s->rho, s->cells},        {"rho_old", s->rho_old, s->cells}, {"mu", s->mu, s->cells},
+      {"rho", s->rho, s->cells},        {"mu", s->mu, s->cells},
       {"drag", s->drag, s->cells},      {"pc", s->pc, s->cells},           {"cf", s->cf, s->cells},
       {"Ml", s->Ml, s->cells},          {"Mg", s->Mg, s->cells},           {"kappa", s->kappa, s->cells},
       {"mx", s->m[0], s->cells},        {"my", s->m[1], s->cells},         {"mz", s->m[2], s->cells},
@@ -1283,7 +1283,6 @@ void orc_destroy(orc_state* s) {
   free(s->pc);
   free(s->cf);
   free(s->rho);
-  free(s->rho_old);
   free(s->mu);
   free(s->drag);
   free(s->kappa);

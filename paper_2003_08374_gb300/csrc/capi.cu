@@ -198,7 +198,6 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   F.pc = cd();
   F.cf = cd();
   F.rho = cd();
-  F.rho_old = cd();
   F.mu = cd();
   F.drag = cd();
   for (int e = 0; e < 3; e++) F.m[e] = cd();
@@ -1041,7 +1040,7 @@ int64_t mdbs_debug_array(const mdbs_sim* cs, const char* name, double* out, int6
     const double* a;
     long long n;
   } tab[] = {
-      {"rho", F.rho, nc},          {"rho_old", F.rho_old, nc},  {"mu", F.mu, nc},
+      {"rho", F.rho, nc},          {"mu", F.mu, nc},
       {"drag", F.drag, nc},        {"pc", F.pc, nc},            {"cf", F.cf, nc},
       {"Ml", F.Ml, nc},            {"Mg", F.Mg, nc},            {"kappa", F.kappa, nc},
       {"mx", F.m[0], nc},          {"my", F.m[1], nc},          {"mz", F.m[2], nc},

@@ -75,7 +75,7 @@ struct Fld {
   double* p;
   double* u[3];
   // properties
-  double *Ml, *Mg, *fw, *pc, *cf, *rho, *rho_old, *mu, *drag, *m[3], *kappa;  // fw = M_l / M
+  double *Ml, *Mg, *fw, *pc, *cf, *rho, *mu, *drag, *m[3], *kappa;  // fw = M_l / M
   // saturation step
   double *FLO[3], *AF[3], *aL, *Rp, *Rm;
   // momentum

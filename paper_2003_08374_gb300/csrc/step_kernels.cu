@@ -279,7 +279,6 @@ __global__ void k_finalize_inflow(const StepDom* __restrict__ D, Work w, int slo
 // ------------------------------------------------------------------ closures
 // Appendix A closures, Eqs. 42 and 45 densities / drag, Eq. 38 coefficient.
 __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long long c) {
-  F.rho_old[c] = F.rho[c];  // the density of the previous step feeds the Euler source (Eq. 46)
   const double a = F.alpha[c];
   F.mu[c] = a * P.mu_l + (1.0 - a) * P.mu_g;
   if (F.is_free[c]) {
@@ -373,7 +372,10 @@ __device__ __forceinline__ void b_curvature(const Prm& P, const Fld& F, long lon
 // Staggered momentum equation of a face (Eqs. 46-48): diagonal a_P, neighbour
 // coefficients (implicit upwind convection of rho u u / phi^2 and viscous
 // diffusion), and rhs0 = Euler source + explicit transpose viscous stress +
-// body force (gravity rho g and capillary force F_c, Eqs. 38, 43, 45).
+// body force (gravity rho g and capillary force F_c, Eqs. 38, 43, 45).  The
+// Euler term is taken in advective form, rho^{k+1} (v^{k+1} - v^k) / dt, like
+// the convection: the conservative form would need momentum fluxes consistent
+// with the saturation fluxes.
 __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, long long t, double dt) {
   int d, i, j, k;
   long long f;
@@ -393,7 +395,6 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   const double h = P.h, A = P.A, V = P.V;
   const double phif = 0.5 * (ghost_read(F.phi, P.n, li, lj, lk) + ghost_read(F.phi, P.n, i, j, k));
   const double rhof = 0.5 * (ghost_read(F.rho, P.n, li, lj, lk) + ghost_read(F.rho, P.n, i, j, k));
-  const double rhoo = 0.5 * (ghost_read(F.rho_old, P.n, li, lj, lk) + ghost_read(F.rho_old, P.n, i, j, k));
   const double Df = 0.5 * (ghost_read(F.drag, P.n, li, lj, lk) + ghost_read(F.drag, P.n, i, j, k));
   const double muL = ghost_read(F.mu, P.n, li, lj, lk), muR = ghost_read(F.mu, P.n, i, j, k);
   double Bf = rhof * P.g[d];
@@ -414,7 +415,7 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   const double inv_phi = 1.0 / phif;
   const double inv_h = P.inv_h;
   const double at = V * rhof * inv_phidt;
-  const double S = V * rhoo * uf * inv_phidt;
+  const double S = at * uf;  // advective form rho^{k+1} (v^{k+1} - v^k) / dt
   const double cconv = V * rhof * inv_phi * inv_phi * inv_h;
   double ap = at + V * Df;
   double tt = 0.0;

@@ -62,7 +62,7 @@ def test_stage_arrays_after_one_step():
     from paper_2003_08374_gb300 import workloads as W
     case = W.fracture_2d(nx=24, ny=16, p_tol=1e-15, max_cg=500)
     g, o = run_both(case, 1)
-    for name in ["FLOx", "FLOy", "AFx", "AFy", "aL", "Rp", "Rm", "rho", "rho_old", "mu", "drag", "pc", "cf",
+    for name in ["FLOx", "FLOy", "AFx", "AFy", "aL", "Rp", "Rm", "rho", "mu", "drag", "pc", "cf",
                  "Ml", "Mg", "mx", "my", "kappa", "aPx", "aPy", "rhs0x", "rhs0y", "Bx", "By", "Tx", "Ty",
                  "Dd", "b", "hbyax", "hbyay", "nwx", "nwy"]:
         a, b = g.array(name), o.array(name)
