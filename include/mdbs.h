@@ -60,6 +60,15 @@ extern "C" {
 #define MDBS_BROOKS_COREY 0
 #define MDBS_VAN_GENUCHTEN 1
 
+/* Density of porous cells in the momentum equation.  MDBS_RHO_MOBILITY: the
+ * mobility-weighted rho* = (rho_l M_l + rho_g M_g) / M of Eq. 45 (main
+ * text).  MDBS_RHO_SATURATION: the saturation-weighted rho of Appendix B, with
+ * the porous capillary force extended by M^-1 (M_l a_g - M_g a_l)(rho_l - rho_g) g
+ * so that the Darcy momentum balance is unchanged (Appendix B shows the two are
+ * equivalent). */
+#define MDBS_RHO_MOBILITY 0
+#define MDBS_RHO_SATURATION 1
+
 #define MDBS_FP64 0        /* FP64 everywhere */
 #define MDBS_MIXED 1       /* FP32 multigrid preconditioner inside FP64 flexible CG */
 #define MDBS_MIXED_BF16 2  /* as MDBS_MIXED with coarse-level coefficients stored in BF16 */
@@ -84,6 +93,7 @@ typedef struct {
   double pc0, pc_beta, pc_m;   /* entry pressure [Pa], Brooks-Corey beta, Van Genuchten m */
   double a_pc_irr, a_pc_max;   /* bounds of the p_c effective saturation */
   double pc_eps;               /* the p_c effective saturation is clamped to [eps, 1-eps] */
+  int32_t porous_density;      /* MDBS_RHO_MOBILITY (default) or MDBS_RHO_SATURATION */
 } mdbs_closures;
 
 typedef struct {

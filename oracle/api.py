@@ -22,7 +22,7 @@ class OrcParams(C.Structure):
         ("kr_m", C.c_double), ("a_l_irr", C.c_double), ("a_g_irr", C.c_double),
         ("pc0", C.c_double), ("pc_beta", C.c_double), ("pc_m", C.c_double),
         ("a_pc_irr", C.c_double), ("a_pc_max", C.c_double), ("pc_eps", C.c_double),
-        ("theta_deg", C.c_double),
+        ("porous_density", C.c_int), ("theta_deg", C.c_double),
         ("dt", C.c_double), ("cfl", C.c_double), ("dt_max", C.c_double),
         ("c_alpha", C.c_double), ("p_tol", C.c_double),
         ("n_corr", C.c_int), ("mom_sweeps", C.c_int), ("max_cg", C.c_int),

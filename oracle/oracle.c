@@ -186,7 +186,8 @@ static void update_props(orc_state* s) {
       s->Ml[c] = o[2];
       s->Mg[c] = o[3];
       s->drag[c] = o[4];
-      s->rho[c] = o[5];
+      /* rho* of Eq. 45, or Appendix B's saturation-weighted density */
+      s->rho[c] = P->porous_density ? a * P->rho_l + (1.0 - a) * P->rho_g : o[5];
       s->pc[c] = o[6];
       s->cf[c] = o[7];
     }
@@ -476,6 +477,10 @@ static void momentum_assemble(orc_state* s, double dt) {
               F = (0.5 * (s->cf[l] + s->cf[r]) * (s->pc[r] - s->pc[l]) -
                    0.5 * (s->pc[l] + s->pc[r]) * (s->alpha[r] - s->alpha[l])) /
                   h;
+              /* Appendix B: with the saturation-weighted density, F_c also
+               * carries M^-1 (M_l a_g - M_g a_l)(rho_l - rho_g) g */
+              if (P->porous_density)
+                F += 0.5 * (s->cf[l] + s->cf[r]) * (P->rho_l - P->rho_g) * P->g[d];
             }
           }
           s->B[d][f] = G + F;

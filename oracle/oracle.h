@@ -36,6 +36,7 @@ typedef struct {
   int kr_model, pc_model;
   double kr_m, a_l_irr, a_g_irr;
   double pc0, pc_beta, pc_m, a_pc_irr, a_pc_max, pc_eps;
+  int porous_density; /* 0: rho* of Eq. 45 in porous cells; 1: Appendix B */
   double theta_deg; /* contact angle at the free/porous interface, Eq. 40 */
   /* time stepping and solver */
   double dt, cfl, dt_max, c_alpha, p_tol;

@@ -608,7 +608,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   if (op->n_corr < 1 || op->n_corr > 8 || op->mom_sweeps < 0 || op->max_cg < 1 || op->mg_nu1 < 0 ||
       op->mg_nu2 < 0 || op->mg_coarse_sweeps < 0 || op->precision < 0 || op->precision > 2 || !(op->dt > 0.0))
     return fail(s, MDBS_ERR_ARG, "invalid options");
-  if (cl->kr_model < 0 || cl->kr_model > 1 || cl->pc_model < 0 || cl->pc_model > 1)
+  if (cl->kr_model < 0 || cl->kr_model > 1 || cl->pc_model < 0 || cl->pc_model > 1 ||
+      cl->porous_density < 0 || cl->porous_density > 1)
     return fail(s, MDBS_ERR_ARG, "invalid closure model");
 
   s = new (std::nothrow) mdbs_sim();
@@ -649,6 +650,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.a_pc_irr = cl->a_pc_irr;
   P.a_pc_max = cl->a_pc_max;
   P.pc_eps = cl->pc_eps;
+  P.porous_density = cl->porous_density;
   const double th = contact_angle_deg * M_PI / 180.0;
   P.cos_t = cos(th);
   P.sin_t = sin(th);

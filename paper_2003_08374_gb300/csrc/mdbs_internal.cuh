@@ -54,6 +54,7 @@ struct Prm {
   double rho_l, mu_l, rho_g, mu_g, sigma, g[3];
   int kr_model, pc_model;
   double kr_m, a_l_irr, a_g_irr, pc0, pc_beta, pc_m, a_pc_irr, a_pc_max, pc_eps;
+  int porous_density;   // 0: mobility-weighted rho* (Eq. 45), 1: Appendix B
   double cos_t, sin_t;  // contact angle
   double c_alpha;
   double inv_h, half_inv_h;  // 1/h and 1/(2h)

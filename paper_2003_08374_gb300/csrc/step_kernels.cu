@@ -327,7 +327,9 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
   F.fw[c] = Ml / M;  // M > 0 in porous cells: k0 > 0 and k_rl + k_rg > 0
   const double inv_M = 1.0 / M;
   F.drag[c] = inv_M;
-  F.rho[c] = (P.rho_l * Ml + P.rho_g * Mg) * inv_M;
+  // rho* of Eq. 45, or Appendix B's saturation-weighted rho (its buoyancy remainder
+  // c_f (rho_l - rho_g) g joins the porous capillary force)
+  F.rho[c] = P.porous_density ? a * P.rho_l + (1.0 - a) * P.rho_g : (P.rho_l * Ml + P.rho_g * Mg) * inv_M;
   F.pc[c] = pc;
   F.cf[c] = (Ml * (1.0 - a) - Mg * a) * inv_M;
 }
@@ -404,9 +406,9 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
     if (fl && fr) {
       Bf += P.sigma * 0.5 * (F.kappa[l] + F.kappa[r]) * (F.alpha[r] - F.alpha[l]) * P.inv_h;
     } else if (!fl && !fr) {
-      Bf += (0.5 * (F.cf[l] + F.cf[r]) * (F.pc[r] - F.pc[l]) -
-             0.5 * (F.pc[l] + F.pc[r]) * (F.alpha[r] - F.alpha[l])) *
-            P.inv_h;
+      const double cff = 0.5 * (F.cf[l] + F.cf[r]);
+      Bf += (cff * (F.pc[r] - F.pc[l]) - 0.5 * (F.pc[l] + F.pc[r]) * (F.alpha[r] - F.alpha[l])) * P.inv_h;
+      if (P.porous_density) Bf += cff * (P.rho_l - P.rho_g) * P.g[d];  // Appendix B's F_c
     }
   }
   F.B[d][f] = Bf;

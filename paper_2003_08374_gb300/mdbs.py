@@ -29,7 +29,7 @@ class Closures(C.Structure):
     _fields_ = [("kr_model", C.c_int32), ("pc_model", C.c_int32), ("kr_m", C.c_double),
                 ("a_l_irr", C.c_double), ("a_g_irr", C.c_double), ("pc0", C.c_double),
                 ("pc_beta", C.c_double), ("pc_m", C.c_double), ("a_pc_irr", C.c_double),
-                ("a_pc_max", C.c_double), ("pc_eps", C.c_double)]
+                ("a_pc_max", C.c_double), ("pc_eps", C.c_double), ("porous_density", C.c_int32)]
 
 
 class Options(C.Structure):
@@ -128,7 +128,7 @@ def structs_from_case(case):
     grid = Grid(case.nx, case.ny, case.nz, case.h)
     fl = Fluids(case.rho_l, case.mu_l, case.rho_g, case.mu_g, case.sigma, (C.c_double * 3)(*case.g))
     cl = Closures(case.kr_model, case.pc_model, case.kr_m, case.a_l_irr, case.a_g_irr, case.pc0, case.pc_beta,
-                  case.pc_m, case.a_pc_irr, case.a_pc_max, case.pc_eps)
+                  case.pc_m, case.a_pc_irr, case.a_pc_max, case.pc_eps, case.porous_density)
     op = Options(case.dt, case.cfl, case.dt_max, case.c_alpha, case.p_tol, case.n_corr, case.mom_sweeps,
                  case.max_cg, case.mg_nu1, case.mg_nu2, case.mg_coarse_sweeps, case.precision,
                  (C.c_int32 * 6)(*case.bc), case.inlet_u, case.inlet_alpha)

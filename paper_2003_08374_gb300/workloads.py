@@ -33,6 +33,7 @@ import numpy as np
 
 WALL, INLET, OUTLET = 0, 1, 2
 BROOKS_COREY, VAN_GENUCHTEN = 0, 1
+RHO_MOBILITY, RHO_SATURATION = 0, 1  # porous-cell density: Eq. 45 rho*, or Appendix B
 FP64, MIXED, MIXED_BF16 = 0, 1, 2
 
 
@@ -62,6 +63,7 @@ class Case:
     a_pc_irr: float = 0.0
     a_pc_max: float = 1.0
     pc_eps: float = 1e-3
+    porous_density: int = RHO_MOBILITY
     theta_deg: float = 45.0
     # time stepping / solver options
     dt: float = 1e-6

@@ -101,6 +101,21 @@ def test_wave_tank_small_cfl():
     assert g.stats()["dt"] == pytest.approx(o.stats()["dt"], rel=1e-9)
 
 
+def test_appendix_b_density_matches_oracle():
+    """Appendix B's saturation-weighted porous density with the extended capillary force,
+    on the ragged fractured block (porous, free and mixed faces, gravity) and on the
+    wave tank's porous barrier."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(21, 18, 11), seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500,
+                    porous_density=W.RHO_SATURATION)
+    g, o = run_both(case, 10)
+    check_fields(g, o, TOL64)
+    case = W.wave_tank(nx=32, ny=6, nz=20, h=5e-3, depth=10, x0=8, barrier=(20, 26, 8), p_tol=1e-15,
+                       max_cg=500, precision=W.FP64, porous_density=W.RHO_SATURATION)
+    g, o = run_both(case, 20)
+    check_fields(g, o, TOL64)
+
+
 def test_darcy_domain_and_2d_shapes():
     from paper_2003_08374_gb300 import workloads as W
     for shape in [(17, 23, 1), (9, 7, 6)]:
