@@ -188,6 +188,15 @@ void mdbs_destroy(mdbs_sim* sim);
  */
 typedef struct mdbs_batch mdbs_batch;
 int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out);
+/* Membership changes between batch steps (continuous batching): add a simulation
+ * that meets mdbs_batch_create's conditions, or remove a member (which becomes a
+ * simulation of its own again, fields and statistics intact).  The batch's launch
+ * plan and CUDA graph are rebuilt; members' results are unaffected.  A batch keeps
+ * at least one member: removing the last one is MDBS_ERR_ARG, as are NULL
+ * arguments, a simulation already in a batch (add) or not in this one (remove).
+ * On a CUDA error the batch keeps its previous members. */
+int mdbs_batch_add(mdbs_batch* batch, mdbs_sim* sim);
+int mdbs_batch_remove(mdbs_batch* batch, mdbs_sim* sim);
 /* Advances every member n >= 1 steps; MDBS_ERR_DIVERGED names the first diverged member. */
 int mdbs_batch_step(mdbs_batch* batch, int32_t n);
 /* Runs the batch's kernels on the given cudaStream_t (NULL: legacy default stream). */
@@ -264,6 +273,22 @@ const char* mdbs_last_error(const mdbs_sim* sim);
 /* Runs the simulation's kernels on the given cudaStream_t (NULL: legacy default
  * stream).  The caller keeps ownership of the stream. */
 int mdbs_set_stream(mdbs_sim* sim, void* cuda_stream);
+
+/*
+ * Device-memory hook (no counterpart in the paper; lets a host framework such as
+ * PyTorch's caching allocator own the memory): when set, the two bulk device
+ * allocations of every later mdbs_create -- the simulation's field arena and its
+ * pressure-solver block, together mdbs_bytes_required bytes -- come from
+ * alloc(bytes, ctx) and go back through free(ptr, ctx) at mdbs_destroy, with the
+ * hook that allocated them.  alloc must return device memory aligned to 256 bytes
+ * (else mdbs_create fails with MDBS_ERR_ARG) or NULL (MDBS_ERR_OOM).  Both NULL
+ * restores cudaMalloc / cudaFree; exactly one NULL is MDBS_ERR_ARG.  Small
+ * bookkeeping buffers still use the CUDA runtime.  Process-wide; not thread-safe
+ * against concurrent mdbs_create.
+ */
+typedef void* (*mdbs_alloc_fn)(size_t bytes, void* ctx);
+typedef void (*mdbs_free_fn)(void* ptr, void* ctx);
+int mdbs_set_allocator(mdbs_alloc_fn alloc, mdbs_free_fn free_fn, void* ctx);
 
 /* Device bytes mdbs_create allocates for this grid and precision. */
 size_t mdbs_bytes_required(const mdbs_grid* grid, int32_t precision);

@@ -118,6 +118,7 @@ struct mdbs_sim {
   int precision;
   cudaStream_t stream;
   void* arena;
+  DevBlock arena_mem;  // owner record of the arena (allocator hook)
   size_t arena_bytes;
   PressureSolver* ps;
   double* partials;   // 4 channels of pcap
@@ -145,6 +146,47 @@ struct mdbs_batch {
 };
 
 static thread_local std::string g_create_error;
+
+// ---------------------------------------------------------------- device memory hook
+static mdbs_alloc_fn g_alloc = nullptr;
+static mdbs_free_fn g_free = nullptr;
+static void* g_alloc_ctx = nullptr;
+
+namespace mdbs {
+cudaError_t dev_block_alloc(DevBlock* b, size_t bytes) {
+  *b = DevBlock{};
+  if (g_alloc) {
+    void* p = g_alloc(bytes, g_alloc_ctx);
+    if (!p) return cudaErrorMemoryAllocation;
+    if ((uintptr_t)p & 255) {  // the arena layout and the TMA descriptors need 256-byte alignment
+      g_free(p, g_alloc_ctx);
+      return cudaErrorInvalidValue;
+    }
+    b->ptr = p;
+    b->free_fn = g_free;
+    b->ctx = g_alloc_ctx;
+    return cudaSuccess;
+  }
+  return cudaMalloc(&b->ptr, bytes);
+}
+
+void dev_block_free(DevBlock* b) {
+  if (!b->ptr) return;
+  if (b->free_fn)
+    b->free_fn(b->ptr, b->ctx);
+  else
+    cudaFree(b->ptr);
+  *b = DevBlock{};
+}
+}  // namespace mdbs
+
+extern "C" int mdbs_set_allocator(mdbs_alloc_fn alloc, mdbs_free_fn free_fn, void* ctx) {
+  if ((alloc == nullptr) != (free_fn == nullptr)) return MDBS_ERR_ARG;
+  g_alloc = alloc;
+  g_free = free_fn;
+  g_alloc_ctx = alloc ? ctx : nullptr;
+  return MDBS_OK;
+}
 
 namespace {
 
@@ -665,14 +707,19 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   s->stream = nullptr;
 
   s->arena_bytes = carve(nullptr, L, nullptr);
-  cudaError_t e = cudaMalloc(&s->arena, s->arena_bytes);
+  cudaError_t e = dev_block_alloc(&s->arena_mem, s->arena_bytes);
   if (e != cudaSuccess) {
-    int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
-    fail(nullptr, code, std::string("device arena: ") + cudaGetErrorString(e));
+    int code = e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM
+               : e == cudaErrorInvalidValue  ? MDBS_ERR_ARG
+                                              : MDBS_ERR_CUDA;
+    fail(nullptr, code, std::string("device arena: ") +
+                            (e == cudaErrorInvalidValue ? "the allocator hook returned memory not aligned to 256 bytes"
+                                                        : cudaGetErrorString(e)));
     cudaGetLastError();
     delete s;
     return code;
   }
+  s->arena = s->arena_mem.ptr;
   cudaMemset(s->arena, 0, s->arena_bytes);
   carve(s, L, (char*)s->arena);
   e = cudaMallocHost(&s->host_scal, kNumSlots * sizeof(double));
@@ -682,7 +729,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
     fail(nullptr, code, std::string("pressure solver: ") + cudaGetErrorString(e));
     cudaGetLastError();
     if (s->host_scal) cudaFreeHost(s->host_scal);
-    cudaFree(s->arena);
+    dev_block_free(&s->arena_mem);
     delete s;
     return code;
   }
@@ -777,7 +824,7 @@ void mdbs_destroy(mdbs_sim* s) {
   exec_destroy(s->ex);
   pressure_destroy(s->ps);
   if (s->host_scal) cudaFreeHost(s->host_scal);
-  cudaFree(s->arena);
+  dev_block_free(&s->arena_mem);
   delete s;
 }
 
@@ -992,6 +1039,74 @@ int mdbs_batch_step(mdbs_batch* b, int32_t n) {
 }
 
 const char* mdbs_batch_last_error(const mdbs_batch* b) { return b ? b->err.c_str() : g_create_error.c_str(); }
+
+int mdbs_batch_add(mdbs_batch* b, mdbs_sim* s) {
+  if (!b) return fail(nullptr, MDBS_ERR_ARG, "batch is NULL");
+  auto bad = [&](const char* m) {
+    b->err = m;
+    return MDBS_ERR_ARG;
+  };
+  if (!s) return bad("NULL simulation");
+  if (s->in_batch) return bad("the simulation already belongs to a batch");
+  if (!s->fields_set) return bad("mdbs_set_fields has not been called");
+  if (!same_solver_options(s->opt, b->sims[0]->opt))
+    return bad("batched simulations need the same solver options and precision class");
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  cudaDeviceSynchronize();
+  const size_t n = b->sims.size() + 1;
+  double *g = nullptr, *hg = nullptr;
+  cudaError_t e = cudaMalloc(&g, n * kNumSlots * sizeof(double));
+  if (e == cudaSuccess) e = cudaMallocHost(&hg, n * kNumSlots * sizeof(double));
+  if (e == cudaSuccess) {
+    b->sims.push_back(s);
+    e = batch_exec_setup(b);
+    if (e != cudaSuccess) {  // back to the previous members
+      b->sims.pop_back();
+      cudaGetLastError();
+      batch_exec_setup(b);
+    }
+  }
+  if (e != cudaSuccess) {
+    if (g) cudaFree(g);
+    if (hg) cudaFreeHost(hg);
+    b->err = std::string("batch add: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? MDBS_ERR_OOM : MDBS_ERR_CUDA;
+  }
+  cudaFree(b->gather);
+  cudaFreeHost(b->host_gather);
+  b->gather = g;
+  b->host_gather = hg;
+  s->in_batch = true;
+  return MDBS_OK;
+}
+
+int mdbs_batch_remove(mdbs_batch* b, mdbs_sim* s) {
+  if (!b) return fail(nullptr, MDBS_ERR_ARG, "batch is NULL");
+  size_t at = 0;
+  while (at < b->sims.size() && b->sims[at] != s) at++;
+  if (!s || at == b->sims.size()) {
+    b->err = "the simulation is not a member of this batch";
+    return MDBS_ERR_ARG;
+  }
+  if (b->sims.size() == 1) {
+    b->err = "a batch keeps at least one member";
+    return MDBS_ERR_ARG;
+  }
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  cudaDeviceSynchronize();
+  b->sims.erase(b->sims.begin() + at);
+  cudaError_t e = batch_exec_setup(b);
+  if (e != cudaSuccess) {  // back to the previous members
+    b->sims.insert(b->sims.begin() + at, s);
+    cudaGetLastError();
+    batch_exec_setup(b);
+    b->err = std::string("batch remove: ") + cudaGetErrorString(e);
+    return MDBS_ERR_CUDA;
+  }
+  s->in_batch = false;
+  return MDBS_OK;
+}
 
 void mdbs_batch_destroy(mdbs_batch* b) {
   if (!b) return;

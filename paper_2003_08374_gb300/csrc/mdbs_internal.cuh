@@ -305,6 +305,16 @@ void launch_field_stats(const BatchPlan& B, cudaStream_t s);
 void launch_time_advance(const BatchPlan& B, cudaStream_t s);
 void launch_static_geometry(const BatchPlan& B, cudaStream_t s);
 
+// capi.cu: bulk device allocations through the mdbs_set_allocator hook (or the
+// CUDA runtime); a DevBlock remembers the hook that allocated it
+struct DevBlock {
+  void* ptr = nullptr;
+  void (*free_fn)(void*, void*) = nullptr;  // nullptr: cudaFree
+  void* ctx = nullptr;
+};
+cudaError_t dev_block_alloc(DevBlock* b, size_t bytes);
+void dev_block_free(DevBlock* b);
+
 // pressure.cu
 struct PressureSolver;
 PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err);

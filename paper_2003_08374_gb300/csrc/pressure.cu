@@ -1299,6 +1299,7 @@ struct PressureSolver {
   CUtensorMap* tmaps;   // device: TMA descriptors of the FP32 levels (mixed precisions)
   unsigned tma_levels;  // levels that have them
   void* block;     // single device allocation
+  DevBlock mem;    // its owner record (allocator hook)
   size_t bytes;
 };
 
@@ -1473,11 +1474,12 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
   }
   size_t bytes = solver_layout(P.n, ps->precision, nullptr, nullptr);
   ps->bytes = bytes;
-  *err = cudaMalloc(&ps->block, bytes);
+  *err = dev_block_alloc(&ps->mem, bytes);
   if (*err != cudaSuccess) {
     delete ps;
     return nullptr;
   }
+  ps->block = ps->mem.ptr;
   *err = cudaMemset(ps->block, 0, bytes);
   solver_layout(P.n, ps->precision, ps, (char*)ps->block);
   if (*err == cudaSuccess && ps->tmaps) *err = encode_level_maps(ps);
@@ -1486,7 +1488,7 @@ PressureSolver* pressure_create(const Prm& P, int precision, cudaError_t* err) {
 
 void pressure_destroy(PressureSolver* ps) {
   if (!ps) return;
-  cudaFree(ps->block);
+  dev_block_free(&ps->mem);
   delete ps;
 }
 

@@ -49,6 +49,9 @@ class Stats(C.Structure):
 
 _D = C.POINTER(C.c_double)
 _lib = None
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+_hook = None  # keeps the ctypes callbacks of the installed allocator alive
 
 
 class Tuning(C.Structure):
@@ -102,6 +105,9 @@ def lib():
         L.mdbs_batch_last_error.argtypes = [C.c_void_p]
         L.mdbs_batch_last_error.restype = C.c_char_p
         L.mdbs_batch_destroy.argtypes = [C.c_void_p]
+        L.mdbs_batch_add.argtypes = [C.c_void_p, C.c_void_p]
+        L.mdbs_batch_remove.argtypes = [C.c_void_p, C.c_void_p]
+        L.mdbs_set_allocator.argtypes = [ALLOC_FN, FREE_FN, C.c_void_p]
         L.mdbs_field_stats_static.argtypes = [C.c_int64, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p,
                                               C.c_void_p, C.c_void_p]
         L.mdbs_debug_array.argtypes = [C.c_void_p, C.c_char_p, _D, C.c_int64]
@@ -298,6 +304,20 @@ class Batch:
         if rc != OK:
             raise MdbsError(rc, lib().mdbs_batch_last_error(self.h).decode())
 
+    def add(self, sim):
+        """mdbs_batch_add: sim joins the batch before the next step."""
+        rc = lib().mdbs_batch_add(self.h, sim.h)
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_batch_last_error(self.h).decode())
+        self.sims.append(sim)
+
+    def remove(self, sim):
+        """mdbs_batch_remove: sim leaves the batch and can be stepped alone again."""
+        rc = lib().mdbs_batch_remove(self.h, sim.h)
+        if rc != OK:
+            raise MdbsError(rc, lib().mdbs_batch_last_error(self.h).decode())
+        self.sims.remove(sim)
+
     def set_stream(self, stream_handle: int):
         lib().mdbs_batch_set_stream(self.h, C.c_void_p(stream_handle))
 
@@ -326,3 +346,27 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def set_allocator(alloc=None, free=None):
+    """mdbs_set_allocator: alloc(nbytes) -> device address (int, 256-byte aligned, 0 on
+    failure) and free(address) serve the arenas of later Simulations; no arguments
+    restores cudaMalloc.  The callables are kept alive here until replaced."""
+    global _hook
+    if alloc is None and free is None:
+        rc = lib().mdbs_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        _hook = None
+    else:
+        a = ALLOC_FN(lambda n, ctx: alloc(int(n)) or None)
+        f = FREE_FN(lambda p, ctx: free(int(p)))
+        rc = lib().mdbs_set_allocator(a, f, None)
+        if rc == OK:
+            _hook = (a, f)
+    if rc != OK:
+        raise MdbsError(rc, "mdbs_set_allocator")
+
+
+def use_torch_allocator():
+    """Serve the arenas from PyTorch's caching allocator on the current device."""
+    import torch
+    set_allocator(lambda n: torch.cuda.caching_allocator_alloc(n), torch.cuda.caching_allocator_delete)

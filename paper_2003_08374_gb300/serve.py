@@ -6,7 +6,8 @@ library's own device-byte estimate against cudaMemGetInfo, minus a reserve)
 and the slot limit, keeps the admitted requests' fields resident on the device,
 and advances all of them together as one batch (mdbs_batch: one kernel launch
 per step phase, one CUDA graph per step), so that newly admitted work overlaps
-with the work already on the GPU.  A round is never longer than the smallest
+with the work already on the GPU.  Requests join and leave the batch between
+rounds (mdbs_batch_add / mdbs_batch_remove).  A round is never longer than the smallest
 remaining step count, so every request runs exactly its own number of steps;
 finished requests are read back and release their memory at once.  Because a
 member's arithmetic does not depend on the other members, a request's result
@@ -65,7 +66,6 @@ class Server:
         i = 0
         while i < len(pending) or active:
             now = clock() - t0
-            changed = False
             # admission: arrived requests in order while slots and memory allow
             budget = self._free_bytes() - self.reserve
             while i < len(pending) and pending[i].arrival <= now and len(active) < self.max_active:
@@ -77,24 +77,21 @@ class Server:
                     req.rejected = True  # does not fit even on an idle device
                     i += 1
                     continue
-                if batch is not None:
-                    batch.close()
-                    batch = None
                 sim = mdbs.Simulation(req.case)
                 if self.stream_handle is not None:
                     sim.set_stream(self.stream_handle)
+                if batch is not None:
+                    batch.add(sim)  # joins before the next round (mdbs_batch_add)
+                    self.rebuilds += 1
                 req.admitted = clock() - t0
                 active.append([req, sim, req.steps])
                 budget -= need
                 i += 1
-                changed = True
             if not active:
                 if i < len(pending):
                     time.sleep(max(0.0, min(pending[i].arrival - (clock() - t0), 0.05)))
                 continue
-            if changed or batch is None:
-                if batch is not None:
-                    batch.close()
+            if batch is None:
                 batch = mdbs.Batch([a[1] for a in active])
                 if self.stream_handle is not None:
                     batch.set_stream(self.stream_handle)
@@ -124,8 +121,13 @@ class Server:
                 if a[2] == 0:
                     done.append(a)
             if done:
-                batch.close()
-                batch = None
+                for a in done:
+                    if len(batch.sims) > 1:
+                        batch.remove(a[1])  # leaves before the next round (mdbs_batch_remove)
+                        self.rebuilds += 1
+                    else:
+                        batch.close()
+                        batch = None
                 for a in done:
                     req, sim = a[0], a[1]
                     if req.error is None:

@@ -72,3 +72,15 @@ def test_bytes_required_is_host_only_and_monotone(built):
     f64, f32, bf = (mdbs.bytes_required(g, precision=p) for p in (0, 1, 2))
     coarse = sum((64 >> l) ** 3 for l in range(1, 5))  # levels 32^3 .. 4^3
     assert f64 < f32 and f32 - bf >= 0.99 * 3 * 2 * coarse  # (less 256-byte alignment of the small levels)
+
+
+def test_allocator_hook_and_batch_membership_argument_errors(built):
+    """Host-only checks (no device call): exactly one NULL allocator function, and NULL
+    batch or simulation handles, are argument errors; both NULL restores cudaMalloc."""
+    from paper_2003_08374_gb300 import mdbs
+    L = mdbs.lib()
+    assert L.mdbs_set_allocator(mdbs.ALLOC_FN(lambda n, c: None), mdbs.FREE_FN(), None) == mdbs.ERR_ARG
+    assert L.mdbs_set_allocator(mdbs.ALLOC_FN(), mdbs.FREE_FN(lambda p, c: None), None) == mdbs.ERR_ARG
+    assert L.mdbs_set_allocator(mdbs.ALLOC_FN(), mdbs.FREE_FN(), None) == mdbs.OK
+    assert L.mdbs_batch_add(None, None) == mdbs.ERR_ARG
+    assert L.mdbs_batch_remove(None, None) == mdbs.ERR_ARG

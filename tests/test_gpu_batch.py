@@ -61,3 +61,71 @@ def test_batch_rejects_mixed_solver_options_and_double_membership():
         a.step(1)
     b.close()
     a.step(1)
+
+
+def test_members_join_and_leave_between_steps():
+    """mdbs_batch_add / mdbs_batch_remove (continuous batching): a member's results do not
+    depend on when others join or leave, and a removed member steps alone again."""
+    from paper_2003_08374_gb300 import mdbs
+    cases = _cases(0)[:4]
+    ref = []
+    for c in cases:
+        s = mdbs.Simulation(c)
+        s.step(6)
+        ref.append(s.fields())
+        s.close()
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims[:2])
+    b.step(2)                      # members 0, 1 at 2 steps
+    sims[2].step(2)                # member 2 alone to 2 steps, then joins
+    b.add(sims[2])
+    b.step(2)                      # 0, 1, 2 at 4 steps
+    b.remove(sims[0])
+    sims[0].step(2)                # 0 alone to 6
+    b.add(sims[3])                 # 3 joins at 0 steps
+    b.step(2)                      # 1, 2 at 6; 3 at 2
+    b.remove(sims[3])
+    sims[3].step(4)                # 3 alone to 6
+    for s, fa in zip(sims, ref):
+        assert s.stats()["steps"] == 6
+        fb = s.fields()
+        for k in fa:
+            assert np.array_equal(fa[k], fb[k]), k
+    with pytest.raises(mdbs.MdbsError):
+        b.add(sims[1])             # already a member
+    with pytest.raises(mdbs.MdbsError):
+        b.remove(sims[0])          # not a member
+    b.remove(sims[1])
+    with pytest.raises(mdbs.MdbsError):
+        b.remove(sims[2])          # the last member stays
+    b.close()
+
+
+def test_allocator_hook_serves_the_arenas():
+    """mdbs_set_allocator with PyTorch's caching allocator: the arenas come from torch
+    (its allocated bytes grow by mdbs_bytes_required and fall back at destroy), and the
+    results equal those of cudaMalloc'ed arenas."""
+    torch = pytest.importorskip("torch")
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(20, 18, 16), seed=3, corr_len=3.0, frac_w=2, p_tol=1e-10, max_cg=300)
+    s = mdbs.Simulation(case)
+    s.step(3)
+    ref = s.fields()
+    s.close()
+    torch.cuda.synchronize()
+    base = torch.cuda.memory_allocated()
+    mdbs.use_torch_allocator()
+    try:
+        t = mdbs.Simulation(case)
+        held = torch.cuda.memory_allocated() - base
+        assert held >= mdbs.bytes_required(case)
+        t.step(3)
+        f = t.fields()
+        for k in ref:
+            assert np.array_equal(ref[k], f[k]), k
+        t.close()
+        torch.cuda.synchronize()
+        assert torch.cuda.memory_allocated() == base
+    finally:
+        mdbs.set_allocator()
