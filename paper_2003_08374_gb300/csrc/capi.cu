@@ -764,9 +764,14 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   Activate act(s);
   // round-off excursions of the flux-corrected update (|.| ~ 1e-30) must survive a
   // get_fields / set_fields round trip, so the check allows 1e-9 outside [0, 1]
-  for (long long c = 0; c < s->P.cells; c++)
-    if (!(alpha[c] >= -1e-9 && alpha[c] <= 1.0 + 1e-9))
-      return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-9)");
+  // branch-free inner loop (vectorised by the host compiler), one exit test per chunk;
+  // NaN fails both comparisons
+  for (long long c0 = 0; c0 < s->P.cells; c0 += 4096) {
+    const long long c1 = std::min(s->P.cells, c0 + 4096);
+    int ok = 1;
+    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= -1e-9) & (int)(alpha[c] <= 1.0 + 1e-9);
+    if (!ok) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-9)");
+  }
   const double* src[3] = {ux, uy, uz};
   CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
   CK(cudaMemcpyAsync(s->F.p, p, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));

@@ -18,6 +18,8 @@ identical arrays.  Recipes:
   into [0.1, 0.9] and uniform initial saturation (batched / served domains).
 * ``buckley_leverett`` -- the Darcy-scale 1-D column of sections 4.1.1-4.1.2
   (water injected into air or oil, optional gravity along the flow).
+* ``capillary_column`` -- the gravity-capillarity column of section 4.1.3
+  (step-wise initial saturation relaxing to capillary-gravity equilibrium).
 
 Every array is x-fastest: cell c = i + nx*(j + ny*k).  Face arrays hold
 (nx+1)*ny*nz x-faces, nx*(ny+1)*nz y-faces and nx*ny*(nz+1) z-faces; a 2-D
@@ -262,6 +264,36 @@ def buckley_leverett(nx=2000, length=4.0, displaced="air", kr_model=BROOKS_COREY
     c.alpha = np.zeros(nx)
     _zero_fields(c)
     _plug_flow(c, u)
+    return c
+
+
+def capillary_column(ny=1500, length=1.0, model=BROOKS_COREY, phi=0.5, k0=1e-11, dt=None, **kw) -> Case:
+    """Gravity-capillarity column of section 4.1.3 (1 m, 1500 cells, porosity 0.5,
+    k0 = 1e-11 m^2): water (1000, 1e-3) and air (1, 1.76e-5), lower half at
+    saturation 0.5, upper half dry, gravity -9.81 m/s^2 along y; closed bottom and
+    an open top (p = 0, zero-gradient velocity), so the column relaxes to the
+    capillary-gravity equilibrium dp_c/dy = (rho_g - rho_l) g_y.  Brooks-Corey
+    (kr m = 3, p_c0 = 100 Pa, beta = 0.5) or Van Genuchten (m = 0.5) closures
+    (Table 2).  Fixed time step, by default 300 s (40 / ny)^2, about half the
+    explicit capillary-diffusion limit h^2 / (2 D_max) (D = lambda |dp_c/dalpha| / phi
+    peaks at 4.8e-7 m^2/s near alpha = 0.69 for Brooks-Corey): 0.21 s at the paper's
+    1500 cells.  Above the limit the flux-corrected update stays bounded but the
+    profile oscillates."""
+    h = length / ny
+    if dt is None:
+        dt = 300.0 * (40.0 / ny) ** 2
+    c = Case(name="capillary_column_%s_%d" % ("bc" if model == BROOKS_COREY else "vg", ny), nx=1, ny=ny, nz=1,
+             h=h, rho_l=1000.0, mu_l=1e-3, rho_g=1.0, mu_g=1.76e-5, sigma=0.0, g=(0.0, -9.81, 0.0),
+             kr_model=model, pc_model=model, kr_m=3.0 if model == BROOKS_COREY else 0.5, pc0=100.0,
+             pc_beta=0.5, pc_m=0.5, bc=(WALL, WALL, WALL, OUTLET, WALL, WALL), inlet_u=0.0,
+             dt=dt, dt_max=dt, cfl=0.0, p_tol=1e-12, max_cg=500)
+    c = c.replace(**kw)
+    c.porosity = np.full(ny, float(phi))
+    c.permeability = np.full(ny, float(k0))
+    a = np.zeros(ny)
+    a[: ny // 2] = 0.5
+    c.alpha = a
+    _zero_fields(c)
     return c
 
 

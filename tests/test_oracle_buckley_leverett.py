@@ -131,3 +131,49 @@ def test_gravity_dominated_plateau_matches_printed_front(model, m, printed):
     assert abs(float(np.mean(plateau)) - printed) <= 1.5e-3
     xf = U * st["time"] / (PHI * root)
     assert abs((front + 0.5) * case.h - xf) <= 3 * case.h
+
+
+def _bc_equilibrium(ny, length, volume, p0=100.0, beta=0.5, drho_g=(1000.0 - 1.0) * 9.81):
+    """Semi-analytic steady state of section 4.1.3 (Brooks-Corey): p_c(alpha(y)) = C + drho g y
+    with p_c = p0 s^-beta (alpha = 1 where p_c <= p0), C fixed by the water volume."""
+    y = (np.arange(ny) + 0.5) * length / ny
+
+    def profile(C):
+        pc = C + drho_g * y
+        return np.where(pc <= p0, 1.0, (p0 / np.maximum(pc, p0)) ** (1.0 / beta))
+
+    lo, hi = -1e5, 1e5
+    for _ in range(200):
+        C = 0.5 * (lo + hi)
+        if profile(C).sum() * length / ny > volume:
+            lo = C
+        else:
+            hi = C
+    return profile(0.5 * (lo + hi))
+
+
+def test_capillary_column_relaxes_to_equilibrium():
+    """Section 4.1.3: from the step-wise start (lower half at 0.5, upper half dry) the column
+    relaxes toward dp_c/dy = (rho_g - rho_l) g_y -- the capillary and gravity parts of the
+    porous relative flux (Eq. 34) and the porous capillary force (Eq. 38) together.  The
+    L1 distance to the semi-analytic profile falls at every checkpoint and ends near 1 %
+    (the dry tail drains slowly: k_rl ~ alpha^3); the final profile falls monotonically
+    with height, as the equilibrium does; the water volume is conserved exactly (nothing
+    reaches the open top)."""
+    case = W.capillary_column(ny=40)  # dt 300 s, half the capillary-diffusion limit
+    vol = float(case.alpha.sum() * case.h)
+    s = OracleSim(case)
+    dist = []
+    for _ in range(6):
+        s.step(5000)
+        a = s.fields()["alpha"]
+        eq = _bc_equilibrium(case.ny, 1.0, vol)
+        dist.append(float(np.abs(a - eq).sum() / eq.sum()))
+    st = s.stats()
+    s.close()
+    assert all(b < a for a, b in zip(dist, dist[1:])), dist
+    assert dist[-1] < 0.011, dist
+    assert np.all(np.diff(a) <= 1e-4), a  # falls with height (up to a 1e-5-level wall transient)
+    # bounds up to the transport error the pressure tolerance allows over 20000 steps
+    assert st["alpha_min"] >= 0.0 and st["alpha_max"] <= 1.0 + 1e-8
+    assert abs(st["mass"] - 0.5 * vol * case.h ** 2) <= 1e-12 * st["mass"]
