@@ -209,7 +209,19 @@ static void grad_cell(const orc_state* s, const double* a, const int c[3], doubl
 
 /* interface normals (Eq. 24, oriented toward the liquid), contact-angle
  * correction at the free/porous interface (Eq. 40 / 44) and curvature
- * kappa = -div(m) used in the CSF force (Eq. 27 / 43). */
+ * kappa = -div(m) used in the CSF force (Eq. 27 / 43).  Solid-free cells take
+ * their gradients from the fluid side only (free_side). */
+/* value of a at the neighbour nb as a solid-free cell c sees it: a porous
+ * neighbour counts as a zero-gradient ghost (c's own value), like a wall, so
+ * that the normal and curvature next to the porous surface come from the fluid
+ * side before the contact angle replaces the normal (section 2.3, Eq. 40) */
+static double free_side(const orc_state* s, const double* a, const int c[3], const int nb[3]) {
+  int q[3];
+  for (int e = 0; e < 3; e++) q[e] = clampi(nb[e], 0, s->n[e] - 1);
+  long i = cidv(s, q);
+  if (s->is_free[cidv(s, c)] && !s->is_free[i]) return a[cidv(s, c)];
+  return a[i];
+}
 static void normals_curvature(orc_state* s) {
   double dn = 1e-8 / s->h;
   double th = s->P.theta_deg * M_PI / 180.0;
@@ -217,8 +229,15 @@ static void normals_curvature(orc_state* s) {
   for (long c = 0; c < s->cells; c++) {
     int q[3];
     coords_of(s->n, c, q);
-    double g[3];
-    grad_cell(s, s->alpha, q, g);
+    double g[3] = {0.0, 0.0, 0.0};
+    for (int e = 0; e < s->dim; e++) {
+      int lo[3], hi[3];
+      cpy3(lo, q);
+      cpy3(hi, q);
+      lo[e] -= 1;
+      hi[e] += 1;
+      g[e] = (free_side(s, s->alpha, q, hi) - free_side(s, s->alpha, q, lo)) / (2.0 * s->h);
+    }
     double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
     for (int e = 0; e < 3; e++) s->m[e][c] = g[e] / (mag + dn);
   }
@@ -235,7 +254,9 @@ static void normals_curvature(orc_state* s) {
     }
     tn = sqrt(tn);
     for (int e = 0; e < 3; e++) {
-      double te = tn > 0.0 ? t[e] / tn : 0.0;
+      /* the wall tangent is undefined when the interface lies parallel to the
+       * surface: a tangential part below 1e-9 |m| is rounding, not a direction */
+      double te = tn > 1e-9 * mm ? t[e] / tn : 0.0;
       s->m[e][c] = mm * (ct * nw[e] + st * te);
     }
   }
@@ -249,7 +270,7 @@ static void normals_curvature(orc_state* s) {
       cpy3(hi, q);
       lo[e] -= 1;
       hi[e] += 1;
-      k -= (cval(s, s->m[e], hi) - cval(s, s->m[e], lo)) / (2.0 * s->h);
+      k -= (free_side(s, s->m[e], q, hi) - free_side(s, s->m[e], q, lo)) / (2.0 * s->h);
     }
     s->kappa[c] = k;
   }

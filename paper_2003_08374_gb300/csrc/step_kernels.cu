@@ -336,11 +336,30 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
 
 // interface normal toward the liquid (Eq. 24 with the orientation of Eq. 41)
 // and the contact-angle normal of Eq. 40 in free cells next to porous cells
+// central difference along e as the solid-free cell c sees it: a porous neighbour
+// is a zero-gradient ghost (c's own value), like a wall, so that the normal and
+// curvature next to a porous surface come from the fluid side before the contact
+// angle replaces the normal; porous cells take plain central differences
+__device__ __forceinline__ double fluid_grad(const double* __restrict__ a, const Prm& P, const Fld& F, int e,
+                                            int i, int j, int k, long long c) {
+  const int di = (e == 0), dj = (e == 1), dk = (e == 2);
+  const long long hi = cell_index(P.n, clampi(i + di, 0, P.n[0] - 1), clampi(j + dj, 0, P.n[1] - 1),
+                                  clampi(k + dk, 0, P.n[2] - 1));
+  const long long lo = cell_index(P.n, clampi(i - di, 0, P.n[0] - 1), clampi(j - dj, 0, P.n[1] - 1),
+                                  clampi(k - dk, 0, P.n[2] - 1));
+  double ah = a[hi], al = a[lo];
+  if (F.is_free[c]) {
+    if (!F.is_free[hi]) ah = a[c];
+    if (!F.is_free[lo]) al = a[c];
+  }
+  return (ah - al) * P.half_inv_h;
+}
+
 __device__ __forceinline__ void b_normals(const Prm& P, const Fld& F, long long c) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double g[3] = {0.0, 0.0, 0.0};
-  for (int e = 0; e < P.dim; e++) g[e] = cgrad(F.alpha, P, e, i, j, k);
+  for (int e = 0; e < P.dim; e++) g[e] = fluid_grad(F.alpha, P, F, e, i, j, k, c);
   const double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
   const double den = mag + 1e-8 / P.h;
   double m[3] = {g[0] / den, g[1] / den, g[2] / den};
@@ -354,7 +373,10 @@ __device__ __forceinline__ void b_normals(const Prm& P, const Fld& F, long long 
       tn += t[e] * t[e];
     }
     tn = sqrt(tn);
-    for (int e = 0; e < 3; e++) m[e] = mm * (P.cos_t * nw[e] + P.sin_t * (tn > 0.0 ? t[e] / tn : 0.0));
+    // no wall tangent where the interface lies parallel to the surface (a tangential
+    // part below 1e-9 |m| is rounding, not a direction)
+    const bool has_t = tn > 1e-9 * mm;
+    for (int e = 0; e < 3; e++) m[e] = mm * (P.cos_t * nw[e] + P.sin_t * (has_t ? t[e] / tn : 0.0));
   }
   F.m[0][c] = m[0];
   F.m[1][c] = m[1];
@@ -366,7 +388,7 @@ __device__ __forceinline__ void b_curvature(const Prm& P, const Fld& F, long lon
   int i, j, k;
   decode_cell(P, c, i, j, k);
   double kap = 0.0;
-  for (int e = 0; e < P.dim; e++) kap -= cgrad(F.m[e], P, e, i, j, k);
+  for (int e = 0; e < P.dim; e++) kap -= fluid_grad(F.m[e], P, F, e, i, j, k, c);
   F.kappa[c] = kap;
 }
 

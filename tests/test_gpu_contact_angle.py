@@ -1,0 +1,75 @@
+"""Contact angle on a flat porous plate (section 4.2.1) on the CUDA path: parity
+with the oracle on the 60 x 30 cap, then caps at twice that resolution (120 x 60
+cells of 50 um) whose measured angle ends within 5 degrees of the imposed one."""
+import math
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    from paper_2003_08374_gb300.build import build_library
+    from oracle.build import build_oracle
+    build_library()
+    build_oracle()
+
+
+def cap_case(nx, ny, h, plate, theta_init, theta_wall, sub=8, **kw):
+    """Circular water cap (area 1 mm^2, angle theta_init) in air on a plate of
+    negligible permeability, contact angle theta_wall imposed."""
+    from paper_2003_08374_gb300 import workloads as W
+    dt = 0.3 * math.sqrt(500.0 * h ** 3 / (2.0 * math.pi * 0.07))  # capillary time-step limit
+    c = W.Case(name="cap", nx=nx, ny=ny, nz=1, h=h, rho_l=1000.0, mu_l=1e-2, rho_g=1.0, mu_g=1.8e-4,
+               sigma=0.07, theta_deg=theta_wall, dt=dt, dt_max=dt, cfl=0.0, inlet_u=0.0, pc0=0.0,
+               bc=(W.WALL, W.WALL, W.WALL, W.OUTLET, W.WALL, W.WALL), p_tol=1e-10, max_cg=500)
+    c = c.replace(**kw)
+    phi = np.ones((ny, nx))
+    phi[:plate, :] = 0.5
+    k = np.where(phi < 1.0, 1e-20, 0.0)
+    th = math.radians(theta_init)
+    R = math.sqrt(1e-6 / (th - math.sin(th) * math.cos(th)))
+    yc, xc = plate * h - R * math.cos(th), nx * h / 2
+    off = (np.arange(sub) + 0.5) / sub
+    X = (np.arange(nx)[:, None] + off[None, :]) * h
+    a = np.zeros((ny, nx))
+    for j in range(plate, ny):
+        ys = (j + off) * h
+        a[j] = ((X[:, :, None] - xc) ** 2 + (ys[None, None, :] - yc) ** 2 <= R * R).mean(axis=(1, 2))
+    c.porosity, c.permeability, c.alpha = W.to_xfast(phi[None]), W.to_xfast(k[None]), W.to_xfast(a[None])
+    W._zero_fields(c)
+    return c
+
+
+def angle(alpha, nx, ny, plate):
+    a = alpha.reshape(ny, nx)[plate:, :]
+    return 2.0 * math.degrees(math.atan(2.0 * a.sum(axis=0).max() / a[0].sum()))
+
+
+def test_cap_matches_oracle():
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    case = cap_case(60, 30, 1e-4, 3, 90.0, 60.0, p_tol=1e-15, dt=1e-5)
+    g, o = mdbs.Simulation(case), OracleSim(case)
+    g.step(100)
+    o.step(100)
+    fg, fo = g.fields(), o.fields()
+    for k in ("alpha", "p", "ux", "uy"):
+        assert np.linalg.norm(fg[k] - fo[k]) <= 1e-9 * np.linalg.norm(fo[k]), k
+    g.close()
+    o.close()
+
+
+@pytest.mark.parametrize("theta_init,theta_wall,steps", [(90.0, 60.0, 4000), (120.0, 120.0, 1000),
+                                                         (150.0, 150.0, 1000)])
+def test_caps_reach_the_imposed_angle(theta_init, theta_wall, steps):
+    from paper_2003_08374_gb300 import mdbs
+    case = cap_case(120, 60, 5e-5, 6, theta_init, theta_wall)
+    s = mdbs.Simulation(case)
+    s.step(steps)
+    f = s.fields()
+    assert abs(angle(f["alpha"], 120, 60, 6) - theta_wall) <= 5.0
+    assert max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max()) < 0.1
+    s.close()
