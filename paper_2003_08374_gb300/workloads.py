@@ -20,6 +20,7 @@ identical arrays.  Recipes:
   (water injected into air or oil, optional gravity along the flow).
 * ``capillary_column`` -- the gravity-capillarity column of section 4.1.3
   (step-wise initial saturation relaxing to capillary-gravity equilibrium).
+* ``capillary_rise`` -- water rising between porous walls (section 4.2.2).
 
 Every array is x-fastest: cell c = i + nx*(j + ny*k).  Face arrays hold
 (nx+1)*ny*nz x-faces, nx*(ny+1)*nz y-faces and nx*ny*(nz+1) z-faces; a 2-D
@@ -293,6 +294,37 @@ def capillary_column(ny=1500, length=1.0, model=BROOKS_COREY, phi=0.5, k0=1e-11,
     a = np.zeros(ny)
     a[: ny // 2] = 0.5
     c.alpha = a
+    _zero_fields(c)
+    return c
+
+
+def capillary_rise(cells_across=16, walls=2, width=1e-3, height=12.5e-3, meniscus=8e-3, theta=45.0,
+                   mu_l=1e-2, **kw) -> Case:
+    """Capillary rise of section 4.2.2: a 2-D tube 1 mm wide between porous walls of
+    negligible permeability (k0 = 1e-20 m^2, porosity 0.5, ``walls`` cells thick), water
+    below ``meniscus`` and air above, contact angle 45 degrees, gravity -9.81 m/s^2 along y.
+    The bottom is a pressure boundary at the level of an infinite reservoir (p = 0, water
+    enters with the saturation of the cell above it) and the top is open (p = 0), so the
+    meniscus rises toward h = 2 sigma cos(theta) / (rho g width) = 10.1 mm.  The liquid
+    viscosity defaults to 1e-2 Pa s (ten times water's) to damp the approach; the time
+    step is 0.3 of the capillary-wave limit sqrt(rho_mean h^3 / (2 pi sigma))."""
+    h = width / cells_across
+    nx = cells_across + 2 * walls
+    ny = int(round(height / h))
+    dt = 0.3 * math.sqrt(500.0 * h ** 3 / (2.0 * math.pi * 0.07))
+    c = Case(name="capillary_rise_%dx%d" % (nx, ny), nx=nx, ny=ny, nz=1, h=h, rho_l=1000.0, mu_l=mu_l,
+             rho_g=1.0, mu_g=0.018 * mu_l, sigma=0.07, theta_deg=theta, g=(0.0, -9.81, 0.0), pc0=0.0,
+             dt=dt, dt_max=dt, cfl=0.0, bc=(WALL, WALL, OUTLET, OUTLET, WALL, WALL), inlet_u=0.0,
+             p_tol=1e-10, max_cg=500)
+    c = c.replace(**kw)
+    phi = np.ones((ny, nx))
+    phi[:, :walls] = 0.5
+    phi[:, nx - walls:] = 0.5
+    a = np.zeros((ny, nx))
+    a[: int(round(meniscus / h)), :] = 1.0
+    c.porosity = to_xfast(phi[None])
+    c.permeability = to_xfast(np.where(phi < 1.0, 1e-20, 0.0)[None])
+    c.alpha = to_xfast(a[None])
     _zero_fields(c)
     return c
 

@@ -73,3 +73,30 @@ def test_caps_reach_the_imposed_angle(theta_init, theta_wall, steps):
     assert abs(angle(f["alpha"], 120, 60, 6) - theta_wall) <= 5.0
     assert max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max()) < 0.1
     s.close()
+
+
+def test_capillary_rise_matches_oracle_and_rises():
+    """Section 4.2.2's tube: parity with the oracle over 50 steps, then the meniscus rising
+    from 8 mm toward h = 2 sigma cos(45) / (rho g w) = 10.1 mm (the full run to 10.06 mm
+    takes 72000 steps; here 6000)."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.capillary_rise(p_tol=1e-15)
+    g, o = mdbs.Simulation(case), OracleSim(case)
+    g.step(50)
+    o.step(50)
+    fg, fo = g.fields(), o.fields()
+    for k in ("alpha", "p", "uy"):
+        assert np.linalg.norm(fg[k] - fo[k]) <= 1e-9 * np.linalg.norm(fo[k]), k
+    o.close()
+    g.close()
+    case = W.capillary_rise()
+    s = mdbs.Simulation(case)
+    heights = []
+    for _ in range(2):
+        s.step(3000)
+        a = s.fields()["alpha"].reshape(case.ny, case.nx)[:, 2:case.nx - 2]
+        heights.append(float(a.mean(axis=1).sum() * case.h))
+    s.close()
+    assert 8.05e-3 < heights[0] < heights[1] < 10.2e-3, heights  # 8.15 and 8.43 mm measured

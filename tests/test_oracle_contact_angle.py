@@ -77,3 +77,23 @@ def test_cap_relaxes_to_the_imposed_angle():
     s.step(2000)
     assert abs(measured_angle(s.fields()["alpha"]) - 60.0) <= 5.0
     s.close()
+
+
+@pytest.mark.parametrize("theta,sign", [(45.0, 1.0), (135.0, -1.0)])
+def test_capillary_rise_starts_in_the_wetting_direction(theta, sign):
+    """Section 4.2.2's tube between porous walls (16 cells across 1 mm, bottom open to a
+    reservoir at p = 0): a wetting wall (45 degrees) draws the meniscus up from 8 mm, a
+    non-wetting one (135 degrees) pushes it down; the liquid that enters or leaves is the
+    net boundary flux.  (The GPU run to the steady height is in the GPU tests.)"""
+    case = W.capillary_rise(theta=theta)
+    s = OracleSim(case)
+    heights = []
+    for _ in range(2):
+        s.step(100)
+        a = s.fields()["alpha"].reshape(case.ny, case.nx)[:, 2:case.nx - 2]
+        heights.append(float(a.mean(axis=1).sum() * case.h))
+    st = s.stats()
+    s.close()
+    assert sign * (heights[0] - 8e-3) > 0 and sign * (heights[1] - heights[0]) > 0, heights
+    vol0 = float((case.porosity * case.alpha).sum()) * case.h ** 3
+    assert abs(st["mass"] - vol0 - st["boundary_in"]) <= 1e-12 * st["mass"]
