@@ -149,7 +149,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
  * pressure, Eq. 9) from host arrays laid out as above; uz may be NULL in 2-D.
  * Wall and inlet face velocities are overwritten by their boundary values.
  * Resets the statistics.  MDBS_ERR_ARG if alpha is not finite or lies more than
- * 1e-9 outside [0, 1] (round-off excursions of a previous step are accepted).
+ * 1e-6 outside [0, 1] (the excursions a run can accumulate -- transport through a
+ * velocity field divergence-free only to the pressure tolerance -- are accepted).
  */
 int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const double* uy,
                     const double* uz, const double* p);

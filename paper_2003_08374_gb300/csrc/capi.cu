@@ -763,14 +763,16 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   if (!alpha || !ux || !uy || !p || (s->P.dim == 3 && !uz)) return fail(s, MDBS_ERR_ARG, "NULL field");
   Activate act(s);
   // round-off excursions of the flux-corrected update (|.| ~ 1e-30) must survive a
-  // get_fields / set_fields round trip, so the check allows 1e-9 outside [0, 1]
+  // get_fields / set_fields round trip; so must the excursions that transport through a
+  // velocity field divergence-free only to the pressure tolerance accumulates over a run
+  // (beyond 1e-9 after tens of mixed-precision steps at 1e-8), so the check allows 1e-6
   // branch-free inner loop (vectorised by the host compiler), one exit test per chunk;
   // NaN fails both comparisons
   for (long long c0 = 0; c0 < s->P.cells; c0 += 4096) {
     const long long c1 = std::min(s->P.cells, c0 + 4096);
     int ok = 1;
-    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= -1e-9) & (int)(alpha[c] <= 1.0 + 1e-9);
-    if (!ok) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-9)");
+    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= -1e-6) & (int)(alpha[c] <= 1.0 + 1e-6);
+    if (!ok) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-6)");
   }
   const double* src[3] = {ux, uy, uz};
   CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));

@@ -337,12 +337,38 @@ __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* _
   xw[c] = v * dinv[c];
 }
 
+// The first post-smoothing update of a level, with the coarse-grid correction of
+// the piecewise-constant prolongation applied on the fly: every neighbour of a
+// cell being updated has the other colour, and reads x_nb + e_parent(nb) -- the
+// value the separate prolongation would have stored, rounded the same way.  The
+// cells of the updated colour are overwritten and the other colour is
+// overwritten by the next half sweep, so the corrected values need not be stored.
+template <typename R, typename CT>
+__device__ __forceinline__ void smooth_cell_corr(const R* __restrict__ bb, const R* __restrict__ dinv,
+                                                 const R* __restrict__ xr, R* __restrict__ xw, CT Tx, CT Ty, CT Tz,
+                                                 int n0, int n1, int n2, int i, int j, int k, long long c,
+                                                 long long cm, long long cp, const Level<R>& Co) {
+  const R* __restrict__ ex = Co.x;
+  auto e = [&](int a, int b, int d) -> R {
+    return ex[lpos(Co.n, Co.cz[0] ? a >> 1 : a, Co.cz[1] ? b >> 1 : b, Co.cz[2] ? d >> 1 : d)];
+  };
+  const long long sy = n0, sz = (long long)n0 * n1;
+  R v = bb[c];
+  if (i > 0) v = fma_r(Tx[cm], xr[cm] + e(i - 1, j, k), v);
+  if (i + 1 < n0) v = fma_r(Tx[c], xr[cp] + e(i + 1, j, k), v);
+  if (j > 0) v = fma_r(Ty[c - sy], xr[c - sy] + e(i, j - 1, k), v);
+  if (j + 1 < n1) v = fma_r(Ty[c], xr[c + sy] + e(i, j + 1, k), v);
+  if (k > 0) v = fma_r(Tz[c - sz], xr[c - sz] + e(i, j, k - 1), v);
+  if (k + 1 < n2) v = fma_r(Tz[c], xr[c + sz] + e(i, j, k + 1), v);
+  xw[c] = v * dinv[c];
+}
+
 // Red-black half sweep of colour col over REP rows of kBlock half-row cells per
 // work item.  Skips domains whose CG has converged (the V-cycle only runs inside
 // CG iterations).  The level's arrays go to restrict-qualified registers once per
 // work item so that the REP rows of an item overlap their loads: the colour being
 // written and the colour being read are disjoint cells of the same array.
-template <typename R, int REP>
+template <typename R, int REP, bool PRO = false>
 __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
     k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
   MDBS_DEPENDENT_ENTRY();
@@ -371,7 +397,10 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
         // x-split positions: this colour's run, and the other colour's run for i -/+ 1
         const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
         const unsigned cm = sh ? rb + ti : rb + half + ti - 1, cp = sh ? rb + ti + 1 : rb + half + ti;
-        smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
+        if constexpr (PRO)
+          smooth_cell_corr<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, levels_of<R>(G)[l + 1]);
+        else
+          smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
       }
     });
   }
@@ -1559,17 +1588,24 @@ struct Dirs {
   }
 };
 
-template <typename R>
-static void smooth_half(const BatchPlan& B, int l, int col, int zero, Dirs& D, cudaStream_t s) {
+// pro: the half sweep applies the prolongation from level l + 1 to the neighbours
+// it reads (the first post-smoothing half sweep; no separate prolongation launch)
+template <typename R, bool PRO>
+static void smooth_half_t(const BatchPlan& B, int l, int col, int zero, Dirs& D, cudaStream_t s) {
   const int id = l == 0 ? K_SMOOTH0 : K_SMOOTHC;
   const Work& w = B.lhalf[l];
   const int rev = D.next(l);
   switch (w.rep) {
-    case 8: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 8>), B.cg, w, l, col, zero, rev); break;
-    case 4: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 4>), B.cg, w, l, col, zero, rev); break;
-    case 2: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 2>), B.cg, w, l, col, zero, rev); break;
-    default: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 1>), B.cg, w, l, col, zero, rev); break;
+    case 8: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 8, PRO>), B.cg, w, l, col, zero, rev); break;
+    case 4: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 4, PRO>), B.cg, w, l, col, zero, rev); break;
+    case 2: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 2, PRO>), B.cg, w, l, col, zero, rev); break;
+    default: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 1, PRO>), B.cg, w, l, col, zero, rev); break;
   }
+}
+
+template <typename R>
+static void smooth_half(const BatchPlan& B, int l, int col, int zero, Dirs& D, cudaStream_t s) {
+  smooth_half_t<R, false>(B, l, col, zero, D, s);
 }
 
 template <typename R>
@@ -1636,6 +1672,13 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     prof_end(K_TAIL, s);
   }
   for (int l = B.max_first - 1; l >= 0; l--) {
+    if (!fused_sweeps<R>(B) && nu2 > 0) {
+      // split sweeps: the first post-smoothing half sweep applies the prolongation
+      smooth_half_t<R, true>(B, l, 1, 0, D, s);
+      smooth_half<R>(B, l, 0, 0, D, s);
+      for (int it = 1; it < nu2; it++) sweep<R>(B, l, 1, false, 0, D, s);
+      continue;
+    }
     MDBS_LAUNCH(l == 0 ? K_PROLONG0 : K_PROLONGC, grid_of(B, B.lfine[l]), kBlock, s, k_prolong<R>, B.cg, B.lfine[l],
                 l, D.next(l), cur(nu1));
     for (int it = 0; it < nu2; it++) sweep<R>(B, l, 1, false, cur(nu1 + it), D, s);
