@@ -196,10 +196,11 @@ def peaks():
 
 
 def kernel_source_hash():
-    h = hashlib.sha256()
-    for f in ("pressure.cu", "mdbs_internal.cuh"):
-        h.update(open(os.path.join(ROOT, "paper_2003_08374_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:12]
+    """Hash of the half-sweep kernel's source (smooth_cell, smooth_cell_corr, k_smooth)."""
+    src = open(os.path.join(ROOT, "paper_2003_08374_gb300", "csrc", "pressure.cu")).read()
+    a = src.index("// One red-black Gauss-Seidel update of cell c")
+    b = src.index("// ------------------------------------------------------------------ fused red-black sweep (FP32)")
+    return hashlib.sha256(src[a:b].encode()).hexdigest()[:12]
 
 
 def measured_traffic(kernel, precision_tag, cells):
@@ -229,16 +230,18 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM cl
 
 def roofline(prof, cells, word, fp64):
     """Roofline of the finest-level red-black half sweep.  Per V-cycle the finest level runs
-    8 half sweeps (nu1 = nu2 = 2): 1 from a zero guess (b, 1/diag, x written on half the cells:
-    3 words per updated cell) and 7 full ones (b, 1/diag, x written and the other colour's x read
-    on half the cells, the three face-coefficient arrays in full: 5 words per cell).  Flops per
-    updated cell: 6 fused multiply-adds and one multiply (13), 1 for the zero-guess sweep."""
+    8 half sweeps (nu1 = nu2 = 2); the first post-smoothing one also applies the prolongation
+    and is timed with it, so `smooth_fine` holds 7: 1 from a zero guess (b, 1/diag, x written on
+    half the cells: 3 words per updated cell) and 6 full ones (b, 1/diag, x written and the other
+    colour's x read on half the cells, the three face-coefficient arrays in full: 5 words per
+    cell).  Flops per updated cell: 6 fused multiply-adds and one multiply (13), 1 for the
+    zero-guess sweep."""
     if DOMINANT not in prof:
         return None
     tot_ms, cnt = prof[DOMINANT]
     avg_s = tot_ms / cnt / 1e3
-    alg_bytes = (7 * 5 * word + 1 * 1.5 * word) / 8 * cells
-    flops = (7 * 13 + 1 * 1) / 8 * cells / 2
+    alg_bytes = (6 * 5 * word + 1 * 1.5 * word) / 7 * cells
+    flops = (6 * 13 + 1 * 1) / 7 * cells / 2
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     gbs = alg_bytes / avg_s / 1e9

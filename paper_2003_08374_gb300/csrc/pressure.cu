@@ -1592,7 +1592,8 @@ struct Dirs {
 // it reads (the first post-smoothing half sweep; no separate prolongation launch)
 template <typename R, bool PRO>
 static void smooth_half_t(const BatchPlan& B, int l, int col, int zero, Dirs& D, cudaStream_t s) {
-  const int id = l == 0 ? K_SMOOTH0 : K_SMOOTHC;
+  // the half sweep that carries the prolongation is timed as the prolongation
+  const int id = PRO ? (l == 0 ? K_PROLONG0 : K_PROLONGC) : (l == 0 ? K_SMOOTH0 : K_SMOOTHC);
   const Work& w = B.lhalf[l];
   const int rev = D.next(l);
   switch (w.rep) {
