@@ -97,6 +97,11 @@ static double frac_flow(const orc_state* s, const int c[3]) {
   return M > 0.0 ? s->Ml[i] / M : s->alpha[i];
 }
 static void cpy3(int dst[3], const int src[3]) { dst[0] = src[0]; dst[1] = src[1]; dst[2] = src[2]; }
+/* phi^-2 of the cell at c, zero-gradient ghosts */
+static double inv_phi2(const orc_state* s, const int c[3]) {
+  double ph = cval(s, s->phi, c);
+  return 1.0 / (ph * ph);
+}
 static void coords_of(const int n[3], long idx, int c[3]) {
   c[0] = (int)(idx % n[0]);
   c[1] = (int)((idx / n[0]) % n[1]);
@@ -516,6 +521,7 @@ static void momentum_assemble(orc_state* s, double dt) {
           double cconv = V * rhof / (phif * phif * h);
           double ap = at + V * Df; /* Darcy drag K_fs, Eq. 46 */
           double TT = 0.0;        /* explicit div(mu grad(v)^T) */
+          double vgrad = 0.0;     /* v . grad(phi^-2) at the face */
           for (int e = 0; e < s->dim; e++) {
             for (int sg = -1; sg <= 1; sg += 2) {
               int slot = 2 * e + (sg > 0);
@@ -537,6 +543,26 @@ static void momentum_assemble(orc_state* s, double dt) {
               else
                 w = 0.25 * (ue_cell(s, e, L, 0) + ue_cell(s, e, L, 1) + ue_cell(s, e, R, 0) +
                             ue_cell(s, e, R, 1));
+              if (sg < 0) {
+                /* e-derivative of phi^-2 at the face: across it (e == d), or the mean
+                 * of the two cells' central differences (e != d) */
+                double ge;
+                if (e == d) {
+                  ge = (inv_phi2(s, R) - inv_phi2(s, L)) / h;
+                } else {
+                  int Lm[3], Lp[3], Rm[3], Rp[3];
+                  cpy3(Lm, L);
+                  cpy3(Lp, L);
+                  cpy3(Rm, R);
+                  cpy3(Rp, R);
+                  Lm[e] -= 1;
+                  Lp[e] += 1;
+                  Rm[e] -= 1;
+                  Rp[e] += 1;
+                  ge = ((inv_phi2(s, Lp) - inv_phi2(s, Lm)) + (inv_phi2(s, Rp) - inv_phi2(s, Rm))) / (4.0 * h);
+                }
+                vgrad += w * ge;
+              }
               double cup = cconv * (sg < 0 ? fmax(w, 0.0) : fmax(-w, 0.0));
               double mus;
               if (e == d) {
@@ -585,6 +611,19 @@ static void momentum_assemble(orc_state* s, double dt) {
               TT += tsum / h;
             }
           }
+          /* The rest of Eq. 21's convection.  (1/phi) div(rho v v / phi) equals the
+           * advective (rho/phi^2)(v.grad)v above plus (1/phi) v div(rho v / phi); with
+           * div v = 0 and the density carried by the flow (its part cancels the
+           * v d(rho)/dt left out of the Euler term), what remains is
+           * (rho/phi) v (v.grad(1/phi)) = (rho/2) v (v.grad(phi^-2)), non-zero only where
+           * the porosity varies along the flow.  Its coefficient Gp multiplies u_f:
+           * implicit (on the diagonal) where it decelerates the flow, explicit where it
+           * accelerates it. */
+          double Gp = 0.5 * rhof * vgrad;
+          if (Gp >= 0.0)
+            ap += V * Gp;
+          else
+            S -= V * Gp * s->u[d][f];
           s->aP[d][f] = ap;
           s->rhs0[d][f] = S + V * (TT + s->B[d][f]);
         }
