@@ -443,6 +443,7 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   const double cconv = V * rhof * inv_phi * inv_phi * inv_h;
   double ap = at + V * Df;
   double tt = 0.0;
+  double vgrad = 0.0;  // v . grad(phi^-2) at the face
   for (int e = 0; e < P.dim; e++) {
     const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
     // e-velocities on the low / high e-faces of the (clamped) low and high cells
@@ -456,6 +457,17 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       vRhi = F.u[e][face_index(P.n, e, ri + ei, rj + ej, rk + ek)];
     }
     const double w = (e == d) ? uf : 0.25 * (vLlo + vLhi + vRlo + vRhi);
+    // e-derivative of phi^-2 at the face: across it (e == d), or the mean of the two
+    // cells' central differences (e != d)
+    if (e == d) {
+      vgrad += w * ((ghost_read(F.iphi2, P.n, i, j, k) - ghost_read(F.iphi2, P.n, li, lj, lk)) * inv_h);
+    } else {
+      const double gL = ghost_read(F.iphi2, P.n, li + ei, lj + ej, lk + ek) -
+                        ghost_read(F.iphi2, P.n, li - ei, lj - ej, lk - ek);
+      const double gR = ghost_read(F.iphi2, P.n, i + ei, j + ej, k + ek) -
+                        ghost_read(F.iphi2, P.n, i - ei, j - ej, k - ek);
+      vgrad += w * ((gL + gR) * (0.25 * inv_h));
+    }
     for (int sg = -1; sg <= 1; sg += 2) {
       const int slot = 2 * e + (sg > 0);
       const int ce = (e == 0 ? i : (e == 1 ? j : k)) + sg;
@@ -498,8 +510,18 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       tt += ts * inv_h;
     }
   }
+  // The rest of Eq. 21's convection: with div v = 0 and the density carried by the
+  // flow, (1/phi) div(rho v v / phi) minus the advective part above is
+  // (rho/2) v (v . grad(phi^-2)), non-zero only where the porosity varies along the
+  // flow; implicit where it decelerates the flow, explicit where it accelerates it.
+  const double Gp = 0.5 * rhof * vgrad;
+  double Sx = S;
+  if (Gp >= 0.0)
+    ap += V * Gp;
+  else
+    Sx -= V * Gp * uf;
   F.aP[d][f] = 1.0 / ap;  // stored as the reciprocal: every later use multiplies
-  F.rhs0[d][f] = S + V * (tt + Bf);
+  F.rhs0[d][f] = Sx + V * (tt + Bf);
 }
 
 // H(u) = sum_nb a_nb u_nb + rhs0 of an unknown face
@@ -750,6 +772,7 @@ __device__ __forceinline__ void b_static_geometry(const Prm& P, const Fld& F, lo
     }
   }
   for (int e = 0; e < 3; e++) const_cast<double*>(F.nw[e])[c] = n[e];
+  const_cast<double*>(F.iphi2)[c] = 1.0 / (phi[c] * phi[c]);
 }
 
 __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
