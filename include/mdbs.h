@@ -34,7 +34,9 @@
  *
  * Errors.  Every int-returning call returns MDBS_OK (0) or a negative code; a
  * message is kept per simulation (mdbs_last_error).  After MDBS_ERR_DIVERGED or
- * MDBS_ERR_CUDA the fields hold the state reached when the error was found.
+ * MDBS_ERR_CUDA the fields hold the state reached when the error was found; after
+ * MDBS_ERR_NOT_CONVERGED every requested step was taken, with the last CG iterate
+ * of each solve that stopped at max_cg.
  */
 #ifndef MDBS_H
 #define MDBS_H
@@ -51,7 +53,7 @@ extern "C" {
 #define MDBS_ERR_OOM (-2)           /* device allocation failed */
 #define MDBS_ERR_CUDA (-3)          /* a CUDA call failed */
 #define MDBS_ERR_DIVERGED (-4)      /* a non-finite value appeared in the fields */
-#define MDBS_ERR_NOT_CONVERGED (-5) /* reserved: pressure solves that hit max_cg are counted in stats */
+#define MDBS_ERR_NOT_CONVERGED (-5) /* a pressure solve stopped at max_cg above p_tol (the step was taken) */
 
 #define MDBS_BC_WALL 0
 #define MDBS_BC_INLET 1
@@ -148,9 +150,13 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
  * Sets the state (saturation alpha_l in [0, 1], Eq. 8; face velocities, Eq. 10;
  * pressure, Eq. 9) from host arrays laid out as above; uz may be NULL in 2-D.
  * Wall and inlet face velocities are overwritten by their boundary values.
- * Resets the statistics.  MDBS_ERR_ARG if alpha is not finite or lies more than
- * 1e-6 outside [0, 1] (the excursions a run can accumulate -- transport through a
- * velocity field divergence-free only to the pressure tolerance -- are accepted).
+ * Resets the statistics (the simulated time and the time step, too).
+ * MDBS_ERR_ARG if alpha is not finite or lies outside [0, 1] by more than 1e-9 or
+ * than the extremes this simulation's own steps reached (transport through a velocity
+ * field divergence-free only to the pressure tolerance moves alpha outside [0, 1] by
+ * dt |div(A u)| / (phi V) per step; a get_fields / set_fields round trip of such a
+ * state is accepted).  A non-finite pressure or velocity is copied in and reported:
+ * MDBS_ERR_DIVERGED (the state is set; mdbs_step then reports it too).
  */
 int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const double* uy,
                     const double* uz, const double* p);
@@ -158,15 +164,26 @@ int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const 
 /*
  * Advances n >= 1 time steps (section 3.2).  Runs on the simulation's stream and
  * returns after the last step has finished on the device.  MDBS_ERR_DIVERGED if
- * a non-finite value appears.
+ * a non-finite value appears; MDBS_ERR_NOT_CONVERGED if a pressure solve (Eq. 53) of
+ * these steps stopped at max_cg with its relative residual above p_tol (the steps
+ * were taken; mdbs_stats.not_converged counts such solves since mdbs_set_fields).
  */
 int mdbs_step(mdbs_sim* sim, int32_t n);
 
-/* Copies the state to host arrays (any pointer may be NULL to skip it). */
+/*
+ * Copies the state -- the unknowns of the model's summary (section 2.2, Eq. 21):
+ * saturation alpha_l (Eq. 8), single-field face velocities (Eq. 10) and pressure
+ * (Eq. 9) -- to host arrays laid out as above (any pointer may be NULL to skip it;
+ * uz is ignored in 2-D).  Waits for the simulation's stream.  MDBS_ERR_CUDA if a copy
+ * fails.
+ */
 int mdbs_get_fields(const mdbs_sim* sim, double* alpha, double* ux, double* uy, double* uz,
                     double* p);
 
-/* Releases the device memory; NULL is accepted. */
+/* Ends a simulation made by mdbs_create (its device memory goes back to cudaFree or to
+ * the allocator hook that provided it).  No counterpart in the paper.  Waits for the
+ * simulation's work; NULL is accepted.  A simulation still in a batch must leave it
+ * (mdbs_batch_remove / mdbs_batch_destroy) first. */
 void mdbs_destroy(mdbs_sim* sim);
 
 /* ---------------- batches ---------------- */
@@ -198,7 +215,9 @@ int mdbs_batch_create(mdbs_sim* const* sims, int32_t n, mdbs_batch** out);
  * On a CUDA error the batch keeps its previous members. */
 int mdbs_batch_add(mdbs_batch* batch, mdbs_sim* sim);
 int mdbs_batch_remove(mdbs_batch* batch, mdbs_sim* sim);
-/* Advances every member n >= 1 steps; MDBS_ERR_DIVERGED names the first diverged member. */
+/* Advances every member n >= 1 steps; MDBS_ERR_DIVERGED names the first diverged member,
+ * MDBS_ERR_NOT_CONVERGED (when no member diverged) the first member whose pressure
+ * solve stopped at max_cg above p_tol. */
 int mdbs_batch_step(mdbs_batch* batch, int32_t n);
 /* Runs the batch's kernels on the given cudaStream_t (NULL: legacy default stream). */
 int mdbs_batch_set_stream(mdbs_batch* batch, void* cuda_stream);
@@ -227,7 +246,12 @@ void mdbs_batch_destroy(mdbs_batch* batch);
  *                 columns and chunks of sweep_kz planes (every array read once per
  *                 pair); 0, and every FP64 level, runs two half sweeps (then
  *                 smooth_rows applies)
- * Default: {1, 4096, 0, 0, 1}.  Values outside these sets give MDBS_ERR_ARG.
+ *   coarse_coop : 0 or 1; 1 runs every level between the finest one and the tail,
+ *                 and the tail itself (one CTA per domain; tail_ctas then does not
+ *                 apply), in ONE cooperative launch whose phases are separated by
+ *                 grid-wide barriers instead of kernel boundaries (with sweep_kz 0 and
+ *                 at least one such level; otherwise it has no effect)
+ * Default: {1, 4096, 0, 0, 1, 0}.  Values outside these sets give MDBS_ERR_ARG.
  */
 typedef struct {
   int32_t smooth_rows;
@@ -235,6 +259,7 @@ typedef struct {
   int32_t snake;
   int32_t sweep_kz;
   int32_t tail_ctas;
+  int32_t coarse_coop;
 } mdbs_tuning;
 
 /* Sets or reads the schedule of a simulation that is not in a batch (the step
@@ -248,7 +273,8 @@ int mdbs_batch_get_tuning(const mdbs_batch* batch, mdbs_tuning* out);
  * Picks the fastest schedule for this simulation (or batch) by timing real steps:
  * starting from the current schedule it tries the alternatives of snake, then of
  * sweep_kz (mixed precisions only), then of smooth_rows (when the half sweeps
- * run), then of (tail_cells, tail_ctas) pairs (coordinate descent), each for one untimed and
+ * run), then of coarse_coop, then of (tail_cells, tail_ctas) pairs (coordinate
+ * descent), each for one untimed and
  * trial_steps >= 1 timed steps (CUDA events on the simulation's stream), and keeps
  * a change only when it is faster.  The device state (fields, step scalars) is
  * copied aside first and restored after every trial, so the simulation continues
@@ -357,10 +383,14 @@ int mdbs_check_bounded_wait(double* waited_s);
  * Allocates nothing: its scratch is a file-scope __device__ array of
  * MDBS_STATIC_STATS_MAX_BLOCKS * 4 doubles shared by every call.  The first call on a
  * device looks up that array's device address with the device current; make that first
- * call before any stream capture.  Calls whose kernels overlap on the GPU race on the
- * shared scratch: serialise them (one stream, or events).  Each call overwrites every
- * scratch value it reads, so nothing needs clearing between calls.  Returns MDBS_OK,
- * MDBS_ERR_ARG or MDBS_ERR_CUDA; the result is ready when the stream reaches it.
+ * call before any stream capture.  The address is kept for the life of the process: after
+ * cudaDeviceReset on a device it is stale, so do not call this function on that device
+ * again.  Calls whose kernels overlap on the GPU race on the shared scratch: serialise
+ * them (one stream, or events).  Each call overwrites every scratch value it reads, so
+ * nothing needs clearing between calls.  Returns MDBS_OK, MDBS_ERR_ARG or MDBS_ERR_CUDA;
+ * the result is ready when the stream reaches it.  A CUDA error already pending on the
+ * calling thread (from the caller's earlier work) gives MDBS_ERR_CUDA without a launch
+ * and stays pending; an error of this call's own launches is cleared.
  */
 int mdbs_field_stats_static(int64_t cells, double cell_volume, const double* porosity, const double* alpha,
                             const double* p, double* out, void* stream);

@@ -17,13 +17,14 @@ long long faces_total(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P
 }  // namespace
 
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, int tail_ctas, BatchPlan* out) {
+                        int sweep_kz, int tail_ctas, int coarse_coop, BatchPlan* out) {
   BatchPlan B{};
   B.ndom = ndom;
   B.flexible = flexible;
   B.snake = snake;
   B.sweep_kz = sweep_kz;
   B.tail_ctas = tail_ctas;
+  B.coarse_coop = coarse_coop;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -107,6 +108,9 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   if (e == cudaSuccess) e = cudaMalloc(&B.any_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&B.err_flag, sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(B.err_flag, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&B.coop_ctr, sizeof(unsigned long long));
+  if (e == cudaSuccess) e = cudaMemset(B.coop_ctr, 0, sizeof(unsigned long long));
+  if (e == cudaSuccess && coarse_coop) e = coop_grid_size(flexible, B.tail_words, &B.coop_grid);
   if (e != cudaSuccess) {
     plan_destroy(&B);
     return e;
@@ -141,6 +145,8 @@ void plan_destroy(BatchPlan* B) {
   if (B->cg) cudaFree(B->cg);
   if (B->any_flag) cudaFree(B->any_flag);
   if (B->err_flag) cudaFree(B->err_flag);
+  if (B->coop_ctr) cudaFree(B->coop_ctr);
+  B->coop_ctr = nullptr;
   B->table_storage = nullptr;
   B->sd = nullptr;
   B->cg = nullptr;

@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>  // header-only: the ranges cost nothing unless a profiler attaches
+
 #include "../../include/mdbs.h"
 #include "mdbs_internal.cuh"
 
@@ -23,7 +25,7 @@ const char* const kKernelNames[K_COUNT] = {
     "curvature", "momentum_assemble", "jacobi", "hbya", "correct", "boundary", "field_stats", "cfl",
     "static_geometry", "pressure_assemble", "diag", "convert", "coarsen", "smooth_fine", "smooth_coarse",
     "zero", "restrict_fine", "restrict_coarse", "prolong_fine", "prolong_coarse", "cg_resid0",
-    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d", "tail_vcycle"};
+    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d", "tail_vcycle", "coarse_coop"};
 
 // Per-simulation launch counter and optional event timer.
 struct Profiler {
@@ -126,6 +128,7 @@ struct mdbs_sim {
   double* scal;       // device step scalars (kSlot* in mdbs_internal.cuh)
   double* host_scal;  // pinned copy of scal
   mdbs_stats st;
+  double alpha_lo_seen = 0.0, alpha_hi_seen = 1.0;  // extremes of alpha this simulation's steps produced
   bool fields_set;
   bool in_batch;
   std::string err;
@@ -232,6 +235,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   F.k0 = cd();
   F.is_free = (uint8_t*)take(L.cells);
   for (int e = 0; e < 3; e++) F.nw[e] = cd();
+  F.iphi2 = cd();
   F.alpha = cd();
   F.p = cd();
   F.Ml = cd();
@@ -311,7 +315,19 @@ int stats_from(mdbs_sim* s, const double* h) {
   s->st.cg_iters_total = (int64_t)h[kSlotItersTotal];
   s->st.not_converged = (int32_t)h[kSlotNotConverged];
   if (h[kSlotBad] != 0.0) return fail(s, MDBS_ERR_DIVERGED, "non-finite alpha or pressure");
+  s->alpha_lo_seen = std::min(s->alpha_lo_seen, s->st.alpha_min);
+  s->alpha_hi_seen = std::max(s->alpha_hi_seen, s->st.alpha_max);
   return MDBS_OK;
+}
+
+// MDBS_ERR_NOT_CONVERGED when pressure solves of the steps just taken stopped at max_cg
+int convergence_check(mdbs_sim* s, double not_converged_before) {
+  const double nc = s->host_scal[kSlotNotConverged] - not_converged_before;
+  if (nc <= 0.0) return MDBS_OK;
+  return fail(s, MDBS_ERR_NOT_CONVERGED,
+              std::to_string((long long)nc) + " pressure solve(s) stopped at max_cg before the tolerance; the steps "
+              "were taken (last relative residual " + std::to_string(s->st.cg_resid[0]) + " ... " +
+              std::to_string(s->st.cg_resid[std::max(0, std::min(7, s->opt.n_corr - 1))]) + ")");
 }
 
 // copies the device scalars and the statistics they hold; checks health
@@ -334,17 +350,35 @@ StepDom step_view(const mdbs_sim* s) {
 
 // Enqueues one time step (section 3.2) of every domain of the plan on st.
 // capture: st is capturing a graph.  Returns a CUDA error.
+// NVTX range of one step phase (host-side marks around the phase's launches: in eager
+// steps they bracket the kernels; under graph capture they mark the capture)
+struct Phase {
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+};
+
 cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool capture) {
   const BatchPlan& B = ex.plan;
-  // 1. saturation (Eq. 15) by flux-corrected transport
-  launch_alpha_step(B, st);
-  // 3. properties at alpha^{k+1} (the old density is kept for the Euler source of Eq. 46)
-  launch_properties(B, st);
-  // 4. momentum predictor (Eq. 50) from u^k and p^k
-  launch_momentum_assemble(B, st);
-  launch_jacobi_sweeps(B, opt.mom_sweeps, st);
+  Phase step("mdbs step");
+  {
+    // 1. saturation (Eq. 15) by flux-corrected transport
+    Phase ph("saturation (Eq. 15, FCT)");
+    launch_alpha_step(B, st);
+  }
+  {
+    // 3. properties at alpha^{k+1}
+    Phase ph("properties (Eqs. 41-45)");
+    launch_properties(B, st);
+  }
+  {
+    // 4. momentum predictor (Eq. 50) from u^k and p^k
+    Phase ph("momentum predictor (Eq. 50)");
+    launch_momentum_assemble(B, st);
+    launch_jacobi_sweeps(B, opt.mom_sweeps, st);
+  }
   // 5. PISO correctors (Eqs. 51-53)
   for (int c = 0; c < opt.n_corr; c++) {
+    Phase ph("PISO corrector (Eqs. 51-53)");
     launch_hbya(B, st);
     launch_pressure_assemble(B, st);
     cudaError_t e = pressure_solve(B, opt.p_tol, opt.max_cg, opt.mg_nu1, opt.mg_nu2, opt.mg_coarse_sweeps, c,
@@ -352,14 +386,18 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
     if (e != cudaSuccess) return e;
     launch_correct(B, st);
   }
-  // 6. time and next time step; statistics and health sentinel
-  launch_time_advance(B, st);
-  launch_field_stats(B, st);
+  {
+    // 6. time and next time step; statistics and health sentinel
+    Phase ph("time step and health");
+    launch_time_advance(B, st);
+    launch_field_stats(B, st);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible, const mdbs_tuning& t) {
-  cudaError_t e = plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, t.tail_ctas, &ex.plan);
+  cudaError_t e =
+      plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, t.tail_ctas, t.coarse_coop, &ex.plan);
   if (e != cudaSuccess) return e;
   ex.planned = true;
   if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
@@ -424,7 +462,7 @@ cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaSt
   return cudaSuccess;
 }
 
-const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0, 1};
+const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0, 1, 0};
 
 // whether a kernel of the plan reported a bounded wait that ran out (synchronous read)
 bool plan_failed(const BatchPlan& B) {
@@ -438,7 +476,8 @@ bool valid_tuning(const mdbs_tuning* t) {
   return t && (t->smooth_rows == 1 || t->smooth_rows == 2 || t->smooth_rows == 4 || t->smooth_rows == 8) &&
          t->tail_cells >= 0 && t->tail_cells <= kTailCellsMax && (t->snake == 0 || t->snake == 1) &&
          (t->sweep_kz == 0 || t->sweep_kz == 4 || t->sweep_kz == 8 || t->sweep_kz == 16 || t->sweep_kz == 32) &&
-         (t->tail_ctas == 1 || t->tail_ctas == 2 || t->tail_ctas == 4 || t->tail_ctas == 8);
+         (t->tail_ctas == 1 || t->tail_ctas == 2 || t->tail_ctas == 4 || t->tail_ctas == 8) &&
+         (t->coarse_coop == 0 || t->coarse_coop == 1);
 }
 
 // (re)builds the batch-of-one plan of a simulation for its schedule
@@ -561,24 +600,26 @@ int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_optio
   const int snakes[] = {0, 1};
   const int kzs[] = {0, 4, 8, 16, 32};
   const int rows[] = {1, 2, 4, 8};
+  const int coops[] = {0, 1};
   // (tail_cells, tail_ctas): larger tails want more CTAs
   const int tails[][2] = {{0, 1}, {512, 1}, {4096, 1}, {4096, 4}, {32768, 4}, {32768, 8}, {262144, 8}};
-  for (int axis = 0; axis < 4 && e == cudaSuccess; axis++) {
+  for (int axis = 0; axis < 5 && e == cudaSuccess; axis++) {
     if (axis == 2 && best.sweep_kz > 0 && fp32_levels) continue;
     if (axis == 1 && !fp32_levels) continue;
-    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : axis == 2 ? 4 : 7;
+    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : axis == 2 ? 4 : axis == 3 ? 2 : 7;
     const mdbs_tuning base = best;
     for (int v = 0; v < nv && e == cudaSuccess; v++) {
       mdbs_tuning t = base;
       if (axis == 0) t.snake = snakes[v];
       if (axis == 1) t.sweep_kz = kzs[v];
       if (axis == 2) t.smooth_rows = rows[v];
-      if (axis == 3) {
+      if (axis == 3) t.coarse_coop = coops[v];
+      if (axis == 4) {
         t.tail_cells = tails[v][0];
         t.tail_ctas = tails[v][1];
       }
       if (t.snake == base.snake && t.sweep_kz == base.sweep_kz && t.smooth_rows == base.smooth_rows &&
-          t.tail_cells == base.tail_cells && t.tail_ctas == base.tail_ctas)
+          t.tail_cells == base.tail_cells && t.tail_ctas == base.tail_ctas && t.coarse_coop == base.coarse_coop)
         continue;
       double ms = 0.0;
       e = trial(t, &ms);
@@ -762,17 +803,21 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   if (!s) return MDBS_ERR_ARG;
   if (!alpha || !ux || !uy || !p || (s->P.dim == 3 && !uz)) return fail(s, MDBS_ERR_ARG, "NULL field");
   Activate act(s);
-  // round-off excursions of the flux-corrected update (|.| ~ 1e-30) must survive a
-  // get_fields / set_fields round trip; so must the excursions that transport through a
-  // velocity field divergence-free only to the pressure tolerance accumulates over a run
-  // (beyond 1e-9 after tens of mixed-precision steps at 1e-8), so the check allows 1e-6
+  // New input must lie in [0, 1] to 1e-9 (round-off of an earlier computation).  State
+  // this simulation produced itself must survive a get_fields / set_fields round trip:
+  // transport through a velocity field divergence-free only to the pressure tolerance
+  // moves alpha outside [0, 1] by dt |div(A u)| / (phi V) per step, so the range also
+  // admits the extremes its own steps have reached.
   // branch-free inner loop (vectorised by the host compiler), one exit test per chunk;
   // NaN fails both comparisons
+  const double lo = std::min(-1e-9, s->alpha_lo_seen), hi = std::max(1.0 + 1e-9, s->alpha_hi_seen);
   for (long long c0 = 0; c0 < s->P.cells; c0 += 4096) {
     const long long c1 = std::min(s->P.cells, c0 + 4096);
     int ok = 1;
-    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= -1e-6) & (int)(alpha[c] <= 1.0 + 1e-6);
-    if (!ok) return fail(s, MDBS_ERR_ARG, "alpha must lie in [0, 1] (to 1e-6)");
+    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= lo) & (int)(alpha[c] <= hi);
+    if (!ok)
+      return fail(s, MDBS_ERR_ARG,
+                  "alpha must lie in [0, 1] (to 1e-9, or within the extremes this simulation reached)");
   }
   const double* src[3] = {ux, uy, uz};
   CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
@@ -799,16 +844,18 @@ int mdbs_step(mdbs_sim* s, int32_t n) {
   if (s->in_batch) return fail(s, MDBS_ERR_ARG, "the simulation belongs to a batch: step the batch");
   Activate act(s);
   const double it0 = s->host_scal[kSlotItersTotal];
+  const double nc0 = s->host_scal[kSlotNotConverged];
   const bool eager = s->prof.on;
   CK(exec_steps(s->ex, s->opt, s->prof, s->stream, n));
   s->st.steps += n;
-  const int rc = refresh_stats(s);
+  int rc = refresh_stats(s);
   if (plan_failed(s->ex.plan)) return fail(s, MDBS_ERR_CUDA, "a device wait for staged data timed out");
   // kernels launched by the graphs: the fixed part of every step plus the CG bodies run
   if (!eager)
     s->prof.launches += (long long)n * s->ex.static_launches +
                         (long long)(s->host_scal[kSlotItersTotal] - it0) * s->ex.body_launches;
   s->st.kernel_launches = s->prof.launches;
+  if (rc == MDBS_OK) rc = convergence_check(s, nc0);
   return rc;
 }
 
@@ -997,7 +1044,11 @@ int mdbs_batch_step(mdbs_batch* b, int32_t n) {
   const int nd = (int)b->sims.size();
   const bool eager = b->prof.on;
   double it0 = 0.0;
-  for (mdbs_sim* s : b->sims) it0 += s->host_scal[kSlotItersTotal];
+  std::vector<double> nc0(nd);
+  for (int i = 0; i < nd; i++) {
+    it0 += b->sims[i]->host_scal[kSlotItersTotal];
+    nc0[i] = b->sims[i]->host_scal[kSlotNotConverged];
+  }
   cudaError_t e = exec_steps(b->ex, b->opt, b->prof, b->stream, n);
   // gather every member's scalars, then one copy to the host
   for (int i = 0; i < nd && e == cudaSuccess; i++)
@@ -1023,8 +1074,10 @@ int mdbs_batch_step(mdbs_batch* b, int32_t n) {
     for (int k = 0; k < kNumSlots; k++) s->host_scal[k] = h[k];
     s->st.steps += n;
     it1 += h[kSlotItersTotal];
-    const int r = stats_from(s, h);
-    if (r != MDBS_OK && rc == MDBS_OK) {
+    int r = stats_from(s, h);
+    if (r == MDBS_OK) r = convergence_check(s, nc0[i]);
+    // a diverged member outranks one whose solves stopped at max_cg
+    if (r != MDBS_OK && (rc == MDBS_OK || (rc == MDBS_ERR_NOT_CONVERGED && r != MDBS_ERR_NOT_CONVERGED))) {
       rc = r;
       b->err = "domain " + std::to_string(i) + ": " + s->err;
     }

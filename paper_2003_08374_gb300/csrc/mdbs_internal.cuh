@@ -71,6 +71,7 @@ struct Fld {
   const double* k0;
   const uint8_t* is_free;
   const double* nw[3];  // wall normal (zero outside contact cells)
+  const double* iphi2;  // phi^-2 (porosity-gradient part of the convection)
   // state
   double* alpha;
   double* p;
@@ -219,7 +220,7 @@ enum KernelId {
   K_ALPHA_FLUX, K_ALPHA_LO, K_ALPHA_LIMIT, K_ALPHA_UPDATE, K_FINALIZE, K_PROPERTIES, K_NORMALS,
   K_CURVATURE, K_MOM_ASSEMBLE, K_JACOBI, K_HBYA, K_CORRECT, K_BOUNDARY, K_STATS, K_CFL, K_STATIC,
   K_ASSEMBLE, K_DIAG, K_CONVERT, K_COARSEN, K_SMOOTH0, K_SMOOTHC, K_ZERO, K_RESTRICT0, K_RESTRICTC,
-  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_TAIL, K_COUNT
+  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_TAIL, K_COOP, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 void prof_begin(int id, cudaStream_t s);
@@ -281,6 +282,9 @@ struct BatchPlan {
   int any_cfl;                // some domain uses the adaptive time step
   int snake;                  // alternate the traversal direction of consecutive level kernels
   int sweep_kz;               // > 0: fused red-black sweeps (FP32 levels) over chunks of this many planes
+  int coarse_coop;            // levels between the finest and the tail in one cooperative launch
+  int coop_grid;              // CTAs of that launch (all resident)
+  unsigned long long* coop_ctr;  // device: arrival counter of its grid barriers
   StepDom* sd;                // device tables (ndom entries)
   CgDom* cg;
   int* table_storage;         // device memory of every block table
@@ -360,8 +364,11 @@ cudaError_t bounded_wait_selftest(int* status, double* waited_s);
 // smooth_rows: kBlock rows per work item of the finest-level half sweeps (1, 2, 4, 8);
 // sweep_kz: planes per fused-sweep chunk (0: half sweeps); tail_ctas: CTAs per domain
 // in the tail kernel (1, 2, 4, 8: one cluster)
+// coarse_coop: run the levels between the finest and the tail in one cooperative launch
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, int tail_ctas, BatchPlan* out);
+                        int sweep_kz, int tail_ctas, int coarse_coop, BatchPlan* out);
+// CTAs of the cooperative coarse-level kernel that are resident at once on this device
+cudaError_t coop_grid_size(int flexible, long long tail_words, int* grid);
 void plan_destroy(BatchPlan* B);
 
 }  // namespace mdbs

@@ -119,6 +119,10 @@ extern "C" int mdbs_field_stats_static(int64_t cells, double cell_volume, const 
   long long blocks = (cells + kThreads - 1) / kThreads;
   const int nb = (int)(blocks < MDBS_STATIC_STATS_MAX_BLOCKS ? blocks : MDBS_STATIC_STATS_MAX_BLOCKS);
   cudaStream_t s = (cudaStream_t)stream;
+  // An error already pending on this thread belongs to the caller's earlier work: report
+  // it as MDBS_ERR_CUDA without launching and leave it pending (cudaPeekAtLastError does
+  // not clear it).  Otherwise any error after the launches is theirs and is cleared.
+  if (cudaPeekAtLastError() != cudaSuccess) return MDBS_ERR_CUDA;
   k_stats_partials<<<nb, kThreads, 0, s>>>(cells, cell_volume, porosity, alpha, p, scratch, nb);
   k_stats_final<<<1, 32, 0, s>>>(scratch, nb, out);
   return cudaGetLastError() == cudaSuccess ? MDBS_OK : MDBS_ERR_CUDA;

@@ -292,16 +292,27 @@ __global__ void k_coarsen(const CgDom* __restrict__ C, Work w, int l) {
 }
 
 // sum_nb T x_nb at cell c of level L (order x-, x+, y-, y+, z-, z+)
-template <typename R>
-__device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* __restrict__ x, const int q[3],
-                                           long long c) {
+// Load of an iterate or right-hand side.  COH: through L2 (ld.global.cg), for the
+// phases of the cooperative kernel, where other CTAs rewrote the value since this
+// SM may last have read it (L2 is the point of coherence; a load that allocates in
+// L1, or takes the read-only path, could return the old value).
+template <bool COH, typename R>
+__device__ __forceinline__ R ldc(const R* p) {
+  if constexpr (COH)
+    return __ldcg(p);
+  else
+    return *p;
+}
+
+template <typename R, bool COH = false>
+__device__ __forceinline__ R neighbour_sum(const Level<R>& L, const R* x, const int q[3], long long c) {
   R v = R(0);
   for (int d = 0; d < 3; d++) {
     if (q[d] > 0) {
       const unsigned cl = lo_pos(L.n, q, (unsigned)c, d);
-      v += tcoef(L, d, cl) * x[cl];
+      v += tcoef(L, d, cl) * ldc<COH>(x + cl);
     }
-    if (q[d] + 1 < L.n[d]) v += tcoef(L, d, (unsigned)c) * x[hi_pos(L.n, q, (unsigned)c, d)];
+    if (q[d] + 1 < L.n[d]) v += tcoef(L, d, (unsigned)c) * ldc<COH>(x + hi_pos(L.n, q, (unsigned)c, d));
   }
   return v;
 }
@@ -317,23 +328,23 @@ __device__ __forceinline__ float fma_r(float a, float b, float c) { return fmaf(
 // tail share this function, so a cell's value does not depend on which of them
 // updates it.
 // c, cm, cp: storage positions of the cell and of its x neighbours i - 1, i + 1
-template <typename R, typename CT>
+template <typename R, typename CT, bool COH = false>
 __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* __restrict__ dinv,
                                             const R* __restrict__ xr, R* __restrict__ xw, CT Tx, CT Ty, CT Tz,
                                             int n0, int n1, int n2, int i, int j, int k, long long c, long long cm,
                                             long long cp, int zero) {
   if (zero) {
-    xw[c] = bb[c] * dinv[c];
+    xw[c] = ldc<COH>(bb + c) * dinv[c];
     return;
   }
   const long long sy = n0, sz = (long long)n0 * n1;
-  R v = bb[c];
-  if (i > 0) v = fma_r(Tx[cm], xr[cm], v);
-  if (i + 1 < n0) v = fma_r(Tx[c], xr[cp], v);
-  if (j > 0) v = fma_r(Ty[c - sy], xr[c - sy], v);
-  if (j + 1 < n1) v = fma_r(Ty[c], xr[c + sy], v);
-  if (k > 0) v = fma_r(Tz[c - sz], xr[c - sz], v);
-  if (k + 1 < n2) v = fma_r(Tz[c], xr[c + sz], v);
+  R v = ldc<COH>(bb + c);
+  if (i > 0) v = fma_r(Tx[cm], ldc<COH>(xr + cm), v);
+  if (i + 1 < n0) v = fma_r(Tx[c], ldc<COH>(xr + cp), v);
+  if (j > 0) v = fma_r(Ty[c - sy], ldc<COH>(xr + c - sy), v);
+  if (j + 1 < n1) v = fma_r(Ty[c], ldc<COH>(xr + c + sy), v);
+  if (k > 0) v = fma_r(Tz[c - sz], ldc<COH>(xr + c - sz), v);
+  if (k + 1 < n2) v = fma_r(Tz[c], ldc<COH>(xr + c + sz), v);
   xw[c] = v * dinv[c];
 }
 
@@ -343,23 +354,23 @@ __device__ __forceinline__ void smooth_cell(const R* __restrict__ bb, const R* _
 // value the separate prolongation would have stored, rounded the same way.  The
 // cells of the updated colour are overwritten and the other colour is
 // overwritten by the next half sweep, so the corrected values need not be stored.
-template <typename R, typename CT>
+template <typename R, typename CT, bool COH = false>
 __device__ __forceinline__ void smooth_cell_corr(const R* __restrict__ bb, const R* __restrict__ dinv,
                                                  const R* __restrict__ xr, R* __restrict__ xw, CT Tx, CT Ty, CT Tz,
                                                  int n0, int n1, int n2, int i, int j, int k, long long c,
                                                  long long cm, long long cp, const Level<R>& Co) {
   const R* __restrict__ ex = Co.x;
   auto e = [&](int a, int b, int d) -> R {
-    return ex[lpos(Co.n, Co.cz[0] ? a >> 1 : a, Co.cz[1] ? b >> 1 : b, Co.cz[2] ? d >> 1 : d)];
+    return ldc<COH>(ex + lpos(Co.n, Co.cz[0] ? a >> 1 : a, Co.cz[1] ? b >> 1 : b, Co.cz[2] ? d >> 1 : d));
   };
   const long long sy = n0, sz = (long long)n0 * n1;
-  R v = bb[c];
-  if (i > 0) v = fma_r(Tx[cm], xr[cm] + e(i - 1, j, k), v);
-  if (i + 1 < n0) v = fma_r(Tx[c], xr[cp] + e(i + 1, j, k), v);
-  if (j > 0) v = fma_r(Ty[c - sy], xr[c - sy] + e(i, j - 1, k), v);
-  if (j + 1 < n1) v = fma_r(Ty[c], xr[c + sy] + e(i, j + 1, k), v);
-  if (k > 0) v = fma_r(Tz[c - sz], xr[c - sz] + e(i, j, k - 1), v);
-  if (k + 1 < n2) v = fma_r(Tz[c], xr[c + sz] + e(i, j, k + 1), v);
+  R v = ldc<COH>(bb + c);
+  if (i > 0) v = fma_r(Tx[cm], ldc<COH>(xr + cm) + e(i - 1, j, k), v);
+  if (i + 1 < n0) v = fma_r(Tx[c], ldc<COH>(xr + cp) + e(i + 1, j, k), v);
+  if (j > 0) v = fma_r(Ty[c - sy], ldc<COH>(xr + c - sy) + e(i, j - 1, k), v);
+  if (j + 1 < n1) v = fma_r(Ty[c], ldc<COH>(xr + c + sy) + e(i, j + 1, k), v);
+  if (k > 0) v = fma_r(Tz[c - sz], ldc<COH>(xr + c - sz) + e(i, j, k - 1), v);
+  if (k + 1 < n2) v = fma_r(Tz[c], ldc<COH>(xr + c + sz) + e(i, j, k + 1), v);
   xw[c] = v * dinv[c];
 }
 
@@ -368,6 +379,47 @@ __device__ __forceinline__ void smooth_cell_corr(const R* __restrict__ bb, const
 // CG iterations).  The level's arrays go to restrict-qualified registers once per
 // work item so that the REP rows of an item overlap their loads: the colour being
 // written and the colour being read are disjoint cells of the same array.
+// The REP rows of work item lb of a half sweep of colour col over level l of domain G,
+// thread tid of kBlock (shared by the per-level launches and the cooperative kernel).
+template <typename R, int REP, bool PRO, bool COH = false>
+__device__ __forceinline__ void smooth_item_lv(const Level<R>& Lr, const Level<R>& Lc, int lb, unsigned tid, int col,
+                                               int zero) {
+  const int n0 = Lr.n[0], n1 = Lr.n[1], n2 = Lr.n[2];
+  const R* __restrict__ bb = Lr.b;
+  const R* __restrict__ dinv = Lr.dinv;
+  R* __restrict__ x = Lr.x;
+  const unsigned half = (n0 + 1) >> 1;
+  const unsigned total = half * (unsigned)n1 * (unsigned)n2;
+  const FastDiv dh = Lr.dhalf, dn = Lr.dn1;
+  with_coefs(Lr, [&](auto Tx, auto Ty, auto Tz) {
+#pragma unroll
+    for (int r = 0; r < REP; r++) {
+      const unsigned t = ((unsigned)lb * REP + r) * kBlock + tid;
+      if (t >= total) continue;
+      const unsigned row = fastdiv(t, dh);
+      const int ti = (int)(t - row * half);
+      const unsigned kk = fastdiv(row, dn);
+      const int j = (int)(row - kk * (unsigned)n1), k = (int)kk;
+      const int sh = (j + k + col) & 1, i = sh + 2 * ti;
+      if (i >= n0) continue;
+      // x-split positions: this colour's run, and the other colour's run for i -/+ 1
+      const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
+      const unsigned cm = sh ? rb + ti : rb + half + ti - 1, cp = sh ? rb + ti + 1 : rb + half + ti;
+      if constexpr (PRO)
+        smooth_cell_corr<R, decltype(Tx), COH>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, Lc);
+      else
+        smooth_cell<R, decltype(Tx), COH>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
+    }
+  });
+}
+
+// the same for domain G's level l (and l + 1, the coarse level of the prolongation)
+template <typename R, int REP, bool PRO, bool COH = false>
+__device__ __forceinline__ void smooth_item(const CgDom& G, int l, int lb, unsigned tid, int col, int zero) {
+  const Level<R>* L = levels_of<R>(G);
+  smooth_item_lv<R, REP, PRO, COH>(L[l], L[PRO ? l + 1 : l], lb, tid, col, zero);
+}
+
 template <typename R, int REP, bool PRO = false>
 __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
     k_smooth(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
@@ -375,34 +427,7 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
     if (G.scal[kCond] == 0.0) continue;
-    const Level<R>& Lr = levels_of<R>(G)[l];
-    const int n0 = Lr.n[0], n1 = Lr.n[1], n2 = Lr.n[2];
-    const R* __restrict__ bb = Lr.b;
-    const R* __restrict__ dinv = Lr.dinv;
-    R* __restrict__ x = Lr.x;
-    const unsigned half = (n0 + 1) >> 1;
-    const unsigned total = half * (unsigned)n1 * (unsigned)n2;
-    const FastDiv dh = Lr.dhalf, dn = Lr.dn1;
-    with_coefs(Lr, [&](auto Tx, auto Ty, auto Tz) {
-#pragma unroll
-      for (int r = 0; r < REP; r++) {
-        const unsigned t = ((unsigned)lb * REP + r) * blockDim.x + threadIdx.x;
-        if (t >= total) continue;
-        const unsigned row = fastdiv(t, dh);
-        const int ti = (int)(t - row * half);
-        const unsigned kk = fastdiv(row, dn);
-        const int j = (int)(row - kk * (unsigned)n1), k = (int)kk;
-        const int sh = (j + k + col) & 1, i = sh + 2 * ti;
-        if (i >= n0) continue;
-        // x-split positions: this colour's run, and the other colour's run for i -/+ 1
-        const unsigned rb = (unsigned)n0 * row, c = rb + (sh ? half + ti : ti);
-        const unsigned cm = sh ? rb + ti : rb + half + ti - 1, cp = sh ? rb + ti + 1 : rb + half + ti;
-        if constexpr (PRO)
-          smooth_cell_corr<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, levels_of<R>(G)[l + 1]);
-        else
-          smooth_cell<R>(bb, dinv, x, x, Tx, Ty, Tz, n0, n1, n2, i, j, k, c, cm, cp, zero);
-      }
-    });
+    smooth_item<R, REP, PRO>(G, l, lb, threadIdx.x, col, zero);
   }
 }
 
@@ -718,7 +743,7 @@ __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int 
 }
 
 // coarse b = sum of the fine residuals b - A x over the covered fine cells
-template <typename R>
+template <typename R, bool COH = false>
 __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
   decode_pos(Co, ci, Q[0], Q[1], Q[2]);
@@ -733,8 +758,8 @@ __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level
       for (int x = lo[0]; x <= hi[0]; x++) {
         const int q[3] = {x, y, z};
         const long long c = lpos(Fi.n, x, y, z);
-        const R ax = Fi.diag[c] * Fi.x[c] - neighbour_sum(Fi, Fi.x, q, c);
-        s += Fi.b[c] - ax;
+        const R ax = Fi.diag[c] * ldc<COH>(Fi.x + c) - neighbour_sum<R, COH>(Fi, Fi.x, q, c);
+        s += ldc<COH>(Fi.b + c) - ax;
       }
   Co.b[ci] = s;
 }
@@ -755,13 +780,13 @@ __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int
   }
 }
 
-template <typename R>
+template <typename R, bool COH = false>
 __device__ __forceinline__ void b_prolong(const Level<R>& Fi, const Level<R>& Co, long long c) {
   int q[3];
   decode_pos(Fi, c, q[0], q[1], q[2]);
   int Q[3];
   for (int a = 0; a < 3; a++) Q[a] = Co.cz[a] ? q[a] / 2 : q[a];
-  Fi.x[c] += Co.x[lpos(Co.n, Q[0], Q[1], Q[2])];
+  Fi.x[c] = ldc<COH>(Fi.x + c) + ldc<COH>(Co.x + lpos(Co.n, Q[0], Q[1], Q[2]));
 }
 
 template <typename R>
@@ -937,18 +962,14 @@ __device__ void tail_prolong(const Level<R>& Fi, const Level<R>& Co, const TailP
 // smem != 0 (single CTA only) the iterates and right-hand sides of those levels
 // live in shared memory for the whole cycle (the coefficients, read-only here, stay
 // in L1): b of the first tail level is copied in, its x copied out.
+// The tail levels of domain G's V-cycle (called by every thread of the CTA, or of
+// the cluster when tp.size > 1); lv: the CTA's shared copy of the level views.
 template <typename R>
-__global__ void __launch_bounds__(kTailThreads)
-    k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs, int smem, int ctas) {
-  MDBS_DEPENDENT_ENTRY();
-  extern __shared__ __align__(16) unsigned char tail_smem_raw[];
-  const CgDom& G = CG[blockIdx.x / ctas];
-  if (G.scal[kCond] == 0.0) return;  // the same for the whole cluster
-  const int rank = blockIdx.x % ctas;
-  const TailPart tp{(unsigned)(rank * blockDim.x + threadIdx.x), (unsigned)(ctas * blockDim.x), ctas};
+__device__ void tail_body(const CgDom& G, int nu1, int nu2, int cs, int smem, const TailPart& tp, Level<R>* lv,
+                          unsigned char* tail_smem_raw) {
   const Level<R>* gl = levels_of<R>(G);
   const int first = G.first, nlev = G.nlev;
-  __shared__ Level<R> lv[kMaxLevels];  // one copy of the level views per block
+  __syncthreads();  // lv may still be read by the previous domain's last phase
   if (threadIdx.x == 0) {
     R* p = reinterpret_cast<R*>(tail_smem_raw);
     for (int l = first; l < nlev; l++) {
@@ -992,8 +1013,215 @@ __global__ void __launch_bounds__(kTailThreads)
     for (unsigned c = threadIdx.x; c < (unsigned)lv[first].cells; c += blockDim.x) gl[first].x[c] = lv[first].x[c];
 }
 
+template <typename R>
+__global__ void __launch_bounds__(kTailThreads)
+    k_tail_vcycle(const CgDom* __restrict__ CG, int nu1, int nu2, int cs, int smem, int ctas) {
+  MDBS_DEPENDENT_ENTRY();
+  extern __shared__ __align__(16) unsigned char tail_smem_raw[];
+  const CgDom& G = CG[blockIdx.x / ctas];
+  if (G.scal[kCond] == 0.0) return;  // the same for the whole cluster
+  const int rank = blockIdx.x % ctas;
+  const TailPart tp{(unsigned)(rank * blockDim.x + threadIdx.x), (unsigned)(ctas * blockDim.x), ctas};
+  __shared__ Level<R> lv[kMaxLevels];  // one copy of the level views per block
+  tail_body<R>(G, nu1, nu2, cs, smem, tp, lv, tail_smem_raw);
+}
+
 // largest shared-memory footprint the tail takes (beyond it, it works in global memory)
 constexpr size_t kTailSmemMax = 200 * 1024;
+
+// ------------------------------------------------------------------ coarse levels in one cooperative launch
+// The levels between the finest one and the tail, which per-level launches would
+// run as about twenty small kernels per V-cycle (each a few microseconds of launch
+// and ramp latency for a few MB that sit in L2), in ONE cooperative launch: every
+// CTA is resident, and a grid-wide barrier separates the phases (half sweeps,
+// restriction) that kernel boundaries separate otherwise.  Each phase walks the
+// same work tables as the per-level launches (virtual blocks of kBlock threads)
+// with the same per-cell arithmetic, so every value is bitwise the same.  Between
+// the descending and the ascending levels each domain's tail runs in one CTA
+// (domain d in CTA d mod grid), with block barriers.
+constexpr int kCoopThreads = 1024;
+constexpr int kCoopVB = kCoopThreads / kBlock;  // virtual blocks of kBlock threads per CTA
+
+__device__ __forceinline__ unsigned long long ld_acquire_u64(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];\n" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Grid-wide barrier on a monotonic arrival counter: the k-th barrier of a launch of G
+// CTAs completes when the counter reaches (k + 1) G (counted across launches, so
+// nothing needs resetting between graph replays).  Thread 0 of each CTA arrives after
+// a block barrier and a gpu-scope fence (the CTA's writes become visible), spins
+// with acquire loads, and fences again.  The wait is bounded: after kWaitLimitNs, or
+// once another CTA has given up, it sets *err and returns false, and the caller
+// returns (the step then reports MDBS_ERR_CUDA).
+__device__ __forceinline__ bool coop_sync(unsigned long long* ctr, int* err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 0;
+    if (*(volatile int*)err == 0) {
+      ok = 1;
+      __threadfence();
+      const unsigned long long g = gridDim.x;
+      const unsigned long long target = (atomicAdd(ctr, 1ull) / g + 1) * g;
+      if (ld_acquire_u64(ctr) < target) {
+        const unsigned long long t0 = global_ns();
+        unsigned spins = 0;
+        while (ld_acquire_u64(ctr) < target) {
+          if ((++spins & 255u) == 0) {
+            if (*(volatile int*)err != 0) {
+              ok = 0;
+              break;
+            }
+            if (global_ns() - t0 > kWaitLimitNs) {
+              atomicExch(err, 1);
+              ok = 0;
+              break;
+            }
+          }
+        }
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// work tables of the levels the cooperative kernel runs (first .. last - 1)
+struct CoopWork {
+  Work half[kMaxLevels];    // red / black half cells
+  Work coarse[kMaxLevels];  // cells of level l + 1 (restriction)
+  Work fine[kMaxLevels];    // cells of level l (zero guess without pre-smoothing, prolongation without post-smoothing)
+  int first, last, ndom;
+};
+
+// domains whose level views and convergence flag the cooperative kernel keeps in
+// shared memory for the whole launch (batches of more domains read them from global
+// memory in every phase)
+constexpr int kCoopCacheDoms = 4;
+
+template <typename R>
+__global__ void __launch_bounds__(kCoopThreads, 1)
+    k_coarse_coop(const CgDom* __restrict__ C, CoopWork cw, int nu1, int nu2, int cs, int tail_smem,
+                  unsigned long long* ctr, int* err) {
+  extern __shared__ __align__(16) unsigned char tail_smem_raw[];
+  __shared__ Level<R> lv[kMaxLevels];
+  // Every grid barrier ends in an acquire that invalidates L1, so the per-domain data a
+  // phase starts from (level views, convergence flag, block tables) would come from L2
+  // again in every phase, a chain of dependent round trips; small batches keep them in
+  // shared memory instead (they do not change during the launch).
+  __shared__ Level<R> cl[kCoopCacheDoms][kMaxLevels];
+  __shared__ int cact[kCoopCacheDoms];
+  __shared__ int cblk[2][kMaxLevels][kCoopCacheDoms + 1];  // block tables of cw.half / cw.coarse
+  const bool cached = cw.ndom <= kCoopCacheDoms;
+  if (cached) {
+    for (int t = threadIdx.x; t < cw.ndom * kMaxLevels; t += blockDim.x) {
+      const int d = t / kMaxLevels, l = t % kMaxLevels;
+      if (l < C[d].nlev) cl[d][l] = levels_of<R>(C[d])[l];
+    }
+    for (int d = threadIdx.x; d < cw.ndom; d += blockDim.x) cact[d] = C[d].scal[kCond] != 0.0;
+    for (int t = threadIdx.x; t < 2 * kMaxLevels * (cw.ndom + 1); t += blockDim.x) {
+      const int which = t / (kMaxLevels * (cw.ndom + 1)), r = t % (kMaxLevels * (cw.ndom + 1));
+      const int l = r / (cw.ndom + 1), d = r % (cw.ndom + 1);
+      const Work& w = which ? cw.coarse[l] : cw.half[l];
+      cblk[which][l][d] = (l >= cw.first && l < cw.last) ? w.blk[d] : 0;
+    }
+    __syncthreads();
+  }
+  // virtual blocks dealt round-robin over the CTAs first, so that the few items of a
+  // small level spread over many SMs (GB300's FP64 rate per SM is low)
+  const unsigned vb0 = blockIdx.x + gridDim.x * (threadIdx.x / kBlock), vstep = gridDim.x * kCoopVB;
+  const unsigned tid = threadIdx.x % kBlock;
+  // domain and local item of flat item b of a level's table (which: 0 half, 1 coarse)
+  auto locate = [&](const Work& w, int which, int l, unsigned b, int& dm, int& lb) -> bool {
+    if (cached) {
+      int d = 0;
+      while (d + 1 < cw.ndom && cblk[which][l][d + 1] <= (int)b) d++;
+      dm = d;
+      lb = (int)b - cblk[which][l][d];
+      return cact[d] != 0;
+    }
+    dm = work_domain(w, (int)b);
+    lb = (int)b - w.blk[dm];
+    return C[dm].scal[kCond] != 0.0;
+  };
+  auto level = [&](int dm, int l) -> const Level<R>& { return cached ? cl[dm][l] : levels_of<R>(C[dm])[l]; };
+  // every phase walks the items of one level of every domain that has it
+  auto half = [&](int l, int col, int zero, bool pro) {
+    const Work& w = cw.half[l];
+    for (unsigned b = vb0; b < (unsigned)w.total; b += vstep) {
+      int dm, lb;
+      if (!locate(w, 0, l, b, dm, lb)) continue;
+      if (pro)
+        smooth_item_lv<R, 1, true, true>(level(dm, l), level(dm, l + 1), lb, tid, col, 0);
+      else
+        smooth_item_lv<R, 1, false, true>(level(dm, l), level(dm, l), lb, tid, col, zero);
+    }
+  };
+  auto cells = [&](const Work& w, int l, int what) {  // 0 restrict, 1 zero, 2 prolong
+    for (unsigned b = vb0; b < (unsigned)w.total; b += vstep) {
+      int dm, lb;
+      if (what == 0) {
+        if (!locate(w, 1, l, b, dm, lb)) continue;
+      } else {
+        dm = work_domain(w, (int)b);
+        lb = (int)b - w.blk[dm];
+        if (C[dm].scal[kCond] == 0.0) continue;
+      }
+      const Level<R>& Lf = level(dm, l);
+      const Level<R>& Lc = level(dm, l + 1);
+      for (int r = 0; r < w.rep; r++) {
+        const long long c = ((long long)lb * w.rep + r) * kBlock + tid;
+        if (what == 0) {
+          if (c < Lc.cells) b_resid_restrict<R, true>(Lf, Lc, c);
+        } else if (c < Lf.cells) {
+          if (what == 1)
+            Lf.x[c] = R(0);
+          else
+            b_prolong<R, true>(Lf, Lc, c);
+        }
+      }
+    }
+  };
+  for (int l = cw.first; l < cw.last; l++) {
+    if (nu1 == 0) {
+      cells(cw.fine[l], l, 1);
+      if (!coop_sync(ctr, err)) return;
+    }
+    for (int it = 0; it < nu1; it++) {
+      half(l, 0, it == 0, false);
+      if (!coop_sync(ctr, err)) return;
+      half(l, 1, 0, false);
+      if (!coop_sync(ctr, err)) return;
+    }
+    cells(cw.coarse[l], l, 0);
+    if (!coop_sync(ctr, err)) return;
+  }
+  for (int d = blockIdx.x; d < cw.ndom; d += gridDim.x) {
+    const CgDom& G = C[d];
+    if (G.scal[kCond] == 0.0) continue;  // uniform over the CTA
+    tail_body<R>(G, nu1, nu2, cs, tail_smem, TailPart{threadIdx.x, blockDim.x, 1}, lv, tail_smem_raw);
+  }
+  if (!coop_sync(ctr, err)) return;
+  for (int l = cw.last - 1; l >= cw.first; l--) {
+    const bool last_level = l == cw.first;
+    if (nu2 == 0) {
+      cells(cw.fine[l], l, 2);
+      if (!last_level && !coop_sync(ctr, err)) return;
+      continue;
+    }
+    // the first post-smoothing half sweep applies the prolongation (as the per-level path)
+    for (int it = 0; it < nu2; it++) {
+      half(l, 1, 0, it == 0);
+      if (!coop_sync(ctr, err)) return;
+      half(l, 0, 0, false);
+      if (!(last_level && it == nu2 - 1) && !coop_sync(ctr, err)) return;
+    }
+  }
+}
 
 // ------------------------------------------------------------------ CG kernels (FP64)
 // (A p) at the cell q stored at position c; p is in natural order
@@ -1309,6 +1537,31 @@ cudaError_t sweep_kernel_setup() {
     e = cudaFuncSetAttribute(k_tail_vcycle<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_tail_vcycle<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_coop<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_coarse_coop<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTailSmemMax);
+  return e;
+}
+
+// dynamic shared memory of the tail (and of the cooperative kernel, which runs it):
+// the tail levels' x and b when one CTA per domain runs them and they fit
+static size_t tail_smem_bytes(const BatchPlan& B, size_t word, int ctas) {
+  const size_t bytes = (size_t)B.tail_words * word;
+  return ctas == 1 && bytes <= kTailSmemMax ? bytes : 0;
+}
+
+cudaError_t coop_grid_size(int flexible, long long tail_words, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const size_t word = flexible ? sizeof(float) : sizeof(double);
+  const size_t bytes = (size_t)tail_words * word;
+  const size_t smem = bytes <= kTailSmemMax ? bytes : 0;
+  if (e == cudaSuccess)
+    e = flexible ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_coop<float>, kCoopThreads, smem)
+                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_coarse_coop<double>, kCoopThreads, smem);
+  *grid = e == cudaSuccess ? sms * per_sm : 0;
   return e;
 }
 
@@ -1643,17 +1896,45 @@ template <typename R>
 static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaStream_t s) {
   const int S = nu1 + nu2;
   auto cur = [&](int sw) { return fused_sweeps<R>(B) ? (S - sw) & 1 : 0; };
-  for (int l = 0; l < B.max_first; l++) {
+  // the levels between the finest and the tail in one cooperative launch (split sweeps)
+  const bool coop = B.coarse_coop && B.max_first >= 2 && !fused_sweeps<R>(B) && B.coop_grid > 0;
+  const int batched_end = coop ? 1 : B.max_first;
+  for (int l = 0; l < batched_end; l++) {
     if (nu1 == 0)
       MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l, D.next(l), cur(0));
     for (int it = 0; it < nu1; it++) sweep<R>(B, l, 0, it == 0, cur(it), D, s);
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
                 B.lcoarse[l], l, D.next(l), cur(nu1));
   }
+  if (coop) {
+    const size_t smem = tail_smem_bytes(B, sizeof(R), 1);
+    CoopWork cw;
+    for (int l = 0; l < kMaxLevels; l++) {
+      cw.half[l] = B.lhalf[l];
+      cw.coarse[l] = B.lcoarse[l];
+      cw.fine[l] = B.lfine[l];
+    }
+    cw.first = 1;
+    cw.last = B.max_first;
+    cw.ndom = B.ndom;
+    prof_begin(K_COOP, s);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(B.coop_grid);
+    cfg.blockDim = dim3(kCoopThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeCooperative;  // every CTA resident: the grid barriers are safe
+    at[0].val.cooperative = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_coarse_coop<R>, B.cg, cw, nu1, nu2, cs, smem > 0 ? 1 : 0, B.coop_ctr, B.err_flag);
+    prof_end(K_COOP, s);
+  }
   const int ctas = B.tail_ctas;
   const size_t tail_bytes = (size_t)B.tail_words * sizeof(R);
   const int tail_smem = ctas == 1 && tail_bytes <= kTailSmemMax ? 1 : 0;
-  {
+  if (!coop) {
     prof_begin(K_TAIL, s);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(B.ndom * ctas);
@@ -1672,7 +1953,7 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     cudaLaunchKernelEx(&cfg, k_tail_vcycle<R>, B.cg, nu1, nu2, cs, tail_smem, ctas);
     prof_end(K_TAIL, s);
   }
-  for (int l = B.max_first - 1; l >= 0; l--) {
+  for (int l = batched_end - 1; l >= 0; l--) {
     if (!fused_sweeps<R>(B) && nu2 > 0) {
       // split sweeps: the first post-smoothing half sweep applies the prolongation
       smooth_half_t<R, true>(B, l, 1, 0, D, s);

@@ -50,6 +50,7 @@ class Server:
         self.rebuilds = 0
         self.cell_steps = 0
         self.peak_active = 0
+        self.not_converged_rounds = 0
 
     def _free_bytes(self):
         if self.free_bytes_fn is not None:
@@ -102,13 +103,17 @@ class Server:
             try:
                 batch.step(k)
             except mdbs.MdbsError as e:
-                if e.code != mdbs.ERR_DIVERGED:
+                if e.code == mdbs.ERR_NOT_CONVERGED:
+                    # the round's steps were taken; a solve stopped at max_cg (counted)
+                    self.not_converged_rounds += 1
+                elif e.code != mdbs.ERR_DIVERGED:
                     raise
-                # retire the members whose fields went non-finite; the others are unaffected
-                for a in active:
-                    st = a[1].stats()
-                    if not (np.isfinite(st["mass"]) and np.isfinite(st["alpha_min"])):
-                        failed.append(a)
+                else:
+                    # retire the members whose fields went non-finite; the others are unaffected
+                    for a in active:
+                        st = a[1].stats()
+                        if not (np.isfinite(st["mass"]) and np.isfinite(st["alpha_min"])):
+                            failed.append(a)
             self.rounds += 1
             self.cell_steps += k * sum(a[0].case.cells for a in active if a not in failed)
             done = []
@@ -159,6 +164,7 @@ def summarize(requests, wall, server):
         "rounds": server.rounds,
         "batch_rebuilds": server.rebuilds,
         "peak_active": server.peak_active,
+        "rounds_with_unconverged_solves": server.not_converged_rounds,
     }
 
 

@@ -106,9 +106,9 @@ def test_appendix_b_density_matches_oracle():
     on the ragged fractured block (porous, free and mixed faces, gravity) and on the
     wave tank's porous barrier."""
     from paper_2003_08374_gb300 import workloads as W
-    # (20, 18, 16) as in the ragged test; on (21, 18, 11) the 2-cell fracture has corners of
-    # curvature ~5e4 1/m whose CSF force amplifies rounding: u differs by 1e-8 after 7 steps
-    # under either density, with alpha and p still equal to 1e-11
+    # (20, 18, 16) as in the ragged test: the (21, 18, 11) block amplifies one-ulp differences
+    # to 1e-8 in u within 7 steps in the oracle itself (the test of the fracture corner case
+    # bounds the CUDA path by that spread)
     case = W.grf_3d(shape=(20, 18, 16), seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500,
                     porous_density=W.RHO_SATURATION)
     g, o = run_both(case, 10)
@@ -148,6 +148,111 @@ def test_mixed_precision_matches_fp64_oracle(precision):
                     precision=precision)
     g, o = run_both(case, 10)
     check_fields(g, o, TOLMIX)
+
+
+def _developed_block(steps=20):
+    """The fractured 3-D block of the mixed-precision tests, advanced by the oracle (at 1e-15)
+    from its initial state: the state a benchmark step starts from (warm pressure)."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(24, 20, 16), seed=5, corr_len=4.0, frac_w=4, p_tol=1e-15, max_cg=500)
+    o = OracleSim(case)
+    o.step(steps)
+    return case, o
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_step_at_bench_tolerance_against_fp64_oracle(precision):
+    """One step at the benchmark's pressure residual 1e-8 -- FP64, the FP32 V-cycle, and BF16
+    coarse coefficients -- from a developed state, against the FP64 oracle's step solved to
+    1e-15: within 1e-6 relative L2 on alpha, p and u.  The errors are printed (pytest -s)."""
+    from paper_2003_08374_gb300 import mdbs
+    case, o = _developed_block()
+    f = o.fields()
+    g = mdbs.Simulation(case.replace(p_tol=1e-8, precision=precision))
+    g.set_fields(f["alpha"], f["ux"], f["uy"], f["uz"], f["p"])
+    g.step(1)
+    o.step(1)
+    errs = check_fields(g, o, TOLMIX)
+    print("one step, precision %d at p_tol 1e-8 vs oracle at 1e-15: %s" % (
+        precision, {k: "%.2e" % v for k, v in errs.items()}))
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_run_at_bench_tolerance_drifts_only_as_the_tolerance_allows(precision):
+    """Over 100 steps at a pressure residual of 1e-8 the solution drifts from the one solved to
+    1e-15 (the oracle against itself: alpha 2.4e-6, p 5.1e-6, u 2.0e-3 relative L2 on this
+    block), because every corrected flux keeps a divergence of the size of the residual.  The
+    CUDA path in every precision drifts no further than three times the oracle's own drift at
+    that tolerance: the precision of the preconditioner adds no error of its own."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(24, 20, 16), seed=5, corr_len=4.0, frac_w=4, p_tol=1e-15, max_cg=500)
+    o15, o8 = OracleSim(case), OracleSim(case.replace(p_tol=1e-8))
+    g = mdbs.Simulation(case.replace(p_tol=1e-8, precision=precision))
+    for x in (o15, o8, g):
+        x.step(100)
+    f15, f8, fg = o15.fields(), o8.fields(), g.fields()
+    report = {}
+    for n in ("alpha", "p", "u"):
+        if n == "u":
+            a, b, c = (np.concatenate([f["ux"], f["uy"], f["uz"]]) for f in (fg, f8, f15))
+        else:
+            a, b, c = fg[n], f8[n], f15[n]
+        drift, err = rel(b, c), rel(a, c)
+        report[n] = "gpu %.2e / oracle %.2e" % (err, drift)
+        assert err <= 3.0 * drift + 1e-9, (n, err, drift)
+    print("100 steps, precision %d at p_tol 1e-8 vs oracle at 1e-15: %s" % (precision, report))
+
+
+def test_grf_3d_100_steps():
+    """A 3-D fractured block (gravity, water into oil, porous and free cells, ragged multigrid
+    levels) over 100 steps, FP64, within 1e-9 of the oracle.  Surface tension is off here:
+    with it, the case amplifies rounding itself (the next test)."""
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(20, 18, 16), seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500, sigma=0.0)
+    g, o = run_both(case, 100)
+    check_fields(g, o, TOL64)
+
+
+def _within_rounding_sensitivity(case, checkpoints, factor=3.0):
+    """The CUDA path against the oracle, bounded by the oracle's own spread: the oracle
+    started from velocities perturbed by one rounding unit.  Returns the largest error."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    pert = case.replace()
+    pert.ux = case.ux * (1.0 + 2.2e-16)
+    o, o2, g = OracleSim(case), OracleSim(pert), mdbs.Simulation(case)
+    done, worst = 0, 0.0
+    for step in checkpoints:
+        for x in (o, o2, g):
+            x.step(step - done)
+        done = step
+        fo, fo2, fg = o.fields(), o2.fields(), g.fields()
+        for n in ("alpha", "p", "ux", "uy", "uz"):
+            spread = rel(fo2[n], fo[n])
+            err = rel(fg[n], fo[n])
+            worst = max(worst, err)
+            assert err <= factor * spread + 1e-12, (step, n, err, spread)
+    return worst
+
+
+def test_fracture_corner_case_within_the_oracles_own_rounding_sensitivity():
+    """With surface tension the step amplifies rounding: the interface normal
+    m = grad(a) / (|grad(a)| + 1e-8/h) changes by 5e7 times a one-ulp change of alpha in
+    nearly uniform cells, and the curvature of the next interface cell, and its CSF force,
+    follow.  The oracle started from velocities perturbed by one rounding unit departs from
+    itself by about 1e-9 after two steps and 8e-9 after seven on the (21, 18, 11) block with
+    a 2-cell fracture, and by 1.4e-9 after 100 steps on the (20, 18, 16) block.  The CUDA
+    path must stay as close to the oracle as that: within three times the oracle's own
+    spread at every checkpoint."""
+    from paper_2003_08374_gb300 import workloads as W
+    worst = _within_rounding_sensitivity(
+        W.grf_3d(shape=(21, 18, 11), seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500), range(1, 8))
+    assert worst > 1e-10  # the case is as sensitive as stated: this is not a trivially equal run
+    _within_rounding_sensitivity(
+        W.grf_3d(shape=(20, 18, 16), seed=7, corr_len=3.0, frac_w=2, p_tol=1e-15, max_cg=500), (25, 50, 75, 100))
 
 
 def test_deterministic_rerun():

@@ -7,14 +7,22 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
+def _sch(rows, tail, snake, kz, ctas, coop):
+    return {"smooth_rows": rows, "tail_cells": tail, "snake": snake, "sweep_kz": kz, "tail_ctas": ctas,
+            "coarse_coop": coop}
+
+
 SCHEDULES = [
-    {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0, "tail_ctas": 1},    # default
-    {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 1},    # fused sweeps
-    {"smooth_rows": 2, "tail_cells": 0, "snake": 1, "sweep_kz": 0, "tail_ctas": 2},       # coarsest only, 2 CTAs
-    {"smooth_rows": 4, "tail_cells": 512, "snake": 0, "sweep_kz": 4, "tail_ctas": 4},     # 37 planes: ragged chunks
-    {"smooth_rows": 8, "tail_cells": 0, "snake": 1, "sweep_kz": 32, "tail_ctas": 1},      # fused down to 4x3x3
-    {"smooth_rows": 8, "tail_cells": 32768, "snake": 1, "sweep_kz": 16, "tail_ctas": 1},  # all but level 0, one CTA
-    {"smooth_rows": 1, "tail_cells": 262144, "snake": 0, "sweep_kz": 0, "tail_ctas": 8},  # all but level 0, cluster
+    _sch(1, 4096, 0, 0, 1, 0),     # default
+    _sch(1, 4096, 0, 0, 1, 1),     # levels 1-2 and the tail in one cooperative launch
+    _sch(8, 4096, 1, 8, 1, 0),     # fused sweeps
+    _sch(2, 0, 1, 0, 2, 0),        # coarsest only in the tail, 2 CTAs
+    _sch(2, 0, 1, 0, 1, 1),        # cooperative down to the coarsest level
+    _sch(4, 512, 0, 4, 4, 0),      # 37 planes: ragged chunks
+    _sch(8, 0, 1, 32, 1, 0),       # fused down to 4x3x3
+    _sch(8, 32768, 1, 16, 1, 0),   # all but level 0, one CTA
+    _sch(1, 262144, 0, 0, 8, 0),   # all but level 0, cluster
+    _sch(1, 262144, 0, 0, 1, 1),   # all but level 0: nothing for the cooperative launch (no effect)
 ]
 
 
@@ -64,7 +72,8 @@ def test_invalid_schedules_are_rejected():
                 {"smooth_rows": 8, "tail_cells": 4096, "snake": 2, "sweep_kz": 8},
                 {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 6},
                 {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 3},
-                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 16}):
+                {"smooth_rows": 8, "tail_cells": 4096, "snake": 1, "sweep_kz": 8, "tail_ctas": 16},
+                _sch(1, 4096, 0, 0, 1, 2)):
         with pytest.raises(mdbs.MdbsError) as e:
             s.set_tuning(bad)
         assert e.value.code == mdbs.ERR_ARG
@@ -114,7 +123,7 @@ def test_batch_schedule_and_autotune_keep_members_identical():
         s.close()
     sims = [mdbs.Simulation(c) for c in cases]
     b = mdbs.Batch(sims)
-    b.set_tuning({"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": 0, "tail_ctas": 1})
+    b.set_tuning(_sch(1, 0, 0, 0, 1, 1))
     b.step(1)
     chosen, trials = b.autotune(trial_steps=1)
     assert chosen == b.tuning() and len(trials) >= 5
@@ -135,9 +144,9 @@ def test_fused_sweeps_with_tma_staging_are_bitwise_equal(precision):
     from paper_2003_08374_gb300 import workloads as W
     case = W.grf_3d(shape=(120, 52, 20), seed=9, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300,
                     precision=precision)
-    ref_f, ref_s = _run(case, {"smooth_rows": 1, "tail_cells": 4096, "snake": 0, "sweep_kz": 0, "tail_ctas": 1})
+    ref_f, ref_s = _run(case, _sch(1, 4096, 0, 0, 1, 0))
     for kz in (4, 8, 32):
-        f, st = _run(case, {"smooth_rows": 1, "tail_cells": 0, "snake": 0, "sweep_kz": kz, "tail_ctas": 1})
+        f, st = _run(case, _sch(1, 0, 0, kz, 1, 0))
         for k in ref_f:
             assert np.array_equal(ref_f[k], f[k]), (kz, k)
         assert st["cg_iters"] == ref_s["cg_iters"]
