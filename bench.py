@@ -57,8 +57,13 @@ def parse():
     ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-objects")
+    ap.add_argument("--extra-domains", type=int, default=64, help="batched sub-object: domains")
+    ap.add_argument("--extra-duration", type=float, default=3.0, help="serving sub-object: arrival window [s]")
+    ap.add_argument("--extra-max-side", type=int, default=64, help="serving sub-object: largest cube side")
+    ap.add_argument("--extra-req-steps", type=int, default=50, help="serving sub-object: steps per request")
     ap.add_argument("--schedule", default=None,
-                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1")
+                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1,coop=1")
     return ap.parse_args()
 
 
@@ -228,20 +233,41 @@ def measured_traffic(kernel, precision_tag, cells):
 FP64_PEAK_TFLOPS = 152 * 4 * 2.07e9 / 1e12  # SMs x FP64 flop/clk/SM x max SM clock (GB300: 1.26)
 
 
-def roofline(prof, cells, word, fp64):
-    """Roofline of the finest-level red-black half sweep.  Per V-cycle the finest level runs
-    8 half sweeps (nu1 = nu2 = 2); the first post-smoothing one also applies the prolongation
-    and is timed with it, so `smooth_fine` holds 7: 1 from a zero guess (b, 1/diag, x written on
-    half the cells: 3 words per updated cell) and 6 full ones (b, 1/diag, x written and the other
-    colour's x read on half the cells, the three face-coefficient arrays in full: 5 words per
-    cell).  Flops per updated cell: 6 fused multiply-adds and one multiply (13), 1 for the
-    zero-guess sweep."""
+def level_sizes(n):
+    """Multigrid hierarchy: every axis longer than 4 cells is halved (rounding up)."""
+    out = [tuple(n)]
+    while True:
+        c = tuple((a + 1) // 2 if a > 4 else a for a in out[-1])
+        if c == out[-1]:
+            return out
+        out.append(c)
+
+
+def fused_sweeps(tuning, word):
+    return bool(tuning) and tuning.get("sweep_kz", 0) > 0 and word == 4
+
+
+def roofline(prof, cells, word, fp64, tuning=None, nu=(2, 2)):
+    """Roofline of the finest-level red-black sweeps.  Split schedule: per V-cycle the finest
+    level runs 2 (nu1 + nu2) half sweeps; the first post-smoothing one also applies the
+    prolongation and is timed with it, so `smooth_fine` holds the others: 1 from a zero guess
+    (b, 1/diag, x written on half the cells: 1.5 words per cell) and the rest full (b, 1/diag,
+    x written and the other colour's x read on half the cells, the three face-coefficient
+    arrays in full: 5 words per cell).  Flops per updated cell: 6 fused multiply-adds and one
+    multiply (13), 1 for the zero-guess sweep.  Fused schedule (FP32 levels, sweep_kz > 0):
+    each launch is a sweep pair reading b, 1/diag, T x3 and x_in and writing x_out, 7 words
+    per cell, 13 flops per cell and colour."""
     if DOMINANT not in prof:
         return None
     tot_ms, cnt = prof[DOMINANT]
     avg_s = tot_ms / cnt / 1e3
-    alg_bytes = (6 * 5 * word + 1 * 1.5 * word) / 7 * cells
-    flops = (6 * 13 + 1 * 1) / 7 * cells / 2
+    halves = 2 * (nu[0] + nu[1])
+    if fused_sweeps(tuning, word):
+        alg_bytes = 7 * word * cells
+        flops = 13.0 * cells
+    else:
+        alg_bytes = ((halves - 2) * 5 * word + 1.5 * word) / (halves - 1) * cells
+        flops = ((halves - 2) * 13 + 1) / (halves - 1) * cells / 2
     pk = peaks()
     hbm_peak = pk["hbm_gbs"] if pk else 6800.0
     gbs = alg_bytes / avg_s / 1e9
@@ -262,8 +288,145 @@ def roofline(prof, cells, word, fp64):
                           "frac": tfl / FP64_PEAK_TFLOPS}
     out.update({"kernel": DOMINANT + ("_fp64" if fp64 else "_fp32"), "launches": cnt, "avg_us": avg_s * 1e6,
                 "alg_bytes_per_launch": alg_bytes, "flops_per_launch": flops,
+                # traffic is the ncu DRAM figure of one full half sweep: compare it with this
+                "alg_bytes_full_sweep": (7 if fused_sweeps(tuning, word) else 5) * word * cells,
                 "timing": "CUDA events around every kernel launch in an eager pass of the same K steps"})
     return out
+
+
+VCYCLE_KERNELS = ("smooth_fine", "smooth_coarse", "restrict_fine", "restrict_coarse", "prolong_fine",
+                  "prolong_coarse", "tail_vcycle", "coarse_coop", "zero")
+
+
+def vcycle_bytes(n, word, tuning, nu=(2, 2), bf16_coarse=False):
+    """Algorithmic HBM bytes of one V-cycle, level by level (each array read or written once
+    per sweep; neighbours from cache).  Per level of N cells with word w (coefficients wt):
+    split half sweeps -- one from a zero guess 1.5w, full ones 2w + 3wt, the first
+    post-smoothing one also reads the coarse correction (+ w/8); fused pairs 4w + 3wt plus a
+    separate prolongation 2w + w/8; the residual restriction 3w + 3wt + w/8.  The coarsest
+    level's exact solve reads its dense inverse (N^2 words)."""
+    levels = level_sizes(n)
+    out = []
+    for l, sz in enumerate(levels):
+        N = sz[0] * sz[1] * sz[2]
+        w = word
+        wt = 2 if (bf16_coarse and l >= 1) else w
+        if l == len(levels) - 1:
+            out.append((N, (N * N + 2 * N) * w))
+            continue
+        halves = 2 * (nu[0] + nu[1])
+        if fused_sweeps(tuning, word) and N > tuning.get("tail_cells", 0):
+            b = (nu[0] + nu[1]) * (4 * w + 3 * wt) + 2 * w + w / 8
+        else:
+            b = 1.5 * w + (halves - 2) * (2 * w + 3 * wt) + (2 * w + 3 * wt + w / 8)
+        b += 3 * w + 3 * wt + w / 8
+        out.append((N, b * N))
+    return out
+
+
+def vcycle_roofline(prof, n, word, tuning, graph_ms, nu=(2, 2), bf16_coarse=False):
+    """HBM roofline of the whole preconditioner: algorithmic bytes of every V-cycle run in
+    the eager pass over the summed CUDA-event time of the V-cycle kernels, and the same with
+    those kernels' time scaled by graph step time / eager kernel time (the share of the
+    captured step they take)."""
+    if not prof or "smooth_fine" not in prof:
+        return None
+    levels = vcycle_bytes(n, word, tuning, nu, bf16_coarse)
+    per_cycle = sum(b for _, b in levels)
+    halves = 2 * (nu[0] + nu[1])
+    per_cycle_launches = (nu[0] + nu[1]) if fused_sweeps(tuning, word) else halves - 1
+    cycles = prof["smooth_fine"][1] / per_cycle_launches
+    vc_ms = sum(prof[k][0] for k in VCYCLE_KERNELS if k in prof)
+    all_ms = sum(v[0] for v in prof.values())
+    pk = peaks()
+    peak = pk["hbm_gbs"] if pk else 6800.0
+    gbs = per_cycle * cycles / (vc_ms / 1e3) / 1e9
+    scaled_ms = vc_ms * graph_ms / all_ms
+    gbs_g = per_cycle * cycles / (scaled_ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+            "graph_scaled": {"achieved": gbs_g, "frac": gbs_g / peak, "vcycle_ms": scaled_ms,
+                             "share_of_step": vc_ms / all_ms},
+            "alg_bytes_per_vcycle": per_cycle, "vcycles": cycles, "kernel_ms": vc_ms,
+            "levels": [{"cells": c, "alg_bytes": b} for c, b in levels],
+            "kernels": [k for k in VCYCLE_KERNELS if k in prof],
+            "timing": "sum of CUDA-event kernel times in the eager pass; graph_scaled multiplies them by "
+                      "graph step time / eager kernel time"}
+
+
+def error_vs_oracle(case, precisions):
+    """Error of one benchmark step (pressure residual case.p_tol) against the FP64 oracle's
+    step solved to 1e-15, on the bounded slab of the workload: relative L2 of alpha, p, u."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    sample = slab_of(case)
+    t0 = time.perf_counter()
+    o = OracleSim(sample.replace(p_tol=1e-15, max_cg=1000))
+    o.step(1)
+    fo = o.fields()
+    secs = time.perf_counter() - t0
+    out = {"sample": "one step of z-layers %d-%d (%dx%dx%d cells) from the workload's initial state; oracle "
+                     "solved to 1e-15 (%.1f s)" % (SLAB[0], SLAB[1], sample.nx, sample.ny, sample.nz, secs)}
+    uo = np.concatenate([fo["ux"], fo["uy"], fo["uz"]])
+    rel = lambda a, b: float(np.linalg.norm(a - b) / np.linalg.norm(b))
+    for name, prec in precisions:
+        g = mdbs.Simulation(sample.replace(precision=prec))
+        g.step(1)
+        fg = g.fields()
+        g.close()
+        ug = np.concatenate([fg["ux"], fg["uy"], fg["uz"]])
+        out[name] = {"alpha": rel(fg["alpha"], fo["alpha"]), "p": rel(fg["p"], fo["p"]), "u": rel(ug, uo),
+                     "p_tol": case.p_tol}
+    return out
+
+
+def batched_summary(args, precision, count, steps, warmup, stream, clock_index):
+    """A batch of `count` uneven domains (the batched recipe: 3/4 3-D with sides log-uniform in
+    [32, 96], 1/4 2-D in [64, 256]) in one launch per phase, autotuned; cell-steps/s."""
+    import torch
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    cases = W.batched_domains(count=count, seed=4, p_tol=1e-8, max_cg=200, precision=precision)
+    cells = sum(c.cells for c in cases)
+    sims = [mdbs.Simulation(c) for c in cases]
+    b = mdbs.Batch(sims)
+    b.set_stream(stream.cuda_stream)
+    tuning, _ = pick_schedule(b, args, trial_steps=1)
+    for _ in range(warmup):
+        b.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        b.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    iters = [s.stats()["cg_iters"] for s in sims]
+    b.close()
+    for s in sims:
+        s.close()
+    return {"value": cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps, "steps": steps,
+            "domains": count, "cells": cells, "precision": ["fp64", "mixed", "mixed_bf16"][precision],
+            "cg_iters_max": int(max(max(i) for i in iters)), "tuning": tuning}
+
+
+def serving_summary(precision, rate, duration, max_side, req_steps, stream):
+    """Continuous batching of a seeded Poisson trace of fractured-porous requests: served
+    cell-steps/s and p50/p99 request latency."""
+    from paper_2003_08374_gb300 import workloads as W
+    from paper_2003_08374_gb300.serve import Request, Server, fractured_request_case
+    trace = W.poisson_requests(rate=rate, duration=duration, seed=5, lo=32, hi=max_side)
+    reqs = [Request(rid=i, arrival=t["t"], steps=req_steps,
+                    case=fractured_request_case(t["side"], t["ca"], t["seed"], precision=precision, p_tol=1e-8,
+                                                max_cg=200))
+            for i, t in enumerate(trace)]
+    offered = sum(r.case.cells * r.steps for r in reqs) / duration
+    srv = Server(max_active=256, round_steps=10, keep_fields=False, stream_handle=stream.cuda_stream)
+    summ = srv.run(reqs)
+    summ.update({"precision": ["fp64", "mixed", "mixed_bf16"][precision], "offered_cell_steps_per_s": offered,
+                 "trace": "Poisson %.0f req/s for %.0f s, cube sides log-uniform in [32, %d], capillary number "
+                          "log-uniform in [1e-5, 1e-2], %d steps each" % (rate, duration, max_side, req_steps)})
+    return summ
 
 
 def pick_schedule(obj, args, trial_steps):
@@ -273,7 +436,7 @@ def pick_schedule(obj, args, trial_steps):
         kv = dict(item.split("=") for item in args.schedule.split(","))
         obj.set_tuning({"smooth_rows": int(kv.get("rows", 1)), "tail_cells": int(kv.get("tail", 4096)),
                         "snake": int(kv.get("snake", 0)), "sweep_kz": int(kv.get("kz", 0)),
-                        "tail_ctas": int(kv.get("ctas", 1))})
+                        "tail_ctas": int(kv.get("ctas", 1)), "coarse_coop": int(kv.get("coop", 0))})
         return obj.tuning(), []
     if args.no_autotune:
         return obj.tuning(), []
@@ -343,7 +506,11 @@ def gpu_arm(args):
     _, prof, _, _, _ = timed(sim, args.steps, args.warmup, "*")
     breakdown = {k: round(v[0] / args.steps, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][0])}
 
-    roof = roofline(prof, case.cells, 8 if args.precision == 0 else 4, fp64=args.precision == 0)
+    nu = (case.mg_nu1, case.mg_nu2)
+    word = 8 if args.precision == 0 else 4
+    roof = roofline(prof, case.cells, word, fp64=args.precision == 0, tuning=tuning, nu=nu)
+    roof_vc = vcycle_roofline(prof, (case.nx, case.ny, case.nz), word, tuning, ms, nu=nu,
+                              bf16_coarse=args.precision == 2)
 
     def variant(precision):
         """The same workload with the FP32 V-cycle (precision 1) or FP32 with BF16 coarse-level
@@ -363,8 +530,12 @@ def gpu_arm(args):
                "tuning": vtuning, "cg_iters_last_step": vst["cg_iters"],
                "cg_iters_timed": vst["cg_iters_total"] - it1, "cg_iters_warmup": it1 - it0}
         vsim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
-        _, vprof, _, _, _ = timed(vsim, args.steps, args.warmup, DOMINANT)
-        out["roofline"] = roofline(vprof, case.cells, 4, fp64=False)
+        _, vprof, _, _, _ = timed(vsim, args.steps, args.warmup, "*")
+        out["roofline"] = roofline(vprof, case.cells, 4, fp64=False, tuning=vtuning, nu=nu)
+        out["roofline_vcycle"] = vcycle_roofline(vprof, (case.nx, case.ny, case.nz), 4, vtuning, vms, nu=nu,
+                                                 bf16_coarse=precision == 2)
+        out["kernel_ms_per_step"] = {k: round(v[0] / args.steps, 4)
+                                     for k, v in sorted(vprof.items(), key=lambda kv: -kv[1][0])}
         vsim.close()
         return out
 
@@ -407,12 +578,24 @@ def gpu_arm(args):
     sim.close()
 
     cpu = None
+    errors = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         sample = slab_of(case)
         cval, csec = time_oracle(sample, 2, 0)
         cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": "2 oracle steps on z-layers %d-%d (%dx%dx%d cells) of the workload, %.1f s"
                          % (SLAB[0], SLAB[1], sample.nx, sample.ny, sample.nz, csec)}
+        # the error of each timed configuration against the FP64 oracle
+        errors = error_vs_oracle(case, [("fp64", W.FP64)] + ([] if args.no_mixed else
+                                                             [("mixed", W.MIXED), ("mixed_bf16", W.MIXED_BF16)]))
+    # reduced batched and serving configurations (stated in each object), FP64 and mixed
+    batched = serving = None
+    if not args.no_extras and world == 1:
+        batched = {name: batched_summary(args, prec, args.extra_domains, args.steps, args.warmup, stream, local)
+                   for name, prec in (("fp64", W.FP64), ("mixed", W.MIXED))}
+        serving = {name: serving_summary(prec, args.rate, args.extra_duration, args.extra_max_side,
+                                         args.extra_req_steps, stream)
+                   for name, prec in (("fp64", W.FP64), ("mixed", W.MIXED))}
 
     if rank == 0:
         line = {
@@ -424,9 +607,11 @@ def gpu_arm(args):
                        "l2": "inputs larger than L2 (%.1f GB device state)" % (mdbs.bytes_required(case) / 1e9),
                        "cg_iters_last_step": cg_iters, "tuning": tuning,
                        "autotune_ms_per_trial": [round(t, 3) for t in tune_ms]},
-            "mixed": mixed, "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "mixed": mixed, "roofline": roof, "roofline_vcycle": roof_vc, "error_vs_oracle": errors,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches,
             "kernel_ms_per_step": breakdown,
+            "batched": batched, "serving": serving,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
