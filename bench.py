@@ -63,7 +63,7 @@ def parse():
     ap.add_argument("--extra-max-side", type=int, default=64, help="serving sub-object: largest cube side")
     ap.add_argument("--extra-req-steps", type=int, default=50, help="serving sub-object: steps per request")
     ap.add_argument("--schedule", default=None,
-                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1,coop=1")
+                    help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1,coop=0,vec=0")
     return ap.parse_args()
 
 
@@ -436,7 +436,8 @@ def pick_schedule(obj, args, trial_steps):
         kv = dict(item.split("=") for item in args.schedule.split(","))
         obj.set_tuning({"smooth_rows": int(kv.get("rows", 1)), "tail_cells": int(kv.get("tail", 4096)),
                         "snake": int(kv.get("snake", 0)), "sweep_kz": int(kv.get("kz", 0)),
-                        "tail_ctas": int(kv.get("ctas", 1)), "coarse_coop": int(kv.get("coop", 0))})
+                        "tail_ctas": int(kv.get("ctas", 1)), "coarse_coop": int(kv.get("coop", 0)),
+                        "vec_sweeps": int(kv.get("vec", 0))})
         return obj.tuning(), []
     if args.no_autotune:
         return obj.tuning(), []

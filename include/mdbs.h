@@ -251,7 +251,12 @@ void mdbs_batch_destroy(mdbs_batch* batch);
  *                 apply), in ONE cooperative launch whose phases are separated by
  *                 grid-wide barriers instead of kernel boundaries (with sweep_kz 0 and
  *                 at least one such level; otherwise it has no effect)
- * Default: {1, 4096, 0, 0, 1, 0}.  Values outside these sets give MDBS_ERR_ARG.
+ *   vec_sweeps  : 0 or 1; 1 runs the half sweeps of every level whose n_x is a
+ *                 multiple of 4 (FP64) or 8 (FP32), with FP32 or FP64 coefficients,
+ *                 with each thread updating 2 (FP64) or 4 (FP32) consecutive cells of a
+ *                 colour run through 16-byte loads and stores (smooth_rows then does not
+ *                 apply to those levels)
+ * Default: {1, 4096, 0, 0, 1, 0, 0}.  Values outside these sets give MDBS_ERR_ARG.
  */
 typedef struct {
   int32_t smooth_rows;
@@ -260,6 +265,7 @@ typedef struct {
   int32_t sweep_kz;
   int32_t tail_ctas;
   int32_t coarse_coop;
+  int32_t vec_sweeps;
 } mdbs_tuning;
 
 /* Sets or reads the schedule of a simulation that is not in a batch (the step
@@ -273,8 +279,8 @@ int mdbs_batch_get_tuning(const mdbs_batch* batch, mdbs_tuning* out);
  * Picks the fastest schedule for this simulation (or batch) by timing real steps:
  * starting from the current schedule it tries the alternatives of snake, then of
  * sweep_kz (mixed precisions only), then of smooth_rows (when the half sweeps
- * run), then of coarse_coop, then of (tail_cells, tail_ctas) pairs (coordinate
- * descent), each for one untimed and
+ * run), then of coarse_coop, then of (tail_cells, tail_ctas) pairs, then of
+ * vec_sweeps (coordinate descent), each for one untimed and
  * trial_steps >= 1 timed steps (CUDA events on the simulation's stream), and keeps
  * a change only when it is faster.  The device state (fields, step scalars) is
  * copied aside first and restored after every trial, so the simulation continues

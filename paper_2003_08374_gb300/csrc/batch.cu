@@ -17,7 +17,7 @@ long long faces_total(const Prm& P) { return P.nf[0] + P.nf[1] + (P.dim == 3 ? P
 }  // namespace
 
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, int tail_ctas, int coarse_coop, BatchPlan* out) {
+                        int sweep_kz, int tail_ctas, int coarse_coop, int vec_sweeps, BatchPlan* out) {
   BatchPlan B{};
   B.ndom = ndom;
   B.flexible = flexible;
@@ -25,6 +25,7 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
   B.sweep_kz = sweep_kz;
   B.tail_ctas = tail_ctas;
   B.coarse_coop = coarse_coop;
+  B.vec_sweeps = vec_sweeps;
   int dev = 0, sms = 1;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -36,7 +37,7 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     if (e != cudaSuccess) return e;
   }
   // host block tables: spaces in a fixed order, each ndom + 1 prefix entries
-  const int nspace = 5 + 5 * kMaxLevels;
+  const int nspace = 5 + 6 * kMaxLevels;
   std::vector<int> tab((size_t)nspace * (ndom + 1), 0);
   auto fill = [&](int space, auto count) -> int {
     int* t = &tab[(size_t)space * (ndom + 1)];
@@ -48,11 +49,11 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     t[ndom] = (int)acc;
     return (int)acc;
   };
-  int totals[5 + 5 * kMaxLevels];
+  int totals[5 + 6 * kMaxLevels];
   // one row of kBlock elements per item, except the reduction spaces (kRepBig rows:
   // fewer block reductions and partials)
-  int reps[5 + 5 * kMaxLevels];
-  for (int q = 0; q < 5 + 5 * kMaxLevels; q++) reps[q] = 1;
+  int reps[5 + 6 * kMaxLevels];
+  for (int q = 0; q < 5 + 6 * kMaxLevels; q++) reps[q] = 1;
   reps[3] = reps[4] = kRepBig;
   reps[5 + kMaxLevels] = smooth_rows;  // finest-level red/black half sweeps
   auto blocks_of = [&](long long n, int space) { return items_of(n, reps[space]); };
@@ -90,6 +91,23 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     });
     totals[s2] = fill(s2, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l), s2) : 0LL; });
     totals[s3] = fill(s3, [&](int d) { return l < cg[d].first ? blocks_of(cells_at(d, l + 1), s3) : 0LL; });
+    // vector half sweeps: every domain whose level l precedes its tail needs n_x a
+    // multiple of 2 V (aligned colour runs) and, in FP32, coefficients that are not BF16
+    const int V = flexible ? 4 : 2;
+    bool vec_ok = true;
+    for (int d = 0; d < ndom; d++) {
+      if (l >= cg[d].first) continue;
+      if (cg[d].ld[l].n[0] % (2 * V) != 0) vec_ok = false;
+      if (flexible && cg[d].lf[l].Tb[0] != nullptr) vec_ok = false;
+    }
+    if (vec_ok) B.vec_levels |= 1u << l;
+    const int s5 = 5 + 5 * kMaxLevels + l;
+    totals[s5] = fill(s5, [&](int d) -> long long {
+      if (!vec_ok || l >= cg[d].first) return 0;
+      const Level<double>& L = cg[d].ld[l];
+      const long long halfs = (long long)(L.n[0] / 2) * L.n[1] * L.n[2];
+      return (halfs / V + kBlock - 1) / kBlock;
+    });
     const int s4 = 5 + 4 * kMaxLevels + l;
     totals[s4] = fill(s4, [&](int d) -> long long {
       if (l >= cg[d].first || sweep_kz <= 0) return 0;
@@ -134,6 +152,7 @@ cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexib
     B.lfine[l] = work(5 + 2 * kMaxLevels + l);
     B.lcoarse[l] = work(5 + 3 * kMaxLevels + l);
     B.lsweep[l] = work(5 + 4 * kMaxLevels + l);
+    B.lvec[l] = work(5 + 5 * kMaxLevels + l);
   }
   *out = B;
   return cudaSuccess;

@@ -397,7 +397,8 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
 
 cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible, const mdbs_tuning& t) {
   cudaError_t e =
-      plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, t.tail_ctas, t.coarse_coop, &ex.plan);
+      plan_create(sd, cg, ndom, flexible, t.smooth_rows, t.snake, t.sweep_kz, t.tail_ctas, t.coarse_coop,
+                  t.vec_sweeps, &ex.plan);
   if (e != cudaSuccess) return e;
   ex.planned = true;
   if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
@@ -462,7 +463,7 @@ cudaError_t exec_steps(Exec& ex, const mdbs_options& opt, Profiler& prof, cudaSt
   return cudaSuccess;
 }
 
-const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0, 1, 0};
+const mdbs_tuning kDefaultTuning = {1, 4096, 0, 0, 1, 0, 0};
 
 // whether a kernel of the plan reported a bounded wait that ran out (synchronous read)
 bool plan_failed(const BatchPlan& B) {
@@ -477,7 +478,7 @@ bool valid_tuning(const mdbs_tuning* t) {
          t->tail_cells >= 0 && t->tail_cells <= kTailCellsMax && (t->snake == 0 || t->snake == 1) &&
          (t->sweep_kz == 0 || t->sweep_kz == 4 || t->sweep_kz == 8 || t->sweep_kz == 16 || t->sweep_kz == 32) &&
          (t->tail_ctas == 1 || t->tail_ctas == 2 || t->tail_ctas == 4 || t->tail_ctas == 8) &&
-         (t->coarse_coop == 0 || t->coarse_coop == 1);
+         (t->coarse_coop == 0 || t->coarse_coop == 1) && (t->vec_sweeps == 0 || t->vec_sweeps == 1);
 }
 
 // (re)builds the batch-of-one plan of a simulation for its schedule
@@ -601,12 +602,13 @@ int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_optio
   const int kzs[] = {0, 4, 8, 16, 32};
   const int rows[] = {1, 2, 4, 8};
   const int coops[] = {0, 1};
+  const int vecs[] = {0, 1};
   // (tail_cells, tail_ctas): larger tails want more CTAs
   const int tails[][2] = {{0, 1}, {512, 1}, {4096, 1}, {4096, 4}, {32768, 4}, {32768, 8}, {262144, 8}};
-  for (int axis = 0; axis < 5 && e == cudaSuccess; axis++) {
+  for (int axis = 0; axis < 6 && e == cudaSuccess; axis++) {
     if (axis == 2 && best.sweep_kz > 0 && fp32_levels) continue;
     if (axis == 1 && !fp32_levels) continue;
-    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : axis == 2 ? 4 : axis == 3 ? 2 : 7;
+    const int nv = axis == 0 ? 2 : axis == 1 ? 5 : axis == 2 ? 4 : axis == 3 ? 2 : axis == 4 ? 7 : 2;
     const mdbs_tuning base = best;
     for (int v = 0; v < nv && e == cudaSuccess; v++) {
       mdbs_tuning t = base;
@@ -618,8 +620,10 @@ int autotune_impl(const std::vector<mdbs_sim*>& sims, Exec& ex, const mdbs_optio
         t.tail_cells = tails[v][0];
         t.tail_ctas = tails[v][1];
       }
+      if (axis == 5) t.vec_sweeps = vecs[v];
       if (t.snake == base.snake && t.sweep_kz == base.sweep_kz && t.smooth_rows == base.smooth_rows &&
-          t.tail_cells == base.tail_cells && t.tail_ctas == base.tail_ctas && t.coarse_coop == base.coarse_coop)
+          t.tail_cells == base.tail_cells && t.tail_ctas == base.tail_ctas && t.coarse_coop == base.coarse_coop &&
+          t.vec_sweeps == base.vec_sweeps)
         continue;
       double ms = 0.0;
       e = trial(t, &ms);

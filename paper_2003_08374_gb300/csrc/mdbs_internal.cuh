@@ -274,6 +274,9 @@ struct BatchPlan {
   Work lfine[kMaxLevels];     // level-l cells of the same domains (prolongation)
   Work lcoarse[kMaxLevels];   // level-(l+1) cells of the same domains (restriction)
   Work lsweep[kMaxLevels];    // fused-sweep tiles (kSweepTX x kSweepTY columns x sweep_kz planes) of the same domains
+  Work lvec[kMaxLevels];      // vector half sweeps: kBlock threads x (2 FP64 / 4 FP32) half cells per item
+  unsigned vec_levels;        // bit l: every domain's level l (before its tail) allows vector half sweeps
+  int vec_sweeps;             // use them (schedule)
   int max_first;              // largest tail start over the domains
   long long tail_words;       // largest x + b element count of a domain's tail levels
   int tail_ctas;              // CTAs (one cluster) per domain in the tail kernel
@@ -366,7 +369,7 @@ cudaError_t bounded_wait_selftest(int* status, double* waited_s);
 // in the tail kernel (1, 2, 4, 8: one cluster)
 // coarse_coop: run the levels between the finest and the tail in one cooperative launch
 cudaError_t plan_create(const StepDom* sd, const CgDom* cg, int ndom, int flexible, int smooth_rows, int snake,
-                        int sweep_kz, int tail_ctas, int coarse_coop, BatchPlan* out);
+                        int sweep_kz, int tail_ctas, int coarse_coop, int vec_sweeps, BatchPlan* out);
 // CTAs of the cooperative coarse-level kernel that are resident at once on this device
 cudaError_t coop_grid_size(int flexible, long long tail_words, int* grid);
 void plan_destroy(BatchPlan* B);

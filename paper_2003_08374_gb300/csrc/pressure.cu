@@ -431,6 +431,159 @@ __global__ void __launch_bounds__(kBlock, REP == 1 ? 8 : 1)
   }
 }
 
+// ------------------------------------------------------------------ vector half sweeps
+// A half sweep in which each thread updates kVec consecutive cells of one colour
+// run of a row (2 in FP64, 4 in FP32: 16 bytes) with 128-bit loads and stores.  In
+// the x-split storage a run of cells of one colour, their right-hand sides, 1/diag,
+// their T_x, T_y, T_z and their y and z neighbours are all contiguous and, when n_x
+// is a multiple of 2 kVec, 16-byte aligned; the x neighbours are the other colour's
+// run shifted by one cell (one extra scalar load).  Each cell's arithmetic is
+// smooth_cell's (the same fma chain in the same order), so values are bitwise those
+// of the scalar sweep.  Levels of BF16 coefficients use the scalar sweep.
+template <typename R>
+struct VecOf;
+template <>
+struct VecOf<double> {
+  using T = double2;
+  static constexpr int N = 2;
+};
+template <>
+struct VecOf<float> {
+  using T = float4;
+  static constexpr int N = 4;
+};
+
+template <typename R>
+__device__ __forceinline__ void ld_vec(const R* __restrict__ p, R* o) {
+  const typename VecOf<R>::T v = *reinterpret_cast<const typename VecOf<R>::T*>(p);
+  if constexpr (VecOf<R>::N == 2) {
+    o[0] = v.x;
+    o[1] = v.y;
+  } else {
+    o[0] = v.x;
+    o[1] = v.y;
+    o[2] = v.z;
+    o[3] = v.w;
+  }
+}
+template <typename R>
+__device__ __forceinline__ void st_vec(R* __restrict__ p, const R* o) {
+  typename VecOf<R>::T v;
+  if constexpr (VecOf<R>::N == 2) {
+    v.x = o[0];
+    v.y = o[1];
+  } else {
+    v.x = o[0];
+    v.y = o[1];
+    v.z = o[2];
+    v.w = o[3];
+  }
+  *reinterpret_cast<typename VecOf<R>::T*>(p) = v;
+}
+
+template <typename R, bool PRO>
+__global__ void __launch_bounds__(kBlock, 3)
+    k_smooth_vec(const CgDom* __restrict__ C, Work w, int l, int col, int zero, int rev) {
+  constexpr int V = VecOf<R>::N;
+  MDBS_DEPENDENT_ENTRY();
+  FOR_WORK_DIR(w, rev)
+    const CgDom& G = C[dm];
+    if (G.scal[kCond] == 0.0) continue;
+    const Level<R>& Lr = levels_of<R>(G)[l];
+    const int n0 = Lr.n[0], n1 = Lr.n[1], n2 = Lr.n[2];
+    const unsigned half = (unsigned)n0 >> 1;  // both runs: n0 is a multiple of 2 V
+    const unsigned total = half * (unsigned)n1 * (unsigned)n2;
+    const unsigned t0 = ((unsigned)lb * kBlock + threadIdx.x) * V;  // first half cell of this thread
+    if (t0 >= total) continue;
+    const unsigned row = fastdiv(t0, Lr.dhalf), ti0 = t0 - row * half;
+    const unsigned kk = fastdiv(row, Lr.dn1);
+    const int j = (int)(row - kk * (unsigned)n1), k = (int)kk;
+    const int sh = (j + k + col) & 1;
+    const unsigned rb = (unsigned)n0 * row, c0 = rb + (sh ? half + ti0 : ti0);
+    const R* __restrict__ bb = Lr.b;
+    const R* __restrict__ dinv = Lr.dinv;
+    R* __restrict__ x = Lr.x;
+    const R* __restrict__ Tx = Lr.T[0];
+    const R* __restrict__ Ty = Lr.T[1];
+    const R* __restrict__ Tz = Lr.T[2];
+    R acc[V], di[V];
+    ld_vec(bb + c0, acc);
+    ld_vec(dinv + c0, di);
+    if (zero) {
+      for (int v = 0; v < V; v++) acc[v] = acc[v] * di[v];
+      st_vec(x + c0, acc);
+      continue;
+    }
+    // x neighbours: the other colour's run, shifted by one cell to the left (even cells)
+    // or to the right (odd cells); the coefficient of the low face sits at the low
+    // neighbour, that of the high face at the cell itself
+    R xm[V], xp[V], tm[V], tp[V], ta[V];
+    if (sh == 0) {  // cells i = 2 (ti0 + v); i - 1 at rb + half + ti0 + v - 1, i + 1 at rb + half + ti0 + v
+      ld_vec(x + rb + half + ti0, xp);
+      ld_vec(Tx + rb + half + ti0, ta);
+      ld_vec(Tx + c0, tp);
+      const bool first = ti0 == 0;
+      xm[0] = first ? R(0) : x[rb + half + ti0 - 1];
+      tm[0] = first ? R(0) : Tx[rb + half + ti0 - 1];
+      for (int v = 1; v < V; v++) {
+        xm[v] = xp[v - 1];
+        tm[v] = ta[v - 1];
+      }
+    } else {  // cells i = 2 (ti0 + v) + 1; i - 1 at rb + ti0 + v, i + 1 at rb + ti0 + v + 1
+      ld_vec(x + rb + ti0, xm);
+      ld_vec(Tx + rb + ti0, tm);
+      ld_vec(Tx + c0, tp);
+      for (int v = 0; v + 1 < V; v++) xp[v] = xm[v + 1];
+      const bool last = ti0 + V == half;  // the last odd cell of the row has no x+ neighbour
+      xp[V - 1] = last ? R(0) : x[rb + ti0 + V];
+    }
+    auto e = [&](int a, int b2, int d) -> R {
+      const Level<R>& Co = levels_of<R>(G)[l + 1];
+      return Co.x[lpos(Co.n, Co.cz[0] ? a >> 1 : a, Co.cz[1] ? b2 >> 1 : b2, Co.cz[2] ? d >> 1 : d)];
+    };
+    const unsigned sy = (unsigned)n0, sz = (unsigned)n0 * (unsigned)n1;
+    R ym[V], yp[V], zm[V], zp[V], tym[V], typ[V], tzm[V], tzp[V];
+    if (j > 0) {
+      ld_vec(x + c0 - sy, ym);
+      ld_vec(Ty + c0 - sy, tym);
+    }
+    if (j + 1 < n1) {
+      ld_vec(x + c0 + sy, yp);
+      ld_vec(Ty + c0, typ);
+    }
+    if (k > 0) {
+      ld_vec(x + c0 - sz, zm);
+      ld_vec(Tz + c0 - sz, tzm);
+    }
+    if (k + 1 < n2) {
+      ld_vec(x + c0 + sz, zp);
+      ld_vec(Tz + c0, tzp);
+    }
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      const int i = 2 * (int)(ti0 + v) + sh;
+      R s = acc[v];
+      if constexpr (PRO) {
+        if (i > 0) s = fma_r(tm[v], xm[v] + e(i - 1, j, k), s);
+        if (i + 1 < n0) s = fma_r(tp[v], xp[v] + e(i + 1, j, k), s);
+        if (j > 0) s = fma_r(tym[v], ym[v] + e(i, j - 1, k), s);
+        if (j + 1 < n1) s = fma_r(typ[v], yp[v] + e(i, j + 1, k), s);
+        if (k > 0) s = fma_r(tzm[v], zm[v] + e(i, j, k - 1), s);
+        if (k + 1 < n2) s = fma_r(tzp[v], zp[v] + e(i, j, k + 1), s);
+      } else {
+        if (i > 0) s = fma_r(tm[v], xm[v], s);
+        if (i + 1 < n0) s = fma_r(tp[v], xp[v], s);
+        if (j > 0) s = fma_r(tym[v], ym[v], s);
+        if (j + 1 < n1) s = fma_r(typ[v], yp[v], s);
+        if (k > 0) s = fma_r(tzm[v], zm[v], s);
+        if (k + 1 < n2) s = fma_r(tzp[v], zp[v], s);
+      }
+      acc[v] = s * di[v];
+    }
+    st_vec(x + c0, acc);
+  }
+}
+
 // ------------------------------------------------------------------ fused red-black sweep (FP32)
 // One launch per sweep pair of an FP32 level: colour c1 everywhere, then the other
 // colour.  A CTA owns an extended tile of kSweepCX x kSweepBY cells (the interior
@@ -1849,6 +2002,11 @@ static void smooth_half_t(const BatchPlan& B, int l, int col, int zero, Dirs& D,
   const int id = PRO ? (l == 0 ? K_PROLONG0 : K_PROLONGC) : (l == 0 ? K_SMOOTH0 : K_SMOOTHC);
   const Work& w = B.lhalf[l];
   const int rev = D.next(l);
+  if (B.vec_sweeps && (B.vec_levels >> l & 1u)) {
+    const Work& wv = B.lvec[l];
+    MDBS_LAUNCH(id, grid_of(B, wv), kBlock, s, (k_smooth_vec<R, PRO>), B.cg, wv, l, col, zero, rev);
+    return;
+  }
   switch (w.rep) {
     case 8: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 8, PRO>), B.cg, w, l, col, zero, rev); break;
     case 4: MDBS_LAUNCH(id, grid_of(B, w), kBlock, s, (k_smooth<R, 4, PRO>), B.cg, w, l, col, zero, rev); break;

@@ -57,18 +57,20 @@ _hook = None  # keeps the ctypes callbacks of the installed allocator alive
 class Tuning(C.Structure):
     """Schedule of the multigrid kernels (mdbs_tuning); results do not depend on it."""
     _fields_ = [("smooth_rows", C.c_int32), ("tail_cells", C.c_int32), ("snake", C.c_int32),
-                ("sweep_kz", C.c_int32), ("tail_ctas", C.c_int32), ("coarse_coop", C.c_int32)]
+                ("sweep_kz", C.c_int32), ("tail_ctas", C.c_int32), ("coarse_coop", C.c_int32),
+                ("vec_sweeps", C.c_int32)]
 
     def as_dict(self):
         return {"smooth_rows": self.smooth_rows, "tail_cells": self.tail_cells, "snake": self.snake,
-                "sweep_kz": self.sweep_kz, "tail_ctas": self.tail_ctas, "coarse_coop": self.coarse_coop}
+                "sweep_kz": self.sweep_kz, "tail_ctas": self.tail_ctas, "coarse_coop": self.coarse_coop,
+                "vec_sweeps": self.vec_sweeps}
 
 
 def _tuning(t):
     if isinstance(t, Tuning):
         return t
     return Tuning(t["smooth_rows"], t["tail_cells"], t["snake"], t["sweep_kz"], t.get("tail_ctas", 1),
-                  t.get("coarse_coop", 0))
+                  t.get("coarse_coop", 0), t.get("vec_sweeps", 0))
 
 
 class MdbsError(RuntimeError):

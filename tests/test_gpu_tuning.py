@@ -7,14 +7,17 @@ import pytest
 
 pytestmark = pytest.mark.gpu
 
-def _sch(rows, tail, snake, kz, ctas, coop):
+def _sch(rows, tail, snake, kz, ctas, coop, vec=0):
     return {"smooth_rows": rows, "tail_cells": tail, "snake": snake, "sweep_kz": kz, "tail_ctas": ctas,
-            "coarse_coop": coop}
+            "coarse_coop": coop, "vec_sweeps": vec}
 
 
 SCHEDULES = [
-    _sch(1, 4096, 0, 0, 1, 0),     # default
+    _sch(1, 4096, 0, 0, 1, 0, 0),  # default
+    _sch(1, 4096, 0, 0, 1, 0, 1),  # vector half sweeps where aligned
     _sch(1, 4096, 0, 0, 1, 1),     # levels 1-2 and the tail in one cooperative launch
+    _sch(1, 0, 1, 0, 1, 1, 1),     # vector sweeps where aligned, cooperative down to the coarsest level
+    _sch(1, 4096, 1, 8, 1, 0, 1),  # fused sweeps (FP32) with vector sweeps elsewhere
     _sch(8, 4096, 1, 8, 1, 0),     # fused sweeps
     _sch(2, 0, 1, 0, 2, 0),        # coarsest only in the tail, 2 CTAs
     _sch(2, 0, 1, 0, 1, 1),        # cooperative down to the coarsest level
@@ -162,3 +165,21 @@ def test_bounded_wait_gives_up_and_the_device_stays_usable():
     s.step(1)
     assert s.stats()["steps"] == 1
     s.close()
+
+
+@pytest.mark.parametrize("precision", [0, 1, 2])
+def test_vector_half_sweeps_are_bitwise_equal(precision):
+    """Vector half sweeps (2 FP64 / 4 FP32 consecutive cells of a colour run per thread,
+    16-byte loads) on every level whose n_x allows them: 40 x 23 x 19 (levels with n_x 40,
+    20, 10, 5: the vector path where n_x is a multiple of 4 or 8, the scalar one
+    elsewhere, ragged y and z) and 72 x 30 x 17, with and without the single-CTA tail;
+    the fields must equal the scalar sweeps'."""
+    from paper_2003_08374_gb300 import workloads as W
+    for shape in ((40, 23, 19), (72, 30, 17)):
+        case = W.grf_3d(shape=shape, seed=4, corr_len=4.0, frac_w=3, p_tol=1e-10, max_cg=300, precision=precision)
+        ref_f, ref_s = _run(case, _sch(1, 0, 0, 0, 1, 0, 0))
+        for sch in (_sch(1, 0, 0, 0, 1, 0, 1), _sch(1, 4096, 1, 0, 1, 0, 1), _sch(1, 0, 0, 0, 1, 1, 1)):
+            f, st = _run(case, sch)
+            for k in ref_f:
+                assert np.array_equal(ref_f[k], f[k]), (shape, sch, k)
+            assert st["cg_iters"] == ref_s["cg_iters"]
