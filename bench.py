@@ -13,7 +13,14 @@ properties, momentum predictor, two PISO correctors with GMG-PCG).
 
 Under torchrun (N > 1) every rank advances its own replica of the workload:
 the single-domain step has no data-parallel split, so the GPUs run
-independent replicas (weak scaling) and the job throughput is the sum.
+independent replicas (weak scaling) and the job throughput is the sum.  The
+batched and serving workloads deal their independent domains / requests to
+the ranks instead (no collective on the data path).
+
+The default line also carries, on stated reduced configurations: the error of
+one step of every precision against the oracle (``error_vs_oracle``), the
+V-cycle-wide roofline, a 64-domain batch, a 3 s serving trace (p50/p99), the
+512 x 128 x 256 wave tank (mixed + BF16 and FP64) and the 2-D 64^2 case.
 ``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
 workload (a 16-layer slab), on rank 0 only.
 """
@@ -62,6 +69,7 @@ def parse():
     ap.add_argument("--extra-duration", type=float, default=3.0, help="serving sub-object: arrival window [s]")
     ap.add_argument("--extra-max-side", type=int, default=64, help="serving sub-object: largest cube side")
     ap.add_argument("--extra-req-steps", type=int, default=50, help="serving sub-object: steps per request")
+    ap.add_argument("--wave-steps", type=int, default=10, help="wave tank sub-object: timed steps")
     ap.add_argument("--schedule", default=None,
                     help="fixed multigrid schedule instead of autotuning, e.g. rows=1,tail=4096,snake=0,kz=8,ctas=1,coop=0,vec=0")
     return ap.parse_args()
@@ -114,6 +122,29 @@ def max_over_ranks(x, world, device):
     t = torch.tensor([x], dtype=torch.float64, device=device)
     torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
     return float(t.item())
+
+
+def shard_by_cells(cells, world):
+    """Independent units (domains, requests) of the given cell counts dealt to `world` ranks:
+    largest first to the rank with the fewest cells so far (ties: lowest rank), so every
+    rank's share is within one unit of the mean.  Returns one index list per rank."""
+    load = [0] * world
+    out = [[] for _ in range(world)]
+    for i in sorted(range(len(cells)), key=lambda i: (-cells[i], i)):
+        r = min(range(world), key=lambda q: (load[q], q))
+        out[r].append(i)
+        load[r] += cells[i]
+    return [sorted(o) for o in out]
+
+
+def gather_lists(values, world):
+    """Concatenation of every rank's host list (statistics only; no device data)."""
+    if world == 1:
+        return list(values)
+    import torch.distributed as dist
+    parts = [None] * world
+    dist.all_gather_object(parts, list(values))
+    return [v for part in parts for v in part]
 
 
 def replicas_value(cells, steps, world, ms):
@@ -410,6 +441,92 @@ def batched_summary(args, precision, count, steps, warmup, stream, clock_index):
             "cg_iters_max": int(max(max(i) for i in iters)), "tuning": tuning}
 
 
+def timed_steps(sim, steps, warmup, stream):
+    import torch
+    for _ in range(warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        sim.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def field_errors(fg, fo):
+    rel = lambda a, b: float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+    ug = np.concatenate([fg["ux"], fg["uy"], fg["uz"]])
+    uo = np.concatenate([fo["ux"], fo["uy"], fo["uz"]])
+    return {"alpha": rel(fg["alpha"], fo["alpha"]), "p": rel(fg["p"], fo["p"]), "u": rel(ug, uo)}
+
+
+def wave_tank_summary(args, steps, warmup, stream):
+    """The wave tank of section 5.1's stand-in (512 x 128 x 256 cells, porous barrier, solitary
+    wave, CFL 0.5): mixed precision with BF16 coarse coefficients (its configuration) and
+    FP64, autotuned, over a stated number of steps from the initial state; the error of one
+    step of a 2-cell-wide span of the same tank (it is uniform along y) against the oracle."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    out = {"workload": "wave_tank_512x128x256 (16.8 M cells, CFL 0.5, dt_max 2e-3 s)", "p_tol": 1e-8}
+    for name, prec in (("mixed_bf16", W.MIXED_BF16), ("fp64", W.FP64)):
+        case = W.wave_tank(p_tol=1e-8, max_cg=200, precision=prec)
+        sim = mdbs.Simulation(case)
+        sim.set_stream(stream.cuda_stream)
+        tuning, _ = pick_schedule(sim, args, trial_steps=1)
+        sim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
+        ms = timed_steps(sim, steps, warmup, stream)
+        st = sim.stats()
+        out[name] = {"value": case.cells * steps / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / steps,
+                     "steps": steps, "warmup": warmup, "dt_after": st["dt"], "time_after": st["time"],
+                     "cg_iters_last_step": st["cg_iters"], "tuning": tuning}
+        sim.close()
+    out["mixed_bf16"]["speedup_vs_fp64"] = out["mixed_bf16"]["value"] / out["fp64"]["value"]
+    # error of one step against the oracle on the same recipe at a quarter of the length and
+    # depth and a 2-cell span (a full-size span already needs about 500 oracle CG iterations
+    # at 1e-15: the free surface at a density ratio of 1000 makes the pressure system stiff)
+    small = W.wave_tank(nx=128, ny=2, nz=64, depth=20, x0=32, barrier=(80, 96, 24), p_tol=1e-8, max_cg=500)
+    t0 = time.perf_counter()
+    o = OracleSim(small.replace(p_tol=1e-15, max_cg=2000, precision=W.FP64))
+    o.step(1)
+    fo = o.fields()
+    secs = time.perf_counter() - t0
+    out["error_vs_oracle"] = {"sample": "one step of the tank recipe at quarter length and depth with a 2-cell span "
+                                        "(128 x 2 x 64), oracle at 1e-15 (%.1f s)" % secs}
+    for name, prec in (("mixed_bf16", W.MIXED_BF16), ("fp64", W.FP64)):
+        g = mdbs.Simulation(small.replace(precision=prec))
+        g.step(1)
+        out["error_vs_oracle"][name] = field_errors(g.fields(), fo)
+        g.close()
+    return out
+
+
+def fracture_2d_summary(stream):
+    """The 2-D 64 x 64 fracture case (dx 10 um, dt 1e-6 s, FP64, 100 steps): a launch-bound
+    step; its error after the 100 steps against the oracle at 1e-15, the case at 1e-8."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    out = {"workload": "fracture_2d_64x64 (FP64, 100 steps)"}
+    ref = OracleSim(W.fracture_2d(nx=64, ny=64, p_tol=1e-15, max_cg=500))
+    ref.step(100)
+    fo = ref.fields()
+    for p_tol in (1e-8, 1e-15):
+        case = W.fracture_2d(nx=64, ny=64, p_tol=p_tol, max_cg=500)
+        sim = mdbs.Simulation(case)
+        sim.set_stream(stream.cuda_stream)
+        ms = timed_steps(sim, 100, 0, stream)
+        st = sim.stats()
+        key = "p_tol_%.0e" % p_tol
+        out[key] = {"value": case.cells * 100 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / 100,
+                    "launches_per_step": st["kernel_launches"] / 100.0, "cg_iters_last_step": st["cg_iters"]}
+        out[key]["error_vs_oracle_1e-15"] = field_errors(sim.fields(), fo)
+        sim.close()
+    return out
+
+
 def serving_summary(precision, rate, duration, max_side, req_steps, stream):
     """Continuous batching of a seeded Poisson trace of fractured-porous requests: served
     cell-steps/s and p50/p99 request latency."""
@@ -590,8 +707,10 @@ def gpu_arm(args):
         errors = error_vs_oracle(case, [("fp64", W.FP64)] + ([] if args.no_mixed else
                                                              [("mixed", W.MIXED), ("mixed_bf16", W.MIXED_BF16)]))
     # reduced batched and serving configurations (stated in each object), FP64 and mixed
-    batched = serving = None
+    batched = serving = wave = frac2d = None
     if not args.no_extras and world == 1:
+        wave = wave_tank_summary(args, args.wave_steps, args.warmup, stream)
+        frac2d = fracture_2d_summary(stream)
         batched = {name: batched_summary(args, prec, args.extra_domains, args.steps, args.warmup, stream, local)
                    for name, prec in (("fp64", W.FP64), ("mixed", W.MIXED))}
         serving = {name: serving_summary(prec, args.rate, args.extra_duration, args.extra_max_side,
@@ -612,7 +731,7 @@ def gpu_arm(args):
             "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches,
             "kernel_ms_per_step": breakdown,
-            "batched": batched, "serving": serving,
+            "batched": batched, "serving": serving, "wave_tank": wave, "fracture_2d": frac2d,
         }
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -620,18 +739,32 @@ def gpu_arm(args):
     return 0
 
 
-def batched_arm(args):
-    """Many uneven independent domains advanced as one batch (one launch per step phase,
-    one CUDA graph per step): sides log-uniform in [32, 96] (3-D) or [64, 256] (2-D)."""
-    import torch
+def init_ranks(torch):
     rank, world, local = dist_info()
     torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return rank, world, local
+
+
+def batched_arm(args):
+    """Many uneven independent domains advanced as one batch (one launch per step phase,
+    one CUDA graph per step): sides log-uniform in [32, 96] (3-D) or [64, 256] (2-D).
+    Under torchrun the seeded set of `domains` x N domains is dealt to the N ranks by cell
+    count (every rank about `domains` domains: weak scaling); each rank advances its own
+    batch, nothing crosses ranks but the timing and the statistics."""
+    import torch
+    rank, world, local = init_ranks(torch)
     from paper_2003_08374_gb300.build import build_library
     build_library()
     from paper_2003_08374_gb300 import mdbs
     from paper_2003_08374_gb300 import workloads as W
-    cases = W.batched_domains(count=args.domains, seed=4, p_tol=1e-8, max_cg=200, precision=args.precision)
-    cells = sum(c.cells for c in cases)
+    all_cases = W.batched_domains(count=args.domains * world, seed=4, p_tol=1e-8, max_cg=200,
+                                  precision=args.precision)
+    mine = shard_by_cells([c.cells for c in all_cases], world)[rank]
+    cases = [all_cases[i] for i in mine]
+    cells_all = sum(c.cells for c in all_cases)
     stream = torch.cuda.current_stream()
     sims = [mdbs.Simulation(c) for c in cases]
     b = mdbs.Batch(sims)
@@ -639,6 +772,8 @@ def batched_arm(args):
     tuning, tune_ms = pick_schedule(b, args, trial_steps=1)
     for _ in range(args.warmup):
         b.step(1)
+    if world > 1:
+        torch.distributed.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(local) as clk:
@@ -647,18 +782,25 @@ def batched_arm(args):
             b.step(1)
         e1.record(stream)
         torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
-    iters = [s.stats()["cg_iters"] for s in sims]
-    line = {"metric": METRIC, "value": cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "batched_%d_domains" % len(cases), "cells": cells,
-                       "precision": "fp64" if args.precision == 0 else "mixed",
-                       "cg_iters_max": max(max(i) for i in iters), "cg_iters_mean": float(np.mean(iters)),
-                       "tuning": tuning, "autotune_ms_per_trial": [round(t, 2) for t in tune_ms]},
-            "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.barrier()
+    ms = max_over_ranks(e0.elapsed_time(e1), world, "cuda")
+    iters = gather_lists([max(s.stats()["cg_iters"]) for s in sims], world)
+    if rank == 0:
+        line = {"metric": METRIC, "value": cells_all * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic",
+                "config": {"workload": "batched_%d_domains" % len(all_cases), "cells": cells_all,
+                           "precision": "fp64" if args.precision == 0 else "mixed",
+                           "parallelism": "domains dealt to %d ranks by cell count" % world if world > 1 else "single",
+                           "cg_iters_max": int(max(iters)), "cg_iters_mean": float(np.mean(iters)),
+                           "tuning": tuning, "autotune_ms_per_trial": [round(t, 2) for t in tune_ms]},
+                "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
     b.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
@@ -757,33 +899,49 @@ def bl_arm(args):
 
 def serving_arm(args):
     """Continuous batching of a seeded Poisson trace of fractured-porous requests (sides
-    log-uniform in [32, max_side], capillary number log-uniform in [1e-5, 1e-2])."""
+    log-uniform in [32, max_side], capillary number log-uniform in [1e-5, 1e-2]).  Under
+    torchrun the trace arrives at N times the rate and its requests are dealt to the N
+    ranks round robin in arrival order (weak scaling); each rank serves its own; the
+    latencies are gathered on the host for p50/p99 over all requests."""
     import torch
-    rank, world, local = dist_info()
-    torch.cuda.set_device(local)
+    rank, world, local = init_ranks(torch)
     from paper_2003_08374_gb300.build import build_library
     build_library()
     from paper_2003_08374_gb300 import workloads as W
     from paper_2003_08374_gb300.serve import Request, Server, fractured_request_case
-    trace = W.poisson_requests(rate=args.rate, duration=args.duration, seed=5, lo=32, hi=args.max_side)
+    trace = W.poisson_requests(rate=args.rate * world, duration=args.duration, seed=5, lo=32, hi=args.max_side)
     reqs = [Request(rid=i, arrival=t["t"], steps=args.req_steps,
                     case=fractured_request_case(t["side"], t["ca"], t["seed"], precision=args.precision,
                                                 p_tol=1e-8, max_cg=200))
-            for i, t in enumerate(trace)]
-    offered = sum(r.case.cells * r.steps for r in reqs) / args.duration
+            for i, t in enumerate(trace) if i % world == rank]
+    offered = sum(c["side"] ** 3 for c in trace) * args.req_steps / args.duration
     srv = Server(max_active=256, round_steps=10, keep_fields=False,
                  stream_handle=torch.cuda.current_stream().cuda_stream)
+    if world > 1:
+        torch.distributed.barrier()
     with ClockSampler(local) as clk:
         summary = srv.run(reqs)
-    line = {"metric": METRIC, "value": summary["served_cell_steps_per_s"], "unit": UNIT, "n_gpus": 1,
-            "steps": args.req_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "serving_poisson_%.0fps_%.0fs_side32-%d_%dsteps" % (args.rate, args.duration,
-                                                                                    args.max_side, args.req_steps),
-                       "precision": "fp64" if args.precision == 0 else "mixed",
-                       "offered_cell_steps_per_s": offered},
-            "serving": summary, "clocks": clk.summary()}
-    print(json.dumps(line), flush=True)
+    lat = gather_lists([r.finished - r.arrival for r in reqs if r.finished is not None], world)
+    served = gather_lists([srv.cell_steps], world)
+    wall = max_over_ranks(summary["wall_s"], world, "cuda")
+    if world > 1:
+        summary.update({"completed": len(lat), "requests": len(trace), "wall_s": wall,
+                        "p50_latency_s": float(np.percentile(lat, 50)) if lat else None,
+                        "p99_latency_s": float(np.percentile(lat, 99)) if lat else None,
+                        "served_cell_steps_per_s": sum(served) / wall})
+    if rank == 0:
+        line = {"metric": METRIC, "value": summary["served_cell_steps_per_s"], "unit": UNIT, "n_gpus": world,
+                "steps": args.req_steps, "warmup": 0, "ms_per_step": None, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": "serving_poisson_%.0fps_%.0fs_side32-%d_%dsteps" % (
+                    args.rate * world, args.duration, args.max_side, args.req_steps),
+                    "precision": "fp64" if args.precision == 0 else "mixed",
+                    "parallelism": "requests dealt to %d ranks round robin" % world if world > 1 else "single",
+                    "offered_cell_steps_per_s": offered},
+                "serving": summary, "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
     return 0
 
 
