@@ -90,6 +90,16 @@ void prof_begin(int id, cudaStream_t s) {
 
 long long launch_count() { return g_active ? g_active->launches : 0; }
 
+static thread_local cudaError_t g_launch_error = cudaSuccess;
+void set_launch_error(cudaError_t e) {
+  if (g_launch_error == cudaSuccess) g_launch_error = e;
+}
+cudaError_t take_launch_error() {
+  const cudaError_t e = g_launch_error;
+  g_launch_error = cudaSuccess;
+  return e;
+}
+
 void prof_end(int id, cudaStream_t s) {
   Profiler* p = g_active;
   if (!p || !p->on || p->open_id != id || p->open_ev == (size_t)-1) return;
@@ -392,7 +402,8 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
     launch_time_advance(B, st);
     launch_field_stats(B, st);
   }
-  return cudaGetLastError();
+  const cudaError_t le = take_launch_error();
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, int flexible, const mdbs_tuning& t) {

@@ -225,6 +225,9 @@ enum KernelId {
 extern const char* const kKernelNames[K_COUNT];
 void prof_begin(int id, cudaStream_t s);
 void prof_end(int id, cudaStream_t s);
+// the first error a kernel launch returned on this thread since the last take
+void set_launch_error(cudaError_t e);
+cudaError_t take_launch_error();
 long long launch_count();  // kernels launched so far by the active simulation
 
 //
@@ -254,7 +257,8 @@ long long launch_count();  // kernels launched so far by the active simulation
     at_[0].val.programmaticStreamSerializationAllowed = 1;                                         \
     cfg_.attrs = at_;                                                                              \
     cfg_.numAttrs = 1;                                                                             \
-    cudaLaunchKernelEx(&cfg_, KERNEL, __VA_ARGS__);                                                \
+    const cudaError_t le_ = cudaLaunchKernelEx(&cfg_, KERNEL, __VA_ARGS__);                        \
+    if (le_ != cudaSuccess) ::mdbs::set_launch_error(le_);                                         \
     ::mdbs::prof_end((ID), (STREAM));                                                              \
   } while (0)
 

@@ -2086,7 +2086,9 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     at[0].val.cooperative = 1;
     cfg.attrs = at;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_coarse_coop<R>, B.cg, cw, nu1, nu2, cs, smem > 0 ? 1 : 0, B.coop_ctr, B.err_flag);
+    const cudaError_t le =
+        cudaLaunchKernelEx(&cfg, k_coarse_coop<R>, B.cg, cw, nu1, nu2, cs, smem > 0 ? 1 : 0, B.coop_ctr, B.err_flag);
+    if (le != cudaSuccess) set_launch_error(le);
     prof_end(K_COOP, s);
   }
   const int ctas = B.tail_ctas;
@@ -2108,7 +2110,8 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
     at[1].val.clusterDim.z = 1;
     cfg.attrs = at;
     cfg.numAttrs = 2;
-    cudaLaunchKernelEx(&cfg, k_tail_vcycle<R>, B.cg, nu1, nu2, cs, tail_smem, ctas);
+    const cudaError_t le = cudaLaunchKernelEx(&cfg, k_tail_vcycle<R>, B.cg, nu1, nu2, cs, tail_smem, ctas);
+    if (le != cudaSuccess) set_launch_error(le);
     prof_end(K_TAIL, s);
   }
   for (int l = batched_end - 1; l >= 0; l--) {
@@ -2210,7 +2213,8 @@ cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, 
     }
   }
   MDBS_LAUNCH(K_FINALIZE, B.ndom, 32, s, k_record, B.sd, B.cg, corr, tol);
-  return cudaGetLastError();
+  const cudaError_t le = take_launch_error();
+  return le != cudaSuccess ? le : cudaGetLastError();
 }
 
 }  // namespace mdbs
