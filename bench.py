@@ -334,7 +334,9 @@ def vcycle_bytes(n, word, tuning, nu=(2, 2), bf16_coarse=False):
     per sweep; neighbours from cache).  Per level of N cells with word w (coefficients wt):
     split half sweeps -- one from a zero guess 1.5w, full ones 2w + 3wt, the first
     post-smoothing one also reads the coarse correction (+ w/8); fused pairs 4w + 3wt plus a
-    separate prolongation 2w + w/8; the residual restriction 3w + 3wt + w/8.  The coarsest
+    separate prolongation 2w + w/8; the residual restriction 2w + 3wt + w/8 (x of every
+    cell, b and diag of the colour-0 cells whose residual it forms, the face coefficients,
+    the coarse b).  The coarsest
     level's exact solve reads its dense inverse (N^2 words)."""
     levels = level_sizes(n)
     out = []
@@ -350,7 +352,7 @@ def vcycle_bytes(n, word, tuning, nu=(2, 2), bf16_coarse=False):
             b = (nu[0] + nu[1]) * (4 * w + 3 * wt) + 2 * w + w / 8
         else:
             b = 1.5 * w + (halves - 2) * (2 * w + 3 * wt) + (2 * w + 3 * wt + w / 8)
-        b += 3 * w + 3 * wt + w / 8
+        b += 2 * w + 3 * wt + w / 8
         out.append((N, b * N))
     return out
 
