@@ -757,9 +757,13 @@ static void level_diag(level_t* L) {
   }
 }
 
-/* Coarse transmissibilities: the fine rows crossing a coarse face are summed
- * (parallel); along a row, half of each coarse cell's interior fine link and
- * the fine face link are combined in series. */
+/* Coarse transmissibilities.  A coarse face link is the sum of the fine links
+ * that cross the face (the Galerkin coarse operator of piecewise-constant
+ * prolongation with its transpose as restriction), halved when the face's normal
+ * axis is coarsened: in a uniform medium the fine links crossing a face sum to
+ * k A_face / h, while the 2h link is k A_face / (2 h).  With every axis coarsened
+ * the coarse operator is half the Galerkin operator, i.e. the coarse correction
+ * is doubled. */
 static void coarsen_coeffs(const level_t* F, level_t* C) {
   for (long ci = 0; ci < C->cells; ci++) {
     int Q[3];
@@ -777,32 +781,17 @@ static void coarsen_coeffs(const level_t* F, level_t* C) {
         lo[a] = C->cz[a] ? 2 * Q[a] : Q[a];
         hi[a] = C->cz[a] ? (2 * Q[a] + 1 < F->n[a] ? 2 * Q[a] + 1 : 2 * Q[a]) : Q[a];
       }
-      lo[d] = hi[d] = 0;
+      /* the fine link across the coarse face: from the last fine cell of coarse
+       * cell Q to the first of coarse cell Q + 1 */
+      lo[d] = hi[d] = C->cz[d] ? 2 * Q[d] + 1 : Q[d];
       double sum = 0.0;
       for (int z = lo[2]; z <= hi[2]; z++)
         for (int y = lo[1]; y <= hi[1]; y++)
           for (int x = lo[0]; x <= hi[0]; x++) {
             int fc[3] = {x, y, z};
-            double inv;
-            if (C->cz[d]) {
-              int a0[3], a1[3], a2[3];
-              cpy3(a0, fc);
-              cpy3(a1, fc);
-              cpy3(a2, fc);
-              a0[d] = 2 * Q[d];     /* interior link of the left coarse cell */
-              a1[d] = 2 * Q[d] + 1; /* link across the coarse face */
-              a2[d] = 2 * Q[d] + 2; /* interior link of the right coarse cell */
-              inv = 1.0 / Tf[cid3(F->n, a1)] + 1.0 / (2.0 * Tf[cid3(F->n, a0)]);
-              if (2 * Q[d] + 3 < F->n[d]) inv += 1.0 / (2.0 * Tf[cid3(F->n, a2)]);
-            } else {
-              int a1[3];
-              cpy3(a1, fc);
-              a1[d] = Q[d];
-              inv = 1.0 / Tf[cid3(F->n, a1)];
-            }
-            sum += 1.0 / inv;
+            sum += Tf[cid3(F->n, fc)];
           }
-      Tc[ci] = sum;
+      Tc[ci] = C->cz[d] ? 0.5 * sum : sum;
     }
   }
   /* Dirichlet (outlet) diagonal: half the sum over the covered fine cells */

@@ -1,7 +1,7 @@
 // pressure.cu -- pressure equation of the PISO corrector (Eq. 53) on sm_103a:
 // assembly of the 7-point (5-point in 2-D) variable-coefficient operator,
 // geometric multigrid V-cycle (red-black Gauss-Seidel, cell-centred 2:1
-// coarsening with series/parallel transmissibilities) and preconditioned CG in
+// coarsening with halved Galerkin transmissibilities) and preconditioned CG in
 // FP64 with deterministic block reductions.  In mixed precision the V-cycle
 // runs in FP32 inside a flexible (Polak-Ribiere) FP64 CG.  Every kernel runs over
 // all domains of a batch (see mdbs_internal.cuh); per-domain CG scalars and
@@ -230,8 +230,9 @@ __global__ void k_level0_to_float(const CgDom* __restrict__ C, Work w) {
   }
 }
 
-// coarse transmissibilities: fine rows across a coarse face in parallel, along a
-// row half of each coarse cell's interior link and the crossing link in series
+// coarse transmissibilities: the sum of the fine links crossing the coarse face
+// (the Galerkin operator of piecewise-constant transfer), halved when the face's
+// normal axis is coarsened, where the 2h link spans twice the fine distance
 template <typename R>
 __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co, long long ci) {
   int Q[3];
@@ -247,30 +248,12 @@ __device__ __forceinline__ void b_coarsen(const Level<R>& Fi, const Level<R>& Co
       continue;
     }
     int rl[3] = {lo[0], lo[1], lo[2]}, rh[3] = {hi[0], hi[1], hi[2]};
-    rl[d] = rh[d] = 0;
+    rl[d] = rh[d] = Co.cz[d] ? 2 * Q[d] + 1 : Q[d];  // last fine cell of coarse cell Q
     R sum = R(0);
     for (int z = rl[2]; z <= rh[2]; z++)
       for (int y = rl[1]; y <= rh[1]; y++)
-        for (int x = rl[0]; x <= rh[0]; x++) {
-          int fc[3] = {x, y, z};
-          R inv;
-          if (Co.cz[d]) {
-            fc[d] = 2 * Q[d] + 1;
-            const R tface = tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
-            fc[d] = 2 * Q[d];
-            const R tin_l = tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
-            inv = R(1) / tface + R(1) / (R(2) * tin_l);
-            if (2 * Q[d] + 3 < Fi.n[d]) {
-              fc[d] = 2 * Q[d] + 2;
-              inv += R(1) / (R(2) * tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2])));
-            }
-          } else {
-            fc[d] = Q[d];
-            inv = R(1) / tcoef(Fi, d, (unsigned)lpos(Fi.n, fc[0], fc[1], fc[2]));
-          }
-          sum += R(1) / inv;
-        }
-    tstore(Co, d, (unsigned)ci, sum);
+        for (int x = rl[0]; x <= rh[0]; x++) sum += tcoef(Fi, d, (unsigned)lpos(Fi.n, x, y, z));
+    tstore(Co, d, (unsigned)ci, Co.cz[d] ? R(0.5) * sum : sum);
   }
   R dd = R(0);
   for (int z = lo[2]; z <= hi[2]; z++)
