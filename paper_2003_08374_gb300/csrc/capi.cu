@@ -116,6 +116,8 @@ struct Exec {
   BatchPlan plan{};
   bool planned = false;
   cudaStream_t cap_stream = nullptr, body_stream = nullptr;
+  cudaStream_t side_stream = nullptr;               // the pressure operator's branch of the step graph
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;  // its fork from and join to the main branch
   cudaGraphExec_t graph = nullptr;
   long long static_launches = 0;  // kernels outside the CG loops per step
   long long body_launches = 0;    // kernels per CG iteration
@@ -278,6 +280,8 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
     F.B[d] = fd();
     F.hbya[d] = fd();
     F.utmp[d] = fd();
+    F.iphif[d] = fd();
+    F.gphi[d] = (double*)take(3 * nf * 8);
   }
   const long long faces = L.nf[0] + L.nf[1] + (L.dim == 3 ? L.nf[2] : 0);
   const long long pcap = (std::max(L.cells, faces) + kBlock * kRepBig - 1) / (kBlock * kRepBig);
@@ -381,16 +385,35 @@ cudaError_t record_step(Exec& ex, const mdbs_options& opt, cudaStream_t st, bool
     launch_properties(B, st);
   }
   {
-    // 4. momentum predictor (Eq. 50) from u^k and p^k
+    // 4. momentum predictor (Eq. 50) from u^k and p^k.  The pressure operator of
+    // Eq. 53 depends on a_P alone: in the step graph it is assembled, with its
+    // multigrid hierarchy, on a side branch while the Jacobi sweeps run, and joins
+    // before the first pressure solve (eager steps run it in line).
     Phase ph("momentum predictor (Eq. 50)");
     launch_momentum_assemble(B, st);
+    cudaStream_t ms = st;
+    if (capture) {
+      cudaError_t e = cudaEventRecord(ex.ev_fork, st);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ex.side_stream, ex.ev_fork, 0);
+      if (e != cudaSuccess) return e;
+      ms = ex.side_stream;
+    }
+    launch_pressure_matrix(B, opt.mg_coarse_sweeps, ms);
+    if (capture) {
+      const cudaError_t e = cudaEventRecord(ex.ev_join, ms);
+      if (e != cudaSuccess) return e;
+    }
     launch_jacobi_sweeps(B, opt.mom_sweeps, st);
   }
   // 5. PISO correctors (Eqs. 51-53)
   for (int c = 0; c < opt.n_corr; c++) {
     Phase ph("PISO corrector (Eqs. 51-53)");
     launch_hbya(B, st);
-    launch_pressure_assemble(B, st);
+    launch_pressure_rhs(B, st);
+    if (capture && c == 0) {
+      const cudaError_t e = cudaStreamWaitEvent(st, ex.ev_join, 0);
+      if (e != cudaSuccess) return e;
+    }
     cudaError_t e = pressure_solve(B, opt.p_tol, opt.max_cg, opt.mg_nu1, opt.mg_nu2, opt.mg_coarse_sweeps, c,
                                    capture, st, ex.body_stream, ex.host_flag, &ex.body_launches);
     if (e != cudaSuccess) return e;
@@ -414,6 +437,9 @@ cudaError_t exec_setup(Exec& ex, const StepDom* sd, const CgDom* cg, int ndom, i
   ex.planned = true;
   if (!ex.cap_stream) e = cudaStreamCreateWithFlags(&ex.cap_stream, cudaStreamNonBlocking);
   if (e == cudaSuccess && !ex.body_stream) e = cudaStreamCreateWithFlags(&ex.body_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ex.side_stream) e = cudaStreamCreateWithFlags(&ex.side_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess && !ex.ev_fork) e = cudaEventCreateWithFlags(&ex.ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess && !ex.ev_join) e = cudaEventCreateWithFlags(&ex.ev_join, cudaEventDisableTiming);
   if (e == cudaSuccess && !ex.host_flag) e = cudaMallocHost(&ex.host_flag, sizeof(double));
   return e;
 }
@@ -423,6 +449,9 @@ void exec_destroy(Exec& ex) {
   if (ex.planned) plan_destroy(&ex.plan);
   if (ex.cap_stream) cudaStreamDestroy(ex.cap_stream);
   if (ex.body_stream) cudaStreamDestroy(ex.body_stream);
+  if (ex.side_stream) cudaStreamDestroy(ex.side_stream);
+  if (ex.ev_fork) cudaEventDestroy(ex.ev_fork);
+  if (ex.ev_join) cudaEventDestroy(ex.ev_join);
   if (ex.host_flag) cudaFreeHost(ex.host_flag);
   ex = Exec{};
 }

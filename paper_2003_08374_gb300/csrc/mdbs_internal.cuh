@@ -72,6 +72,8 @@ struct Fld {
   const uint8_t* is_free;
   const double* nw[3];  // wall normal (zero outside contact cells)
   const double* iphi2;  // phi^-2 (porosity-gradient part of the convection)
+  const double* iphif[3];  // 1 / phi_f, phi_f the mean porosity of a face's two cells
+  const double* gphi[3];   // grad(phi^-2) at a face: component e of direction-d faces at e * nf[d] + f
   // state
   double* alpha;
   double* p;
@@ -338,7 +340,9 @@ void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom
 void pressure_storage(const PressureSolver* ps, void** ptr, size_t* bytes);
 constexpr int kTailCellsMax = 262144;
 int pressure_precision(const PressureSolver* ps);
-void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s);
+constexpr int kAsmMatrix = 1, kAsmRhs = 2;
+void launch_pressure_matrix(const BatchPlan& B, int coarse_sweeps, cudaStream_t s);
+void launch_pressure_rhs(const BatchPlan& B, cudaStream_t s);
 // Enqueues the solve of A p = b for every domain of the batch by GMG-preconditioned
 // CG.  Iterations and the final relative residual of corrector `corr` go to each
 // domain's step scalars.  capture == false: the CG loop is driven from the host

@@ -141,20 +141,22 @@ constexpr int kBB = 0, kRR = 1, kRZ = 2, kDQ = 3, kZQ = 4, kAlpha = 5, kCond = 6
 // T_f = A^2 / a_P,f between cells, 2 A^2 / a_P,f on outlet faces (Dirichlet
 // through the ghost p_ghost = -p), b = -sum_f s_f A ubar_f with ubar = HbyA on
 // unknown faces and the fixed velocity on wall / inlet faces.
-__device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long c) {
+// what: kAsmMatrix (coefficients T, Dd) and / or kAsmRhs (right-hand side b)
+__device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long c, int what) {
+  const bool matrix = what & kAsmMatrix;
   int q[3];
   decode_pos(P, c, q[0], q[1], q[2]);  // c: storage position of the cell
   const double A = P.A, A2 = P.A * P.A;
   double div = 0.0, Dd = 0.0;
   for (int d = 0; d < 3; d++) {
     if (d >= P.dim) {
-      F.T[d][c] = 0.0;
+      if (matrix) F.T[d][c] = 0.0;
       continue;
     }
     const int di = (d == 0), dj = (d == 1), dk = (d == 2);
     const long long flo = face_index(P.n, d, q[0], q[1], q[2]);
     const long long fhi = face_index(P.n, d, q[0] + di, q[1] + dj, q[2] + dk);
-    F.T[d][c] = (q[d] + 1 < P.n[d]) ? A2 * F.aP[d][fhi] : 0.0;  // aP holds 1 / a_P
+    if (matrix) F.T[d][c] = (q[d] + 1 < P.n[d]) ? A2 * F.aP[d][fhi] : 0.0;  // aP holds 1 / a_P
     const bool lo_bnd = q[d] == 0, hi_bnd = q[d] + 1 == P.n[d];
     if (lo_bnd && P.bc[2 * d] == kOutlet) Dd += 2.0 * A2 * F.aP[d][flo];
     if (hi_bnd && P.bc[2 * d + 1] == kOutlet) Dd += 2.0 * A2 * F.aP[d][fhi];
@@ -164,17 +166,17 @@ __device__ __forceinline__ void b_assemble(const Prm& P, const Fld& F, long long
     const double uhi = hi_fixed ? F.u[d][fhi] : F.hbya[d][fhi];
     div += A * uhi - A * ulo;
   }
-  F.Dd[c] = Dd;
-  F.b[c] = -div;
+  if (matrix) F.Dd[c] = Dd;
+  if (what & kAsmRhs) F.b[c] = -div;
 }
 
-__global__ void k_assemble(const StepDom* __restrict__ D, Work w) {
+__global__ void k_assemble(const StepDom* __restrict__ D, Work w, int what) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK(w)
     const StepDom& S = D[dm];
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < S.P.cells) b_assemble(S.P, S.F, c);
+      if (c < S.P.cells) b_assemble(S.P, S.F, c, what);
     }
   }
 }
@@ -983,22 +985,42 @@ __global__ void k_coarse_inverse(const CgDom* __restrict__ CG) {
       }
     }
   }
+  // Gauss-Jordan elimination without pivoting (the matrix is symmetric positive
+  // definite).  Each thread keeps the (row, column) of its entries (the launch has
+  // 1024 threads); per pivot every thread reads what its entries need, a barrier,
+  // all write, a barrier.  The thread that owns the next diagonal entry forms that
+  // pivot's reciprocal from its new value before the first barrier (double buffered:
+  // one FP64 division a pivot).
+  constexpr int kPer = (kCoarseMax * kCoarseMax + 1023) / 1024;
+  __shared__ R piv[2];
+  int ei[kPer], ej[kPer];
+  for (int t = 0; t < kPer; t++) {
+    const int e = threadIdx.x + t * blockDim.x;
+    ei[t] = e < n * n ? e / n : -1;
+    ej[t] = e < n * n ? e - ei[t] * n : -1;
+  }
+  if (threadIdx.x == 0) piv[0] = R(1) / M[0];
   __syncthreads();
   for (int k = 0; k < n; k++) {
-    const R pinv = R(1) / M[k * n + k];
-    __syncthreads();
-    for (int j = threadIdx.x; j < n; j += blockDim.x)
-      if (j != k) M[k * n + j] *= pinv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
-      const int i = e / n, j = e % n;
-      if (i != k && j != k) M[e] -= M[i * n + k] * M[k * n + j];
+    const R pinv = piv[k & 1];
+    R nv[kPer];
+    for (int t = 0; t < kPer; t++) {
+      const int i = ei[t], j = ej[t];
+      if (i < 0) continue;
+      if (i == k && j == k)
+        nv[t] = pinv;
+      else if (i == k)
+        nv[t] = M[k * n + j] * pinv;
+      else if (j == k)
+        nv[t] = -M[i * n + k] * pinv;
+      else
+        nv[t] = M[i * n + j] - M[i * n + k] * (M[k * n + j] * pinv);
+      if (i == k + 1 && j == k + 1) piv[(k + 1) & 1] = R(1) / nv[t];
     }
-    __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x)
-      if (i != k) M[i * n + k] = -M[i * n + k] * pinv;
-    if (threadIdx.x == 0) M[k * n + k] = pinv;
-    __syncthreads();
+    __syncthreads();  // every read of this pivot's step is done
+    for (int t = 0; t < kPer; t++)
+      if (ei[t] >= 0) M[ei[t] * n + ej[t]] = nv[t];
+    __syncthreads();  // the step's writes (and the next reciprocal) are visible
   }
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
     const int i = e / n, j = e % n;
@@ -1956,11 +1978,6 @@ void pressure_view(const PressureSolver* ps, const Fld& F, int tail_cells, CgDom
 }
 
 // ------------------------------------------------------------------ batched host sequencing
-void launch_pressure_assemble(const BatchPlan& B, cudaStream_t s) {
-  MDBS_LAUNCH(K_ASSEMBLE, grid_of(B, B.cells), kBlock, s, k_assemble, B.sd, B.cells);
-  MDBS_LAUNCH(K_DIAG, grid_of(B, B.cells), kBlock, s, k_diag<double>, B.cg, B.cells, 0);
-}
-
 template <typename R>
 static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
   for (int l = 1; l < B.max_levels; l++) {
@@ -1968,6 +1985,25 @@ static void build_hierarchy(const BatchPlan& B, bool direct, cudaStream_t s) {
     MDBS_LAUNCH(K_DIAG, grid_of(B, B.lcells[l]), kBlock, s, k_diag<R>, B.cg, B.lcells[l], l);
   }
   if (direct) MDBS_LAUNCH(K_COARSEN, B.ndom, 1024, s, k_coarse_inverse<R>, B.cg);
+}
+
+// The operator depends on a_P alone, which the correctors of one step share:
+// launch_pressure_matrix assembles it once per step and builds the multigrid
+// hierarchy (and the coarsest inverse); each corrector then assembles only its
+// right-hand side from its HbyA.
+void launch_pressure_matrix(const BatchPlan& B, int coarse_sweeps, cudaStream_t s) {
+  MDBS_LAUNCH(K_ASSEMBLE, grid_of(B, B.cells), kBlock, s, k_assemble, B.sd, B.cells, (int)kAsmMatrix);
+  MDBS_LAUNCH(K_DIAG, grid_of(B, B.cells), kBlock, s, k_diag<double>, B.cg, B.cells, 0);
+  if (!B.flexible) {
+    build_hierarchy<double>(B, coarse_sweeps == 0, s);
+  } else {
+    MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, s, k_level0_to_float, B.cg, B.cells);
+    build_hierarchy<float>(B, coarse_sweeps == 0, s);
+  }
+}
+
+void launch_pressure_rhs(const BatchPlan& B, cudaStream_t s) {
+  MDBS_LAUNCH(K_ASSEMBLE, grid_of(B, B.cells), kBlock, s, k_assemble, B.sd, B.cells, (int)kAsmRhs);
 }
 
 // Traversal direction of the next kernel over each level; flips at every launch
@@ -2120,14 +2156,7 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
 cudaError_t pressure_solve(const BatchPlan& B, double tol, int max_it, int nu1, int nu2, int cs, int corr,
                            bool capture, cudaStream_t s, cudaStream_t body_stream, double* host_flag,
                            long long* body_launches) {
-  const int flexible = B.flexible;
-  // hierarchy for this assembly
-  if (!flexible) {
-    build_hierarchy<double>(B, cs == 0, s);
-  } else {
-    MDBS_LAUNCH(K_CONVERT, grid_of(B, B.cells), kBlock, s, k_level0_to_float, B.cg, B.cells);
-    build_hierarchy<float>(B, cs == 0, s);
-  }
+  const int flexible = B.flexible;  // the hierarchy comes from launch_pressure_matrix
   cudaGraphConditionalHandle handle = 0;
   cudaGraph_t graph = nullptr;
   if (capture) {

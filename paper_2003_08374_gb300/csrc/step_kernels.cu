@@ -400,7 +400,15 @@ __device__ __forceinline__ void b_curvature(const Prm& P, const Fld& F, long lon
 // Euler term is taken in advective form, rho^{k+1} (v^{k+1} - v^k) / dt, like
 // the convection: the conservative form would need momentum fluxes consistent
 // with the saturation fluxes.
-__device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, long long t, double dt) {
+// max(w, 0) and max(-w, 0) from the sign bit: integer selects instead of FP64
+// compares (GB300 runs FP64 compares on its narrow FP64 pipe)
+__device__ __forceinline__ void split_sign(double w, double& pos, double& neg) {
+  const long long wb = __double_as_longlong(w);
+  pos = wb < 0 ? 0.0 : w;
+  neg = wb < 0 ? __longlong_as_double(wb ^ (long long)0x8000000000000000ull) : 0.0;
+}
+
+__device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, long long t, double inv_dt) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
@@ -408,16 +416,16 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   const int di = (d == 0), dj = (d == 1), dk = (d == 2);
   const int cd = d == 0 ? i : (d == 1 ? j : k);
   const int kind = face_kind(P, d, cd);
-  for (int s = 0; s < 6; s++) F.anb[d][s * nf + f] = 0.0;
+  double* __restrict__ anb = F.anb[d] + f;
   if (kind == 1) {
+    for (int s = 0; s < 6; s++) anb[s * nf] = 0.0;
     F.aP[d][f] = 1.0;
     F.rhs0[d][f] = 0.0;
     F.B[d][f] = 0.0;
     return;
   }
   const int li = i - di, lj = j - dj, lk = k - dk;  // low cell (may be a ghost at an outlet)
-  const double h = P.h, A = P.A, V = P.V;
-  const double phif = 0.5 * (ghost_read(F.phi, P.n, li, lj, lk) + ghost_read(F.phi, P.n, i, j, k));
+  const double h = P.h, V = P.V;
   const double rhof = 0.5 * (ghost_read(F.rho, P.n, li, lj, lk) + ghost_read(F.rho, P.n, i, j, k));
   const double Df = 0.5 * (ghost_read(F.drag, P.n, li, lj, lk) + ghost_read(F.drag, P.n, i, j, k));
   const double muL = ghost_read(F.mu, P.n, li, lj, lk), muR = ghost_read(F.mu, P.n, i, j, k);
@@ -435,15 +443,15 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   }
   F.B[d][f] = Bf;
   const double uf = F.u[d][f];
-  const double inv_phidt = 1.0 / (phif * dt);
-  const double inv_phi = 1.0 / phif;
+  const double inv_phi = F.iphif[d][f];  // 1 / phi_f (static)
   const double inv_h = P.inv_h;
-  const double at = V * rhof * inv_phidt;
+  const double at = V * rhof * (inv_phi * inv_dt);
   const double S = at * uf;  // advective form rho^{k+1} (v^{k+1} - v^k) / dt
   const double cconv = V * rhof * inv_phi * inv_phi * inv_h;
   double ap = at + V * Df;
   double tt = 0.0;
   double vgrad = 0.0;  // v . grad(phi^-2) at the face
+  const double* __restrict__ gph = F.gphi[d] + f;
   for (int e = 0; e < P.dim; e++) {
     const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
     // e-velocities on the low / high e-faces of the (clamped) low and high cells
@@ -457,17 +465,10 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       vRhi = F.u[e][face_index(P.n, e, ri + ei, rj + ej, rk + ek)];
     }
     const double w = (e == d) ? uf : 0.25 * (vLlo + vLhi + vRlo + vRhi);
-    // e-derivative of phi^-2 at the face: across it (e == d), or the mean of the two
-    // cells' central differences (e != d)
-    if (e == d) {
-      vgrad += w * ((ghost_read(F.iphi2, P.n, i, j, k) - ghost_read(F.iphi2, P.n, li, lj, lk)) * inv_h);
-    } else {
-      const double gL = ghost_read(F.iphi2, P.n, li + ei, lj + ej, lk + ek) -
-                        ghost_read(F.iphi2, P.n, li - ei, lj - ej, lk - ek);
-      const double gR = ghost_read(F.iphi2, P.n, i + ei, j + ej, k + ek) -
-                        ghost_read(F.iphi2, P.n, i - ei, j - ej, k - ek);
-      vgrad += w * ((gL + gR) * (0.25 * inv_h));
-    }
+    vgrad += w * gph[e * nf];
+    double wpos, wneg;
+    split_sign(w, wpos, wneg);
+    double muE[2] = {0.0, 0.0};  // edge viscosities of the two e-sides (e != d)
     for (int sg = -1; sg <= 1; sg += 2) {
       const int slot = 2 * e + (sg > 0);
       const int ce = (e == 0 ? i : (e == 1 ? j : k)) + sg;
@@ -478,21 +479,21 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
         status = 0;
       else
         status = P.bc[2 * e + (sg > 0)] == kOutlet ? 2 : 1;
-      const double cup = cconv * (sg < 0 ? fmax(w, 0.0) : fmax(-w, 0.0));
+      const double cup = cconv * (sg < 0 ? wpos : wneg);
       double mus;
       if (e == d) {
         mus = sg < 0 ? muL : muR;
       } else {
         mus = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
                       ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
+        muE[sg > 0] = mus;
       }
       const double a = cup + mus * h;  // mu A / h with A = h^2
-      if (status == 0) {
-        F.anb[d][slot * nf + f] = a;
+      anb[slot * nf] = status == 0 ? a : 0.0;
+      if (status == 0)
         ap += a;
-      } else if (status == 1) {
+      else if (status == 1)
         ap += 2.0 * a;
-      }
     }
     // explicit div(mu grad(u)^T), component d
     if (e == d) {
@@ -501,22 +502,19 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       tt += (muR * dR - muL * dL) * inv_h;
     } else {
       double ts = 0.0;
-      for (int sg = -1; sg <= 1; sg += 2) {
-        const double muE = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
-                                   ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
-        const double der = sg > 0 ? (vRhi - vLhi) * inv_h : (vRlo - vLlo) * inv_h;
-        ts += sg > 0 ? muE * der : -muE * der;
-      }
+      ts -= muE[0] * ((vRlo - vLlo) * inv_h);
+      ts += muE[1] * ((vRhi - vLhi) * inv_h);
       tt += ts * inv_h;
     }
   }
+  for (int s = 2 * P.dim; s < 6; s++) anb[s * nf] = 0.0;
   // The rest of Eq. 21's convection: with div v = 0 and the density carried by the
   // flow, (1/phi) div(rho v v / phi) minus the advective part above is
   // (rho/2) v (v . grad(phi^-2)), non-zero only where the porosity varies along the
   // flow; implicit where it decelerates the flow, explicit where it accelerates it.
   const double Gp = 0.5 * rhof * vgrad;
   double Sx = S;
-  if (Gp >= 0.0)
+  if (__double_as_longlong(Gp) >= 0)  // Gp >= 0 (+0 and -0 add nothing either way)
     ap += V * Gp;
   else
     Sx -= V * Gp * uf;
@@ -524,17 +522,22 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   F.rhs0[d][f] = Sx + V * (tt + Bf);
 }
 
-// H(u) = sum_nb a_nb u_nb + rhs0 of an unknown face
-__device__ __forceinline__ double face_H(const Prm& P, const Fld& F, const double* const* u, int d, int i, int j,
-                                         int k, long long f) {
+// H(u) = sum_nb a_nb u_nb + rhs0 of an unknown face.  A missing neighbour has
+// a_nb = 0: its product is formed with the face's own value (a flat index clamped
+// into the array), which adds exactly zero for finite velocities, so the sum needs
+// no FP64 compare per neighbour.
+__device__ __forceinline__ double face_H(const Prm& P, const Fld& F, const double* const* u, int d, long long f) {
   const long long nf = P.nf[d];
+  const long long fx = P.n[0] + (d == 0), fxy = fx * (P.n[1] + (d == 1));
+  const double* __restrict__ ud = u[d];
   double hs = 0.0;
   for (int e = 0; e < P.dim; e++) {
-    const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
+    const long long st = e == 0 ? 1 : (e == 1 ? fx : fxy);
     const double am = F.anb[d][(2 * e) * nf + f];
     const double ap = F.anb[d][(2 * e + 1) * nf + f];
-    if (am != 0.0) hs += am * u[d][face_index(P.n, d, i - ei, j - ej, k - ek)];
-    if (ap != 0.0) hs += ap * u[d][face_index(P.n, d, i + ei, j + ej, k + ek)];
+    const long long fm = f - st >= 0 ? f - st : f, fp = f + st < nf ? f + st : f;
+    hs += am * ud[fm];
+    hs += ap * ud[fp];
   }
   return hs + F.rhs0[d][f];
 }
@@ -564,7 +567,7 @@ __device__ __forceinline__ void b_jacobi(const Prm& P, const Fld& F, long long t
     return;
   }
   const double* u[3] = {in.a[0], in.a[1], in.a[2]};
-  const double hs = face_H(P, F, u, d, i, j, k, f);
+  const double hs = face_H(P, F, u, d, f);
   out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) * F.aP[d][f];  // V/h = A; aP = 1/a_P
 }
 
@@ -595,7 +598,7 @@ __device__ __forceinline__ void b_hbya(const Prm& P, const Fld& F, long long t) 
     return;
   }
   const double* u[3] = {F.u[0], F.u[1], F.u[2]};
-  F.hbya[d][f] = face_H(P, F, u, d, i, j, k, f) * F.aP[d][f];
+  F.hbya[d][f] = face_H(P, F, u, d, f) * F.aP[d][f];
 }
 
 // corrected velocity, Eq. 51
@@ -788,6 +791,48 @@ __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
   }
 }
 
+// Static face data of the momentum equation (the porosity never changes): 1 / phi_f
+// with phi_f the mean of the face's two cells, and grad(phi^-2) at the face --
+// across it along its own axis, the mean of the two cells' central differences
+// along the others (zero components beyond the grid's dimension).
+__device__ __forceinline__ void b_static_faces(const Prm& P, const Fld& F, long long t) {
+  int d, i, j, k;
+  long long f;
+  if (!decode_face(P, t, d, i, j, k, f)) return;
+  const long long nf = P.nf[d];
+  const int li = i - (d == 0), lj = j - (d == 1), lk = k - (d == 2);
+  const double phif = 0.5 * (ghost_read(F.phi, P.n, li, lj, lk) + ghost_read(F.phi, P.n, i, j, k));
+  const_cast<double*>(F.iphif[d])[f] = 1.0 / phif;
+  const double inv_h = P.inv_h;
+  for (int e = 0; e < 3; e++) {
+    const int ei = (e == 0), ej = (e == 1), ek = (e == 2);
+    double g = 0.0;
+    if (e == d) {
+      g = (ghost_read(F.iphi2, P.n, i, j, k) - ghost_read(F.iphi2, P.n, li, lj, lk)) * inv_h;
+    } else if (e < P.dim) {
+      const double gL = ghost_read(F.iphi2, P.n, li + ei, lj + ej, lk + ek) -
+                        ghost_read(F.iphi2, P.n, li - ei, lj - ej, lk - ek);
+      const double gR = ghost_read(F.iphi2, P.n, i + ei, j + ej, k + ek) -
+                        ghost_read(F.iphi2, P.n, i - ei, j - ej, k - ek);
+      g = (gL + gR) * (0.25 * inv_h);
+    }
+    const_cast<double*>(F.gphi[d])[e * nf + f] = g;
+  }
+}
+
+__global__ void k_static_faces(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (t < total_faces(S.P)) b_static_faces(S.P, S.F, t);
+    }
+  }
+}
+
 // ------------------------------------------------------------------ batched entry points
 __global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
@@ -869,13 +914,18 @@ __global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
 
 __global__ void k_momentum_assemble(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
+  __shared__ double s_inv_dt;  // one FP64 division per block, not per face
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
+    __syncthreads();  // the previous item's readers are done
+    if (threadIdx.x == 0) s_inv_dt = 1.0 / S.scal[kSlotDt];
+    __syncthreads();
+    const double inv_dt = s_inv_dt;
     for (int r = 0; r < w.rep; r++) {
       const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (t < total_faces(S.P)) b_momentum_assemble(S.P, S.F, t, S.scal[kSlotDt]);
+      if (t < total_faces(S.P)) b_momentum_assemble(S.P, S.F, t, inv_dt);
     }
   }
 }
@@ -984,6 +1034,9 @@ void launch_time_advance(const BatchPlan& B, cudaStream_t s) {
   MDBS_LAUNCH(K_FINALIZE, B.ndom, 1024, s, k_finalize_time, B.sd, B.rfaces);
 }
 
-void launch_static_geometry(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_STATIC, cells, k_static_geometry); }
+void launch_static_geometry(const BatchPlan& B, cudaStream_t s) {
+  BATCH_LAUNCH(K_STATIC, cells, k_static_geometry);
+  BATCH_LAUNCH(K_STATIC, faces, k_static_faces);  // reads phi^-2 of the cells
+}
 
 }  // namespace mdbs
