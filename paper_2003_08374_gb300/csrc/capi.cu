@@ -784,6 +784,11 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.c_alpha = op->c_alpha;
   P.inv_h = 1.0 / grid->h;
   P.half_inv_h = 0.5 / grid->h;
+  P.inv_mu_l = 1.0 / P.mu_l;
+  P.inv_mu_g = 1.0 / P.mu_g;
+  P.inv_ae_den = 1.0 / (1.0 - P.a_g_irr - P.a_l_irr);
+  P.inv_s_den = 1.0 / (P.a_pc_max - P.a_pc_irr);
+  P.reg_m = 1e-8 / grid->h;
   P.kr_m_int = (cl->kr_m >= 1.0 && cl->kr_m <= 8.0 && cl->kr_m == floor(cl->kr_m)) ? (int)cl->kr_m : 0;
   P.cfl = op->cfl;
   P.dt_max = op->dt_max;

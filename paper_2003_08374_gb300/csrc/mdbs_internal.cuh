@@ -58,6 +58,11 @@ struct Prm {
   double cos_t, sin_t;  // contact angle
   double c_alpha;
   double inv_h, half_inv_h;  // 1/h and 1/(2h)
+  // reciprocals of run-time constants (the kernels multiply; GB300's FP64 division is slow)
+  double inv_mu_l, inv_mu_g;  // 1/mu_l, 1/mu_g
+  double inv_ae_den;          // 1/(1 - a_g_irr - a_l_irr), effective saturation
+  double inv_s_den;           // 1/(a_pc_max - a_pc_irr), capillary saturation
+  double reg_m;               // 1e-8/h, regularisation of |grad alpha| in the interface normal
   int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
   double cfl, dt_max;        // adaptive time step (cfl > 0)
   FastDiv dn0, dn1;          // division by n[0] and by n[1]

@@ -70,6 +70,26 @@ __device__ __forceinline__ double warp_reduce_max(double v) {
   return v;
 }
 
+// Sign and order tests of doubles on the integer pipe (GB300 runs FP64 compares
+// and min / max on its narrow FP64 pipe).  For finite values: ge0 is x >= 0 with
+// -0 counted negative, ge0z is x >= 0, gt0 is x > 0, nz is x != 0; okey maps a double to an int64
+// whose signed order is the IEEE order (-0 just below +0), so min / max of keys
+// select the same value as fmin / fmax.
+__device__ __forceinline__ bool ge0(double x) { return __double_as_longlong(x) >= 0; }
+__device__ __forceinline__ bool gt0(double x) { return __double_as_longlong(x) > 0; }
+__device__ __forceinline__ bool ge0z(double x) {  // x >= 0 exactly as IEEE (-0 included)
+  const long long b = __double_as_longlong(x);
+  return b >= 0 || b == (long long)0x8000000000000000ull;
+}
+__device__ __forceinline__ bool nz(double x) { return (__double_as_longlong(x) << 1) != 0; }
+__device__ __forceinline__ long long okey(double x) {
+  const long long b = __double_as_longlong(x);
+  return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+__device__ __forceinline__ double from_okey(long long k) { return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffll)); }
+__device__ __forceinline__ long long kmax2(long long a, long long b) { return a > b ? a : b; }
+__device__ __forceinline__ long long kmin2(long long a, long long b) { return a < b ? a : b; }
+
 
 // ------------------------------------------------------------------ saturation
 // Van Leer limited face value (section 3.1): aU + (1/2) psi(r) (aD - aU) with
@@ -81,7 +101,7 @@ __device__ __forceinline__ double van_leer(double aU, double aD, double aUU) {
   const double ga = aU - aUU, gb = aD - aU;
   const double ab = ga * gb;
   double v = aU;
-  if (ab > 0.0) v = aU + ab / (ga + gb);
+  if (gt0(ab)) v = aU + ab / (ga + gb);
   return v;
 }
 
@@ -115,7 +135,7 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
       const long long r = cell_index(P.n, i, j, k);
       const double al = F.alpha[l], ar = F.alpha[r];
       // upwind, downwind and second-upwind cells (the last clamped into the grid)
-      const bool pos = Q >= 0.0;
+      const bool pos = ge0z(Q);
       const long long uc = pos ? l : r, dc = pos ? r : l;
       const int s2 = pos ? -2 : 1;
       const long long uu = cell_index(P.n, clampi(i + s2 * di, 0, P.n[0] - 1), clampi(j + s2 * dj, 0, P.n[1] - 1),
@@ -130,12 +150,12 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
         const double fvl = van_leer(frac_flow(F, uc), frac_flow(F, dc), frac_flow(F, uu));
         const double drive = (P.rho_l - P.rho_g) * P.g[d] + (F.pc[r] - F.pc[l]) * inv_h;
         hi = Q * fvl;
-        if (drive != 0.0) {
+        if (nz(drive)) {
           // liquid from the cell the drive pushes it out of, gas from the other
-          const bool fwd = drive >= 0.0;
+          const bool fwd = ge0(drive);
           const double mlw = fwd ? F.Ml[l] : F.Ml[r], mgw = fwd ? F.Mg[r] : F.Mg[l];
-          const double msum = mlw + mgw;
-          if (msum > 0.0) hi += P.A * (mlw * mgw / msum) * drive;
+          const double msum = mlw + mgw;  // mobilities are >= 0
+          if (gt0(msum)) hi += P.A * (mlw * mgw / msum) * drive;
         }
       } else {
         double rel = 0.0;
@@ -146,7 +166,7 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
           const double mag = sqrt(gf[0] * gf[0] + gf[1] * gf[1] + gf[2] * gf[2]);
           const double nfc = gf[d] / (mag + 1e-8 * inv_h);
           const double w = P.c_alpha * fabs(uf) * nfc * P.A;
-          rel = (w >= 0.0) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
+          rel = ge0z(w) ? w * al * (1.0 - ar) : w * ar * (1.0 - al);
         }
         hi = Q * van_leer(aU, aD, aUU) + rel;
       }
@@ -205,41 +225,49 @@ __device__ __forceinline__ void b_alpha_lo(const Prm& P, const Fld& F, long long
 // low-order solutions over the cell and its face neighbours (within [0, 1]) in
 // solid-free cells; [0, 1] in porous cells, where the relative flux is the
 // physical Darcy phase flux of Eq. 34.
-__device__ __forceinline__ void b_alpha_limit(const Prm& P, const Fld& F, long long c, double dt) {
+__device__ __forceinline__ void b_alpha_limit(const Prm& P, const Fld& F, long long c, double inv_dt) {
   int i, j, k;
   decode_cell(P, c, i, j, k);
   const double a0 = F.alpha[c], aLc = F.aL[c];
-  double amax = fmax(a0, aLc), amin = fmin(a0, aLc);
+  // extrema through order-preserving integer keys (the same values fmin / fmax select)
+  const long long k0 = okey(a0), kL = okey(aLc);
+  long long kmax = kmax2(k0, kL), kmin = kmin2(k0, kL);
   double Pp = 0.0, Pm = 0.0;
   for (int d = 0; d < P.dim; d++) {
     const int di = (d == 0), dj = (d == 1), dk = (d == 2);
     const int cd = d == 0 ? i : (d == 1 ? j : k);
     if (cd > 0) {
       long long b = cell_index(P.n, i - di, j - dj, k - dk);
-      amax = fmax(amax, fmax(F.alpha[b], F.aL[b]));
-      amin = fmin(amin, fmin(F.alpha[b], F.aL[b]));
+      const long long ka = okey(F.alpha[b]), kb = okey(F.aL[b]);
+      kmax = kmax2(kmax, kmax2(ka, kb));
+      kmin = kmin2(kmin, kmin2(ka, kb));
     }
     if (cd + 1 < P.n[d]) {
       long long b = cell_index(P.n, i + di, j + dj, k + dk);
-      amax = fmax(amax, fmax(F.alpha[b], F.aL[b]));
-      amin = fmin(amin, fmin(F.alpha[b], F.aL[b]));
+      const long long ka = okey(F.alpha[b]), kb = okey(F.aL[b]);
+      kmax = kmax2(kmax, kmax2(ka, kb));
+      kmin = kmin2(kmin, kmin2(ka, kb));
     }
     const double alo = F.AF[d][face_index(P.n, d, i, j, k)];
     const double ahi = F.AF[d][face_index(P.n, d, i + di, j + dj, k + dk)];
-    Pp += fmax(0.0, alo) + fmax(0.0, -ahi);
-    Pm += fmax(0.0, -alo) + fmax(0.0, ahi);
+    // fmax(0, x) and fmax(0, -x) from the sign bit
+    const double alo_p = ge0(alo) ? alo : 0.0, alo_m = ge0(alo) ? 0.0 : -alo;
+    const double ahi_p = ge0(ahi) ? ahi : 0.0, ahi_m = ge0(ahi) ? 0.0 : -ahi;
+    Pp += alo_p + ahi_m;
+    Pm += alo_m + ahi_p;
   }
-  amax = fmin(1.0, amax);
-  amin = fmax(0.0, amin);
+  double amax = from_okey(kmin2(kmax, okey(1.0)));
+  double amin = from_okey(kmax2(kmin, okey(0.0)));
   if (!F.is_free[c]) {
     amax = 1.0;
     amin = 0.0;
   }
-  const double fac = F.phi[c] * P.V / dt;
-  const double Qp = fmax(0.0, amax - aLc) * fac;
-  const double Qm = fmax(0.0, aLc - amin) * fac;
-  F.Rp[c] = Pp > 0.0 ? fmin(1.0, Qp / Pp) : 1.0;
-  F.Rm[c] = Pm > 0.0 ? fmin(1.0, Qm / Pm) : 1.0;
+  const double fac = F.phi[c] * P.V * inv_dt;
+  const double dq_p = amax - aLc, dq_m = aLc - amin;
+  const double Qp = (ge0(dq_p) ? dq_p : 0.0) * fac;
+  const double Qm = (ge0(dq_m) ? dq_m : 0.0) * fac;
+  F.Rp[c] = gt0(Pp) ? fmin(1.0, Qp / Pp) : 1.0;  // Pp, Pm >= 0
+  F.Rm[c] = gt0(Pm) ? fmin(1.0, Qm / Pm) : 1.0;
 }
 
 __device__ __forceinline__ double limited_af(const Prm& P, const Fld& F, int d, int i, int j, int k) {
@@ -291,7 +319,7 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
     F.rho[c] = a * P.rho_l + (1.0 - a) * P.rho_g;
     return;
   }
-  double ae = (a - P.a_l_irr) / (1.0 - P.a_g_irr - P.a_l_irr);
+  double ae = (a - P.a_l_irr) * P.inv_ae_den;
   ae = fmin(fmax(ae, 0.0), 1.0);
   double krl, krg;
   if (P.kr_model == 0) {
@@ -314,16 +342,18 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
     krl = sqrt(ae) * t * t;
   }
   const double k0 = F.k0[c];
-  const double Ml = k0 * krl / P.mu_l, Mg = k0 * krg / P.mu_g, M = Ml + Mg;
-  double s = (a - P.a_pc_irr) / (P.a_pc_max - P.a_pc_irr);
+  const double Ml = k0 * krl * P.inv_mu_l, Mg = k0 * krg * P.inv_mu_g, M = Ml + Mg;
+  double s = (a - P.a_pc_irr) * P.inv_s_den;
   s = fmin(fmax(s, P.pc_eps), 1.0 - P.pc_eps);
   double pc;
   if (P.pc_model == 0)
-    pc = P.pc_beta == 0.5 ? P.pc0 / sqrt(s) : P.pc0 * pow(s, -P.pc_beta);
+    pc = P.pc_beta == 0.5 ? P.pc0 * rsqrt(s) : P.pc0 * pow(s, -P.pc_beta);
   else
     pc = P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
   F.Ml[c] = Ml;
   F.Mg[c] = Mg;
+  // a division, not Ml * (1/M): with no gas mobility f must be exactly 1, or a
+  // saturated region would carry a rounding-size antidiffusive flux
   F.fw[c] = Ml / M;  // M > 0 in porous cells: k0 > 0 and k_rl + k_rg > 0
   const double inv_M = 1.0 / M;
   F.drag[c] = inv_M;
@@ -361,8 +391,8 @@ __device__ __forceinline__ void b_normals(const Prm& P, const Fld& F, long long 
   double g[3] = {0.0, 0.0, 0.0};
   for (int e = 0; e < P.dim; e++) g[e] = fluid_grad(F.alpha, P, F, e, i, j, k, c);
   const double mag = sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]);
-  const double den = mag + 1e-8 / P.h;
-  double m[3] = {g[0] / den, g[1] / den, g[2] / den};
+  const double inv_den = 1.0 / (mag + P.reg_m);
+  double m[3] = {g[0] * inv_den, g[1] * inv_den, g[2] * inv_den};
   const double nw[3] = {F.nw[0][c], F.nw[1][c], F.nw[2][c]};
   if (nw[0] != 0.0 || nw[1] != 0.0 || nw[2] != 0.0) {
     const double mm = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2]);
@@ -849,13 +879,18 @@ __global__ void k_alpha_lo(const StepDom* __restrict__ D, Work w) {
 
 __global__ void k_alpha_limit(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
+  __shared__ double s_inv_dt;  // one FP64 division per block, not per cell
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
+    __syncthreads();  // the previous item's readers are done
+    if (threadIdx.x == 0) s_inv_dt = 1.0 / S.scal[kSlotDt];
+    __syncthreads();
+    const double inv_dt = s_inv_dt;
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < S.P.cells) b_alpha_limit(S.P, S.F, c, S.scal[kSlotDt]);
+      if (c < S.P.cells) b_alpha_limit(S.P, S.F, c, inv_dt);
     }
   }
 }
