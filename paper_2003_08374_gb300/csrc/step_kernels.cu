@@ -582,23 +582,20 @@ __device__ __forceinline__ double face_dp(const Prm& P, const double* __restrict
   return pr - pl;
 }
 
-struct Faces3 {
-  double* a[3];
-};
-
 // one Jacobi sweep of the momentum predictor (Eq. 50): out = (H(in) - V grad p^k)/a_P
-__device__ __forceinline__ void b_jacobi(const Prm& P, const Fld& F, long long t, Faces3 in, Faces3 out) {
+// (in / out: the three face arrays of the iterate and of the result)
+__device__ __forceinline__ void b_jacobi(const Prm& P, const Fld& F, long long t, const double* const* in,
+                                         double* const* out) {
   int d, i, j, k;
   long long f;
   if (!decode_face(P, t, d, i, j, k, f)) return;
   const int cd = d == 0 ? i : (d == 1 ? j : k);
   if (face_kind(P, d, cd) == 1) {
-    out.a[d][f] = in.a[d][f];
+    out[d][f] = in[d][f];
     return;
   }
-  const double* u[3] = {in.a[0], in.a[1], in.a[2]};
-  const double hs = face_H(P, F, u, d, f);
-  out.a[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) * F.aP[d][f];  // V/h = A; aP = 1/a_P
+  const double hs = face_H(P, F, in, d, f);
+  out[d][f] = (hs - P.A * face_dp(P, F.p, d, i, j, k)) * F.aP[d][f];  // V/h = A; aP = 1/a_P
 }
 
 // utmp -> u (after an odd number of Jacobi sweeps)
@@ -627,8 +624,7 @@ __device__ __forceinline__ void b_hbya(const Prm& P, const Fld& F, long long t) 
     F.hbya[d][f] = 0.0;
     return;
   }
-  const double* u[3] = {F.u[0], F.u[1], F.u[2]};
-  F.hbya[d][f] = face_H(P, F, u, d, f) * F.aP[d][f];
+  F.hbya[d][f] = face_H(P, F, F.u, d, f) * F.aP[d][f];
 }
 
 // corrected velocity, Eq. 51
@@ -971,13 +967,12 @@ __global__ void k_jacobi(const StepDom* __restrict__ D, Work w, int parity) {
     const int dm = work_domain(w, b);
     const StepDom& S = D[dm];
     const int lb = b - w.blk[dm];
-    Faces3 a{{S.F.u[0], S.F.u[1], S.F.u[2]}}, c{{S.F.utmp[0], S.F.utmp[1], S.F.utmp[2]}};
+    // even sweeps u -> utmp, odd sweeps utmp -> u
+    const double* const* in = parity ? S.F.utmp : S.F.u;
+    double* const* out = parity ? S.F.u : S.F.utmp;
     for (int r = 0; r < w.rep; r++) {
       const long long t = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (parity)
-        b_jacobi(S.P, S.F, t, c, a);
-      else
-        b_jacobi(S.P, S.F, t, a, c);
+      b_jacobi(S.P, S.F, t, in, out);
     }
   }
 }
