@@ -64,3 +64,16 @@ def test_shard_by_cells_is_deterministic_and_balanced():
         assert sorted(i for p in parts for i in p) == list(range(len(cells)))
         loads = [sum(cells[i] for i in p) for p in parts]
         assert max(loads) - min(loads) <= max(cells)
+
+
+def test_all_cores_oracle_baseline_runs_one_serial_process_per_core():
+    """The all-cores CPU baseline: one oracle process per host core, each on its own slab,
+    timed together; the aggregate rate counts every process's cells over the slowest one's
+    time (so it cannot exceed cores x the fastest single process)."""
+    import os
+    import bench
+    value, cores, secs = bench.time_oracle_all_cores(24, 1)
+    assert cores == (os.cpu_count() or 1)
+    assert value > 0 and secs > 0
+    one, _ = bench.time_oracle(bench.slab_of(bench.workload(24)), 1, 0)
+    assert value <= cores * one * 3
