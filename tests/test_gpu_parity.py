@@ -178,6 +178,33 @@ def test_step_at_bench_tolerance_against_fp64_oracle(precision):
         precision, {k: "%.2e" % v for k, v in errs.items()}))
 
 
+@pytest.mark.parametrize("which", ["grf", "fracture_2d", "wave_tank"])
+def test_cg_iterations_match_the_oracles_preconditioner(which):
+    """The GPU's V-cycle is the oracle's preconditioner (same hierarchy, coarse operator,
+    red-black order, exact coarsest solve), so at the bench tolerance 1e-8 each corrector's
+    CG takes the oracle's number of iterations (one more or fewer where rounding moves the
+    residual across the threshold) over several steps; a preconditioner that differed in
+    quality would change the counts by several."""
+    from oracle.api import OracleSim
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = {"grf": W.grf_3d(shape=(24, 20, 16), seed=3, corr_len=3.0, frac_w=2, p_tol=1e-8, max_cg=300),
+            "fracture_2d": W.fracture_2d(nx=64, ny=64, p_tol=1e-8, max_cg=300),
+            "wave_tank": W.wave_tank(nx=32, ny=6, nz=20, h=5e-3, depth=10, x0=8, barrier=(20, 26, 8),
+                                     p_tol=1e-8, max_cg=300)}[which]
+    g = mdbs.Simulation(case)
+    o = OracleSim(case)
+    seen = []
+    for _ in range(4):
+        g.step(1)
+        o.step(1)
+        ig, io = g.stats()["cg_iters"], o.stats()["cg_iters"]
+        seen.append((ig, io))
+        assert all(abs(a - b) <= 1 for a, b in zip(ig, io)), seen
+    assert sum(sum(io) for _, io in seen) > 0
+    print(which, "iterations (GPU, oracle) per step:", seen)
+
+
 @pytest.mark.parametrize("precision", [0, 1, 2])
 def test_run_at_bench_tolerance_drifts_only_as_the_tolerance_allows(precision):
     """Over 100 steps at a pressure residual of 1e-8 the solution drifts from the one solved to
