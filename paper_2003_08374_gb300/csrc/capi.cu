@@ -248,6 +248,7 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   F.is_free = (uint8_t*)take(L.cells);
   for (int e = 0; e < 3; e++) F.nw[e] = cd();
   F.iphi2 = cd();
+  F.iphiV = cd();
   F.alpha = cd();
   F.p = cd();
   F.Ml = cd();

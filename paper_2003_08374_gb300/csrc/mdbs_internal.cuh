@@ -77,6 +77,7 @@ struct Fld {
   const uint8_t* is_free;
   const double* nw[3];  // wall normal (zero outside contact cells)
   const double* iphi2;  // phi^-2 (porosity-gradient part of the convection)
+  const double* iphiV;  // 1 / (phi V) (saturation updates)
   const double* iphif[3];  // 1 / phi_f, phi_f the mean porosity of a face's two cells
   const double* gphi[3];   // grad(phi^-2) at a face: component e of direction-d faces at e * nf[d] + f
   // state

@@ -218,7 +218,7 @@ __device__ __forceinline__ void b_alpha_lo(const Prm& P, const Fld& F, long long
     long long fhi = face_index(P.n, d, i + (d == 0), j + (d == 1), k + (d == 2));
     div += F.FLO[d][fhi] - F.FLO[d][flo];
   }
-  F.aL[c] = F.alpha[c] - dt / (F.phi[c] * P.V) * div;
+  F.aL[c] = F.alpha[c] - dt * F.iphiV[c] * div;
 }
 
 // Zalesak limiter coefficients R+ / R-.  Bounds: local extrema of the old and
@@ -276,8 +276,10 @@ __device__ __forceinline__ double limited_af(const Prm& P, const Fld& F, int d, 
   const long long l = cell_index(P.n, i - (d == 0), j - (d == 1), k - (d == 2));
   const long long r = cell_index(P.n, i, j, k);
   const double a = F.AF[d][face_index(P.n, d, i, j, k)];
-  const double lam = a >= 0.0 ? fmin(F.Rm[l], F.Rp[r]) : fmin(F.Rp[l], F.Rm[r]);
-  return lam * a;
+  // R+ and R- lie in [0, 1]: the smaller bit pattern is the smaller value
+  const unsigned long long bl = __double_as_longlong(ge0z(a) ? F.Rm[l] : F.Rp[l]);
+  const unsigned long long br = __double_as_longlong(ge0z(a) ? F.Rp[r] : F.Rm[r]);
+  return __longlong_as_double(bl < br ? bl : br) * a;
 }
 
 __device__ __forceinline__ void b_alpha_update(const Prm& P, const Fld& F, long long c, double dt) {
@@ -289,7 +291,7 @@ __device__ __forceinline__ void b_alpha_update(const Prm& P, const Fld& F, long 
     const double hi = limited_af(P, F, d, i + (d == 0), j + (d == 1), k + (d == 2));
     corr += hi - lo;
   }
-  F.alpha[c] = F.aL[c] - dt / (F.phi[c] * P.V) * corr;
+  F.alpha[c] = F.aL[c] - dt * F.iphiV[c] * corr;
 }
 
 // per domain (one block each): scal[slot] += dt * (deterministic sum of the domain's
@@ -802,6 +804,7 @@ __device__ __forceinline__ void b_static_geometry(const Prm& P, const Fld& F, lo
   }
   for (int e = 0; e < 3; e++) const_cast<double*>(F.nw[e])[c] = n[e];
   const_cast<double*>(F.iphi2)[c] = 1.0 / (phi[c] * phi[c]);
+  const_cast<double*>(F.iphiV)[c] = 1.0 / (phi[c] * P.V);
 }
 
 __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
