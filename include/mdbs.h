@@ -155,7 +155,8 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
  * than the extremes this simulation's own steps reached (transport through a velocity
  * field divergence-free only to the pressure tolerance moves alpha outside [0, 1] by
  * dt |div(A u)| / (phi V) per step; a get_fields / set_fields round trip of such a
- * state is accepted).  A non-finite pressure or velocity is copied in and reported:
+ * state is accepted); the check runs on the device and a rejected call leaves the
+ * state unchanged.  A non-finite pressure or velocity is copied in and reported:
  * MDBS_ERR_DIVERGED (the state is set; mdbs_step then reports it too).
  */
 int mdbs_set_fields(mdbs_sim* sim, const double* alpha, const double* ux, const double* uy,

@@ -848,6 +848,16 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   return MDBS_OK;
 }
 
+// 1 in *flag if any of the n values lies outside [lo, hi] (NaN fails both comparisons)
+__global__ void k_check_range(const double* __restrict__ a, long long n, double lo, double hi, double* flag) {
+  int bad = 0;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < n; c += (long long)gridDim.x * blockDim.x) {
+    const double v = a[c];
+    bad |= !(v >= lo && v <= hi);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) *flag = 1.0;
+}
+
 int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const double* uy, const double* uz,
                     const double* p) {
   if (!s) return MDBS_ERR_ARG;
@@ -858,19 +868,26 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   // transport through a velocity field divergence-free only to the pressure tolerance
   // moves alpha outside [0, 1] by dt |div(A u)| / (phi V) per step, so the range also
   // admits the extremes its own steps have reached.
-  // branch-free inner loop (vectorised by the host compiler), one exit test per chunk;
-  // NaN fails both comparisons
+  // The check runs on the device: alpha goes to the low-order saturation scratch (which
+  // the next step overwrites), a kernel flags any value out of range, and only an
+  // accepted field is copied into place, so a rejected call leaves the state unchanged.
   const double lo = std::min(-1e-9, s->alpha_lo_seen), hi = std::max(1.0 + 1e-9, s->alpha_hi_seen);
-  for (long long c0 = 0; c0 < s->P.cells; c0 += 4096) {
-    const long long c1 = std::min(s->P.cells, c0 + 4096);
-    int ok = 1;
-    for (long long c = c0; c < c1; c++) ok &= (int)(alpha[c] >= lo) & (int)(alpha[c] <= hi);
-    if (!ok)
-      return fail(s, MDBS_ERR_ARG,
-                  "alpha must lie in [0, 1] (to 1e-9, or within the extremes this simulation reached)");
+  double* stage = s->F.aL;
+  CK(cudaMemcpyAsync(stage, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemsetAsync(s->scal + kSlotCheck, 0, sizeof(double), s->stream));
+  {
+    const long long blocks = std::min<long long>((s->P.cells + 255) / 256, 4096);
+    k_check_range<<<(unsigned)blocks, 256, 0, s->stream>>>(stage, s->P.cells, lo, hi, s->scal + kSlotCheck);
+    CK(cudaGetLastError());
   }
+  CK(cudaMemcpyAsync(s->host_scal + kSlotCheck, s->scal + kSlotCheck, sizeof(double), cudaMemcpyDeviceToHost,
+                     s->stream));
+  CK(cudaStreamSynchronize(s->stream));
+  if (s->host_scal[kSlotCheck] != 0.0)
+    return fail(s, MDBS_ERR_ARG,
+                "alpha must lie in [0, 1] (to 1e-9, or within the extremes this simulation reached)");
   const double* src[3] = {ux, uy, uz};
-  CK(cudaMemcpyAsync(s->F.alpha, alpha, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
+  CK(cudaMemcpyAsync(s->F.alpha, stage, s->P.cells * 8, cudaMemcpyDeviceToDevice, s->stream));
   CK(cudaMemcpyAsync(s->F.p, p, s->P.cells * 8, cudaMemcpyHostToDevice, s->stream));
   for (int d = 0; d < s->P.dim; d++)
     CK(cudaMemcpyAsync(s->F.u[d], src[d], s->P.nf[d] * 8, cudaMemcpyHostToDevice, s->stream));

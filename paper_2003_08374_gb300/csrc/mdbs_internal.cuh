@@ -22,7 +22,7 @@ constexpr int kRepBig = 8;  // rows of kBlock per work item in the cell and face
 // slots of the per-domain device scalar array
 constexpr int kSlotMass = 0, kSlotAmin = 1, kSlotAmax = 2, kSlotBad = 3, kSlotUmax = 4, kSlotInflow = 5,
               kSlotDt = 6, kSlotTime = 7, kSlotIters = 8 /* 8 correctors */, kSlotResid = 16 /* 8 */,
-              kSlotItersTotal = 24, kSlotNotConverged = 25, kNumSlots = 32;
+              kSlotItersTotal = 24, kSlotNotConverged = 25, kSlotCheck = 26, kNumSlots = 32;
 
 // Division by a divisor fixed for a level, without a hardware divide: for
 // 0 <= t < 2^31, t / d == (t * m) >> s with s = 31 + ceil(log2 d) and

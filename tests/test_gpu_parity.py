@@ -306,6 +306,21 @@ def test_set_fields_rejects_bad_alpha_and_invalid_create():
     with pytest.raises(mdbs.MdbsError) as e:
         s.set_fields(bad, case.ux, case.uy, case.uz, case.p)
     assert e.value.code == mdbs.ERR_ARG
+    # the check runs on the device: a NaN in the last cell of a field larger than the
+    # check's grid is caught, and a rejected call leaves the state as it was
+    big = W.grf_3d(shape=(160, 130, 64), seed=3, corr_len=3.0, frac_w=2)
+    g = mdbs.Simulation(big)
+    g.step(1)
+    before = g.fields()
+    bad = before["alpha"].copy()
+    bad[-1] = np.nan
+    with pytest.raises(mdbs.MdbsError) as e:
+        g.set_fields(bad, before["ux"], before["uy"], before["uz"], before["p"])
+    assert e.value.code == mdbs.ERR_ARG
+    after = g.fields()
+    assert all(np.array_equal(before[k], after[k]) for k in before)
+    g.step(1)
+    g.close()
     c2 = case.replace(bc=(W.WALL,) * 6)
     with pytest.raises(mdbs.MdbsError):
         mdbs.Simulation(c2)
