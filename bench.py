@@ -412,6 +412,24 @@ def vcycle_bytes(n, word, tuning, nu=(2, 2), bf16_coarse=False):
     return out
 
 
+def vcycle_fp64_instructions(n, nu=(2, 2)):
+    """FP64 instructions of one split-sweep V-cycle, level by level: per updated cell a full
+    half sweep issues 7 (6 fused multiply-adds, 1 multiply), the zero-guess one 1, the
+    prolonging one 13 (6 more adds of the coarse correction); the masked restriction 9 per
+    colour-0 fine cell (diag x, 6 fused multiply-adds, b - Ax, the sum into the coarse
+    cell); the coarsest level's dense product N^2."""
+    levels = level_sizes(n)
+    out = []
+    halves = 2 * (nu[0] + nu[1])
+    for l, sz in enumerate(levels):
+        N = sz[0] * sz[1] * sz[2]
+        if l == len(levels) - 1:
+            out.append(N * N)
+            continue
+        out.append(N / 2 * (1 + (halves - 2) * 7 + 13) + N / 2 * 9)
+    return out
+
+
 def vcycle_roofline(prof, n, word, tuning, graph_ms, nu=(2, 2), bf16_coarse=False):
     """HBM roofline of the whole preconditioner: algorithmic bytes of every V-cycle run in
     the eager pass over the summed CUDA-event time of the V-cycle kernels, and the same with
@@ -431,14 +449,28 @@ def vcycle_roofline(prof, n, word, tuning, graph_ms, nu=(2, 2), bf16_coarse=Fals
     gbs = per_cycle * cycles / (vc_ms / 1e3) / 1e9
     scaled_ms = vc_ms * graph_ms / all_ms
     gbs_g = per_cycle * cycles / (scaled_ms / 1e3) / 1e9
-    return {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-            "graph_scaled": {"achieved": gbs_g, "frac": gbs_g / peak, "vcycle_ms": scaled_ms,
-                             "share_of_step": vc_ms / all_ms},
-            "alg_bytes_per_vcycle": per_cycle, "vcycles": cycles, "kernel_ms": vc_ms,
+    out = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "graph_scaled": {"achieved": gbs_g, "frac": gbs_g / peak, "vcycle_ms": scaled_ms,
+                            "share_of_step": vc_ms / all_ms},
+           "alg_bytes_per_vcycle": per_cycle, "vcycles": cycles, "kernel_ms": vc_ms,
             "levels": [{"cells": c, "alg_bytes": b} for c, b in levels],
             "kernels": [k for k in VCYCLE_KERNELS if k in prof],
-            "timing": "sum of CUDA-event kernel times in the eager pass; graph_scaled multiplies them by "
-                      "graph step time / eager kernel time"}
+           "timing": "sum of CUDA-event kernel times in the eager pass; graph_scaled multiplies them by "
+                     "graph step time / eager kernel time"}
+    if word == 8 and not fused_sweeps(tuning, word):
+        # FP64 levels: each level is bound by the larger of its HBM time and its FP64-pipe
+        # time (GB300 issues FP64 at 2 lanes per clock per SM)
+        instr = vcycle_fp64_instructions(n, nu)
+        rate = FP64_PEAK_TFLOPS * 1e12 / 2  # FP64 instructions per second
+        roof_s = sum(max(b / (peak * 1e9), i / rate) for (_, b), i in zip(levels, instr)) * cycles
+        out["fp64"] = {"instructions_per_vcycle": sum(instr),
+                       "pipe_frac": sum(instr) * cycles / rate / (vc_ms / 1e3),
+                       "time_at_roof_ms": roof_s * 1e3,
+                       "frac_of_roof": roof_s / (vc_ms / 1e3),
+                       "graph_scaled_frac_of_roof": roof_s / (scaled_ms / 1e3),
+                       "roof": "per level the larger of algorithmic bytes / measured HBM and FP64 "
+                               "instructions / (152 SMs x 2 lanes x 2.07 GHz)"}
+    return out
 
 
 def error_vs_oracle(case, precisions):
