@@ -183,3 +183,28 @@ def test_vector_half_sweeps_are_bitwise_equal(precision):
             for k in ref_f:
                 assert np.array_equal(ref_f[k], f[k]), (shape, sch, k)
             assert st["cg_iters"] == ref_s["cg_iters"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_step_equals_eager_step(precision):
+    """The captured step runs the pressure operator's assembly, hierarchy and coarsest
+    inverse on a side branch beside the momentum Jacobi sweeps; eager steps (profiling)
+    run the same kernels in line.  A missing dependency between the branches would show
+    as a difference: fields and CG iteration counts must be bitwise equal."""
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    case = W.grf_3d(shape=(40, 36, 32), seed=5, corr_len=3.0, frac_w=2, p_tol=1e-10, max_cg=300,
+                    precision=precision)
+    g = mdbs.Simulation(case)
+    e = mdbs.Simulation(case)
+    e.profile(True)
+    for _ in range(3):
+        g.step(2)
+        e.step(2)
+        assert g.stats()["cg_iters"] == e.stats()["cg_iters"]
+    fg, fe = g.fields(), e.fields()
+    for k in fg:
+        assert np.array_equal(fg[k], fe[k]), k
+    assert e.profile_read()["coarsen"][1] > 0  # the eager steps did run the in-line build
+    g.close()
+    e.close()
