@@ -21,8 +21,10 @@ The default line also carries, on stated reduced configurations: the error of
 one step of every precision against the oracle (``error_vs_oracle``), the
 V-cycle-wide roofline, a 64-domain batch, a 3 s serving trace (p50/p99), the
 512 x 128 x 256 wave tank (mixed + BF16 and FP64) and the 2-D 64^2 case.
-``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same
-workload (a 16-layer slab), on rank 0 only.
+``--impl reference`` times the FP64 CPU oracle on bounded samples of the same
+workload (one serial oracle process per host core, each on its own 16-layer
+slab), on rank 0 only.  ``--workload wave_tank --steps 2000`` runs configuration
+3 (the 512 x 128 x 256 tank) at its full length.
 """
 import argparse
 import hashlib
@@ -55,7 +57,7 @@ def parse():
     ap.add_argument("--n", type=int, default=128, help="cells per axis of the workload")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-mixed", action="store_true")
-    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched", "serving", "buckley_leverett"])
+    ap.add_argument("--workload", default="grf128", choices=["grf128", "batched", "serving", "buckley_leverett", "wave_tank"])
     ap.add_argument("--columns", type=int, default=512, help="buckley_leverett: columns in the batch")
     ap.add_argument("--rate", type=float, default=20.0, help="serving: arrivals per second")
     ap.add_argument("--duration", type=float, default=10.0, help="serving: arrival window [s]")
@@ -63,6 +65,8 @@ def parse():
     ap.add_argument("--req-steps", type=int, default=100, help="serving: steps per request")
     ap.add_argument("--domains", type=int, default=512, help="batched workload: number of domains")
     ap.add_argument("--precision", type=int, default=0, help="batched workload: 0 FP64, 1 mixed")
+    ap.add_argument("--tank-precision", type=int, default=2,
+                    help="wave_tank workload: 0 FP64, 1 mixed, 2 mixed with BF16 coarse coefficients")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default multigrid schedule")
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving sub-objects")
     ap.add_argument("--extra-domains", type=int, default=64, help="batched sub-object: domains")
@@ -592,6 +596,68 @@ def wave_tank_summary(args, steps, warmup, stream):
     return out
 
 
+def wave_tank_arm(args):
+    """Configuration 3 at full size and length: the 512 x 128 x 256 wave tank (porous
+    barrier, solitary wave, CFL 0.5, walls and an open top), autotuned, --warmup untimed
+    and --steps timed steps from the initial state.  Besides throughput it reports the
+    run's state: simulated time and dt, CG iterations (last step, mean and the largest per
+    corrector), the liquid volume against its initial value (the open top is the only
+    boundary it can cross), the saturation bounds, and unconverged solves."""
+    import torch
+    from paper_2003_08374_gb300 import mdbs
+    from paper_2003_08374_gb300 import workloads as W
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    prec = {0: W.FP64, 1: W.MIXED, 2: W.MIXED_BF16}[args.tank_precision]
+    case = W.wave_tank(p_tol=1e-8, max_cg=200, precision=prec)
+    sim = mdbs.Simulation(case)
+    sim.set_stream(stream.cuda_stream)
+    tuning, _ = pick_schedule(sim, args, trial_steps=1)
+    sim.set_fields(case.alpha, case.ux, case.uy, case.uz, case.p)
+    mass0 = sim.stats()["mass"]
+    for _ in range(args.warmup):
+        sim.step(1)
+    torch.cuda.synchronize()
+    it0 = sim.stats()["cg_iters_total"]
+    iters_max = [0] * case.n_corr
+    amin, amax = 1.0, 0.0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    chunk = 50  # statistics every chunk steps; the device time covers only the steps
+    ms = 0.0
+    done = 0
+    with ClockSampler(0) as clk:
+        while done < args.steps:
+            k = min(chunk, args.steps - done)
+            e0.record(stream)
+            sim.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms += e0.elapsed_time(e1)
+            done += k
+            st = sim.stats()
+            iters_max = [max(a, b) for a, b in zip(iters_max, st["cg_iters"])]
+            amin, amax = min(amin, st["alpha_min"]), max(amax, st["alpha_max"])
+    st = sim.stats()
+    line = {"metric": METRIC, "value": case.cells * args.steps / (ms / 1e3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {0: "f64", 1: "f64 (FP32 V-cycle)", 2: "f64 (FP32 V-cycle, BF16 coarse coefficients)"}[
+                args.tank_precision], "data": "synthetic",
+            "config": {"workload": "wave_tank_512x128x256 (16.8 M cells, CFL 0.5, dt_max 2e-3 s)", "cells": case.cells,
+                       "p_tol": case.p_tol, "tuning": tuning,
+                       "timing": "device time of the steps, in chunks of %d with statistics read between" % chunk},
+            "run": {"time_s": st["time"], "dt_last": st["dt"], "cg_iters_last_step": st["cg_iters"],
+                    "cg_iters_max": iters_max,
+                    "cg_iters_mean_per_corrector": (st["cg_iters_total"] - it0) / (args.steps * case.n_corr),
+                    "unconverged_solves": st["not_converged"],
+                    "liquid_volume_rel_change": (st["mass"] - mass0) / mass0,
+                    "alpha_min": amin, "alpha_max": amax},
+            "clocks": clk.summary()}
+    sim.close()
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def fracture_2d_summary(stream):
     """The 2-D 64 x 64 fracture case (dx 10 um, dt 1e-6 s, FP64, 100 steps): a launch-bound
     step; its error after the 100 steps against the oracle at 1e-15, the case at 1e-8."""
@@ -1049,6 +1115,8 @@ def main():
         return batched_arm(args)
     if args.workload == "buckley_leverett":
         return bl_arm(args)
+    if args.workload == "wave_tank":
+        return wave_tank_arm(args)
     return gpu_arm(args)
 
 
