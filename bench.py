@@ -658,9 +658,10 @@ def wave_tank_arm(args):
     return 0
 
 
-def fracture_2d_summary(stream):
+def fracture_2d_summary(args, stream):
     """The 2-D 64 x 64 fracture case (dx 10 um, dt 1e-6 s, FP64, 100 steps): a launch-bound
-    step; its error after the 100 steps against the oracle at 1e-15, the case at 1e-8."""
+    step, autotuned like the other workloads; its error after the 100 steps against the
+    oracle at 1e-15, the case at 1e-8."""
     from oracle.api import OracleSim
     from paper_2003_08374_gb300 import mdbs
     from paper_2003_08374_gb300 import workloads as W
@@ -672,11 +673,13 @@ def fracture_2d_summary(stream):
         case = W.fracture_2d(nx=64, ny=64, p_tol=p_tol, max_cg=500)
         sim = mdbs.Simulation(case)
         sim.set_stream(stream.cuda_stream)
+        tuning = sim.tuning() if args.no_autotune else sim.autotune(trial_steps=2)[0]
         ms = timed_steps(sim, 100, 0, stream)
         st = sim.stats()
         key = "p_tol_%.0e" % p_tol
         out[key] = {"value": case.cells * 100 / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / 100,
-                    "launches_per_step": st["kernel_launches"] / 100.0, "cg_iters_last_step": st["cg_iters"]}
+                    "launches_per_step": st["kernel_launches"] / 100.0, "cg_iters_last_step": st["cg_iters"],
+                    "tuning": tuning}
         out[key]["error_vs_oracle_1e-15"] = field_errors(sim.fields(), fo)
         sim.close()
     return out
@@ -870,7 +873,7 @@ def gpu_arm(args):
     batched = serving = wave = frac2d = None
     if not args.no_extras and world == 1:
         wave = wave_tank_summary(args, args.wave_steps, args.warmup, stream)
-        frac2d = fracture_2d_summary(stream)
+        frac2d = fracture_2d_summary(args, stream)
         batched = {name: batched_summary(args, prec, args.extra_domains, args.steps, args.warmup, stream, local)
                    for name, prec in (("fp64", W.FP64), ("mixed", W.MIXED))}
         serving = {name: serving_summary(prec, args.rate, args.extra_duration, args.extra_max_side,
