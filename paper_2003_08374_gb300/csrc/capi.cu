@@ -894,7 +894,9 @@ int mdbs_set_fields(mdbs_sim* s, const double* alpha, const double* ux, const do
   for (int d = 0; d < s->P.dim; d++)
     CK(cudaMemcpyAsync(s->F.u[d], src[d], s->P.nf[d] * 8, cudaMemcpyHostToDevice, s->stream));
   launch_set_boundary_velocities(s->ex.plan, s->stream);
-  launch_properties(s->ex.plan, s->stream);
+  // the step's saturation phase reads the closures of the new alpha; normals and
+  // curvature are formed again from alpha^{k+1} before the momentum assembly reads them
+  launch_closures(s->ex.plan, s->stream);
   for (int i = 0; i < kNumSlots; i++) s->host_scal[i] = 0.0;
   s->host_scal[kSlotDt] = s->opt.dt;
   CK(cudaMemcpyAsync(s->scal, s->host_scal, kNumSlots * sizeof(double), cudaMemcpyHostToDevice, s->stream));

@@ -315,6 +315,8 @@ inline int grid_of(const BatchPlan& B, const Work& w) {
 // step_kernels.cu (dt, time and the statistics live in each domain's scalar array)
 void launch_alpha_step(const BatchPlan& B, cudaStream_t s);
 void launch_properties(const BatchPlan& B, cudaStream_t s);
+// the closures alone (no normals or curvature): all the saturation step reads
+void launch_closures(const BatchPlan& B, cudaStream_t s);
 void launch_momentum_assemble(const BatchPlan& B, cudaStream_t s);
 void launch_jacobi_sweeps(const BatchPlan& B, int sweeps, cudaStream_t s);  // result in F.u
 void launch_hbya(const BatchPlan& B, cudaStream_t s);

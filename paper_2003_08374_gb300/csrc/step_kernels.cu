@@ -1037,6 +1037,8 @@ void launch_alpha_step(const BatchPlan& B, cudaStream_t s) {
   BATCH_LAUNCH(K_ALPHA_UPDATE, cells, k_alpha_update);
 }
 
+void launch_closures(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_PROPERTIES, cells, k_properties); }
+
 void launch_properties(const BatchPlan& B, cudaStream_t s) {
   BATCH_LAUNCH(K_PROPERTIES, cells, k_properties);
   BATCH_LAUNCH(K_NORMALS, cells, k_normals);
