@@ -25,7 +25,7 @@ const char* const kKernelNames[K_COUNT] = {
     "curvature", "momentum_assemble", "jacobi", "hbya", "correct", "boundary", "field_stats", "cfl",
     "static_geometry", "pressure_assemble", "diag", "convert", "coarsen", "smooth_fine", "smooth_coarse",
     "zero", "restrict_fine", "restrict_coarse", "prolong_fine", "prolong_coarse", "cg_resid0",
-    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d", "tail_vcycle", "coarse_coop"};
+    "cg_spmv_dot", "cg_update_xr", "cg_dots", "cg_update_d", "tail_vcycle", "coarse_coop", "edge_viscosity"};
 
 // Per-simulation launch counter and optional event timer.
 struct Profiler {
@@ -219,6 +219,7 @@ size_t a256(size_t b) { return (b + 255) & ~(size_t)255; }
 
 struct Layout {
   long long cells, nf[3];
+  long long n[3];
   int dim;
 };
 
@@ -226,6 +227,9 @@ Layout layout_of(const mdbs_grid* g) {
   Layout L;
   L.dim = g->nz == 1 ? 2 : 3;
   L.cells = (long long)g->nx * g->ny * g->nz;
+  L.n[0] = g->nx;
+  L.n[1] = g->ny;
+  L.n[2] = g->nz;
   L.nf[0] = (long long)(g->nx + 1) * g->ny * g->nz;
   L.nf[1] = (long long)g->nx * (g->ny + 1) * g->nz;
   L.nf[2] = (long long)g->nx * g->ny * (g->nz + 1);
@@ -261,6 +265,14 @@ size_t carve(mdbs_sim* s, const Layout& L, char* base) {
   F.drag = cd();
   for (int e = 0; e < 3; e++) F.m[e] = cd();
   F.kappa = cd();
+  for (int q = 0; q < 3; q++) {  // edge viscosities of the axis pairs (0,1), (0,2), (1,2)
+    const int a = q == 2 ? 1 : 0, b = q == 0 ? 1 : 2;
+    const bool has = b < L.dim;
+    long long ext[3] = {L.n[0], L.n[1], L.n[2]};
+    ext[a] += 1;
+    ext[b] += 1;
+    F.muE[q] = (double*)take((has ? ext[0] * ext[1] * ext[2] : 1) * 8);
+  }
   F.aL = cd();
   F.Rp = cd();
   F.Rm = cd();
@@ -792,6 +804,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.inv_ae_den = 1.0 / (1.0 - P.a_g_irr - P.a_l_irr);
   P.inv_s_den = 1.0 / (P.a_pc_max - P.a_pc_irr);
   P.reg_m = 1e-8 / grid->h;
+  P.inv_h2 = 1.0 / (grid->h * grid->h);
   P.kr_m_int = (cl->kr_m >= 1.0 && cl->kr_m <= 8.0 && cl->kr_m == floor(cl->kr_m)) ? (int)cl->kr_m : 0;
   P.cfl = op->cfl;
   P.dt_max = op->dt_max;

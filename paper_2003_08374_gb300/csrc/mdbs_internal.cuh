@@ -63,6 +63,7 @@ struct Prm {
   double inv_ae_den;          // 1/(1 - a_g_irr - a_l_irr), effective saturation
   double inv_s_den;           // 1/(a_pc_max - a_pc_irr), capillary saturation
   double reg_m;               // 1e-8/h, regularisation of |grad alpha| in the interface normal
+  double inv_h2;              // 1/h^2
   int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
   double cfl, dt_max;        // adaptive time step (cfl > 0)
   FastDiv dn0, dn1;          // division by n[0] and by n[1]
@@ -86,6 +87,9 @@ struct Fld {
   double* u[3];
   // properties
   double *Ml, *Mg, *fw, *pc, *cf, *rho, *mu, *drag, *m[3], *kappa;  // fw = M_l / M
+  // edge viscosities (mean of the four cells around an edge) of the axis pairs (0,1),
+  // (0,2), (1,2): extent n + 1 along the pair's axes, natural x-fastest order
+  double* muE[3];
   // saturation step
   double *FLO[3], *AF[3], *aL, *Rp, *Rm;
   // momentum
@@ -228,7 +232,7 @@ enum KernelId {
   K_ALPHA_FLUX, K_ALPHA_LO, K_ALPHA_LIMIT, K_ALPHA_UPDATE, K_FINALIZE, K_PROPERTIES, K_NORMALS,
   K_CURVATURE, K_MOM_ASSEMBLE, K_JACOBI, K_HBYA, K_CORRECT, K_BOUNDARY, K_STATS, K_CFL, K_STATIC,
   K_ASSEMBLE, K_DIAG, K_CONVERT, K_COARSEN, K_SMOOTH0, K_SMOOTHC, K_ZERO, K_RESTRICT0, K_RESTRICTC,
-  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_TAIL, K_COOP, K_COUNT
+  K_PROLONG0, K_PROLONGC, K_RESID0, K_SPMV_DOT, K_UPDATE_XR, K_DOTS, K_UPDATE_D, K_TAIL, K_COOP, K_EDGE_MU, K_COUNT
 };
 extern const char* const kKernelNames[K_COUNT];
 void prof_begin(int id, cudaStream_t s);

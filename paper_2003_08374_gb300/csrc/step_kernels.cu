@@ -425,6 +425,51 @@ __device__ __forceinline__ void b_curvature(const Prm& P, const Fld& F, long lon
   F.kappa[c] = kap;
 }
 
+// ------------------------------------------------------------------ edge viscosities
+// The viscosity of an edge is the mean of the four cells around it (ghost cells
+// clamp to the boundary cell, as for the faces).  Pair q of axes (a, b) = (0,1),
+// (0,2), (1,2); edge (x, y, z) of pair q lies between cells x - 1 and x along a
+// and y - 1 and y along b (in the pair's own coordinates), so its array has one
+// more entry than the grid along a and along b.  Formed once per step here, read
+// by the four faces around each edge in the momentum assembly.
+__device__ __forceinline__ long long edge_index(const Prm& P, int q, int x, int y, int z) {
+  const int a = q == 2 ? 1 : 0, b = q == 0 ? 1 : 2;
+  const long long ex = P.n[0] + (a == 0), ey = P.n[1] + (a == 1 || b == 1);
+  return x + ex * (y + ey * (long long)z);
+}
+
+__device__ __forceinline__ void edge_mu_at(const Prm& P, const Fld& F, int q, int x, int y, int z) {
+  const int a = q == 2 ? 1 : 0, b = q == 0 ? 1 : 2;
+  int c00[3] = {x, y, z}, c10[3] = {x, y, z}, c01[3] = {x, y, z}, c11[3] = {x, y, z};
+  c00[a] -= 1;
+  c00[b] -= 1;
+  c10[b] -= 1;
+  c01[a] -= 1;
+  const double s = ghost_read(F.mu, P.n, c00[0], c00[1], c00[2]) + ghost_read(F.mu, P.n, c10[0], c10[1], c10[2]) +
+                   ghost_read(F.mu, P.n, c01[0], c01[1], c01[2]) + ghost_read(F.mu, P.n, c11[0], c11[1], c11[2]);
+  F.muE[q][edge_index(P, q, x, y, z)] = 0.25 * s;
+}
+
+// cell (i, j, k) forms the edges at its own position, and on the high boundaries of
+// the pair's axes also those one position beyond
+__device__ __forceinline__ void b_edge_mu(const Prm& P, const Fld& F, long long c) {
+  int i, j, k;
+  decode_cell(P, c, i, j, k);
+  const int q_end = P.dim == 3 ? 3 : 1;
+  for (int q = 0; q < q_end; q++) {
+    const int a = q == 2 ? 1 : 0, b = q == 0 ? 1 : 2;
+    const int pos[3] = {i, j, k};
+    const bool ha = pos[a] == P.n[a] - 1, hb = pos[b] == P.n[b] - 1;
+    for (int da = 0; da <= (ha ? 1 : 0); da++)
+      for (int db = 0; db <= (hb ? 1 : 0); db++) {
+        int e[3] = {i, j, k};
+        e[a] += da;
+        e[b] += db;
+        edge_mu_at(P, F, q, e[0], e[1], e[2]);
+      }
+  }
+}
+
 // ------------------------------------------------------------------ momentum
 // Staggered momentum equation of a face (Eqs. 46-48): diagonal a_P, neighbour
 // coefficients (implicit upwind convection of rho u u / phi^2 and viscous
@@ -517,8 +562,11 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       if (e == d) {
         mus = sg < 0 ? muL : muR;
       } else {
-        mus = 0.25 * (muL + muR + ghost_read(F.mu, P.n, li + sg * ei, lj + sg * ej, lk + sg * ek) +
-                      ghost_read(F.mu, P.n, i + sg * ei, j + sg * ej, k + sg * ek));
+        // the edge between this face and its e-neighbour on side sg: at the face's
+        // position along d, between cells c_e - 1 and c_e (sg < 0) or c_e and c_e + 1
+        int q3[3] = {i, j, k};
+        q3[e] += (sg > 0);
+        mus = F.muE[d + e - 1][edge_index(P, d + e - 1, q3[0], q3[1], q3[2])];
         muE[sg > 0] = mus;
       }
       const double a = cup + mus * h;  // mu A / h with A = h^2
@@ -528,16 +576,14 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       else if (status == 1)
         ap += 2.0 * a;
     }
-    // explicit div(mu grad(u)^T), component d
+    // explicit div(mu grad(u)^T), component d (velocity differences; 1/h^2 once below)
     if (e == d) {
-      const double dR = (cd + 1 <= P.n[d]) ? (F.u[d][face_index(P.n, d, i + di, j + dj, k + dk)] - uf) * inv_h : 0.0;
-      const double dL = (cd - 1 >= 0) ? (uf - F.u[d][face_index(P.n, d, li, lj, lk)]) * inv_h : 0.0;
-      tt += (muR * dR - muL * dL) * inv_h;
+      const double dR = (cd + 1 <= P.n[d]) ? F.u[d][face_index(P.n, d, i + di, j + dj, k + dk)] - uf : 0.0;
+      const double dL = (cd - 1 >= 0) ? uf - F.u[d][face_index(P.n, d, li, lj, lk)] : 0.0;
+      tt += muR * dR - muL * dL;
     } else {
-      double ts = 0.0;
-      ts -= muE[0] * ((vRlo - vLlo) * inv_h);
-      ts += muE[1] * ((vRhi - vLhi) * inv_h);
-      tt += ts * inv_h;
+      tt -= muE[0] * (vRlo - vLlo);
+      tt += muE[1] * (vRhi - vLhi);
     }
   }
   for (int s = 2 * P.dim; s < 6; s++) anb[s * nf] = 0.0;
@@ -552,7 +598,7 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   else
     Sx -= V * Gp * uf;
   F.aP[d][f] = 1.0 / ap;  // stored as the reciprocal: every later use multiplies
-  F.rhs0[d][f] = Sx + V * (tt + Bf);
+  F.rhs0[d][f] = Sx + V * (tt * P.inv_h2 + Bf);
 }
 
 // H(u) = sum_nb a_nb u_nb + rhs0 of an unknown face.  A missing neighbour has
@@ -935,6 +981,19 @@ __global__ void k_normals(const StepDom* __restrict__ D, Work w) {
   }
 }
 
+__global__ void k_edge_mu(const StepDom* __restrict__ D, Work w) {
+  MDBS_DEPENDENT_ENTRY();
+  for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+    const int dm = work_domain(w, b);
+    const StepDom& S = D[dm];
+    const int lb = b - w.blk[dm];
+    for (int r = 0; r < w.rep; r++) {
+      const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
+      if (c < S.P.cells) b_edge_mu(S.P, S.F, c);
+    }
+  }
+}
+
 __global__ void k_curvature(const StepDom* __restrict__ D, Work w) {
   MDBS_DEPENDENT_ENTRY();
   for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
@@ -1041,6 +1100,7 @@ void launch_closures(const BatchPlan& B, cudaStream_t s) { BATCH_LAUNCH(K_PROPER
 
 void launch_properties(const BatchPlan& B, cudaStream_t s) {
   BATCH_LAUNCH(K_PROPERTIES, cells, k_properties);
+  BATCH_LAUNCH(K_EDGE_MU, cells, k_edge_mu);  // reads the viscosity the closures just formed
   BATCH_LAUNCH(K_NORMALS, cells, k_normals);
   BATCH_LAUNCH(K_CURVATURE, cells, k_curvature);
 }
