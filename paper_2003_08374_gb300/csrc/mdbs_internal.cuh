@@ -81,6 +81,7 @@ struct Fld {
   const double* iphiV;  // 1 / (phi V) (saturation updates)
   const double* iphif[3];  // 1 / phi_f, phi_f the mean porosity of a face's two cells
   const double* gphi[3];   // grad(phi^-2) at a face: component e of direction-d faces at e * nf[d] + f
+                           // (the components across the face's normal carry a factor 1/4)
   // state
   double* alpha;
   double* p;

@@ -526,6 +526,7 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
   const double at = V * rhof * (inv_phi * inv_dt);
   const double S = at * uf;  // advective form rho^{k+1} (v^{k+1} - v^k) / dt
   const double cconv = V * rhof * inv_phi * inv_phi * inv_h;
+  const double cconv4 = 0.25 * cconv;
   double ap = at + V * Df;
   double tt = 0.0;
   double vgrad = 0.0;  // v . grad(phi^-2) at the face
@@ -542,10 +543,13 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
       vRlo = F.u[e][face_index(P.n, e, ri, rj, rk)];
       vRhi = F.u[e][face_index(P.n, e, ri + ei, rj + ej, rk + ek)];
     }
-    const double w = (e == d) ? uf : 0.25 * (vLlo + vLhi + vRlo + vRhi);
+    // transverse: the sum of the four face velocities (4 w); the 1/4 sits in the static
+    // gradient and in cconv4 (scaling by a power of two is exact)
+    const double w = (e == d) ? uf : vLlo + vLhi + vRlo + vRhi;
     vgrad += w * gph[e * nf];
-    double wpos, wneg;
-    split_sign(w, wpos, wneg);
+    // upwind split of cconv w from its sign (cconv > 0): max(cconv w, 0), max(-cconv w, 0)
+    double cpos, cneg;
+    split_sign((e == d ? cconv : cconv4) * w, cpos, cneg);
     double muE[2] = {0.0, 0.0};  // edge viscosities of the two e-sides (e != d)
     for (int sg = -1; sg <= 1; sg += 2) {
       const int slot = 2 * e + (sg > 0);
@@ -557,7 +561,7 @@ __device__ __forceinline__ void b_momentum_assemble(const Prm& P, const Fld& F, 
         status = 0;
       else
         status = P.bc[2 * e + (sg > 0)] == kOutlet ? 2 : 1;
-      const double cup = cconv * (sg < 0 ? wpos : wneg);
+      const double cup = sg < 0 ? cpos : cneg;
       double mus;
       if (e == d) {
         mus = sg < 0 ? muL : muR;
@@ -870,7 +874,9 @@ __global__ void k_static_geometry(const StepDom* __restrict__ D, Work w) {
 // Static face data of the momentum equation (the porosity never changes): 1 / phi_f
 // with phi_f the mean of the face's two cells, and grad(phi^-2) at the face --
 // across it along its own axis, the mean of the two cells' central differences
-// along the others (zero components beyond the grid's dimension).
+// along the others, stored times 1/4 because the assembly multiplies it with the sum
+// (not the mean) of the four transverse face velocities (zero components beyond the
+// grid's dimension).
 __device__ __forceinline__ void b_static_faces(const Prm& P, const Fld& F, long long t) {
   int d, i, j, k;
   long long f;
@@ -890,7 +896,7 @@ __device__ __forceinline__ void b_static_faces(const Prm& P, const Fld& F, long 
                         ghost_read(F.iphi2, P.n, li - ei, lj - ej, lk - ek);
       const double gR = ghost_read(F.iphi2, P.n, i + ei, j + ej, k + ek) -
                         ghost_read(F.iphi2, P.n, i - ei, j - ej, k - ek);
-      g = (gL + gR) * (0.25 * inv_h);
+      g = 0.25 * ((gL + gR) * (0.25 * inv_h));  // times 1/4: the momentum assembly sums, not averages, w
     }
     const_cast<double*>(F.gphi[d])[e * nf + f] = g;
   }
