@@ -805,6 +805,7 @@ int mdbs_create(const mdbs_grid* grid, const double* porosity, const double* per
   P.inv_s_den = 1.0 / (P.a_pc_max - P.a_pc_irr);
   P.reg_m = 1e-8 / grid->h;
   P.inv_h2 = 1.0 / (grid->h * grid->h);
+  for (int d = 0; d < 3; d++) P.drho_g[d] = (P.rho_l - P.rho_g) * P.g[d];
   P.kr_m_int = (cl->kr_m >= 1.0 && cl->kr_m <= 8.0 && cl->kr_m == floor(cl->kr_m)) ? (int)cl->kr_m : 0;
   P.cfl = op->cfl;
   P.dt_max = op->dt_max;

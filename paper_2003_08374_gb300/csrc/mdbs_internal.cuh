@@ -64,6 +64,7 @@ struct Prm {
   double inv_s_den;           // 1/(a_pc_max - a_pc_irr), capillary saturation
   double reg_m;               // 1e-8/h, regularisation of |grad alpha| in the interface normal
   double inv_h2;              // 1/h^2
+  double drho_g[3];           // (rho_l - rho_g) g_d, the buoyancy drive of the porous relative flux
   int kr_m_int;              // kr exponent when it is an integer in [1, 8], else 0
   double cfl, dt_max;        // adaptive time step (cfl > 0)
   FastDiv dn0, dn1;          // division by n[0] and by n[1]

@@ -148,7 +148,7 @@ __device__ __forceinline__ double b_alpha_flux(const Prm& P, const Fld& F, long 
         // Q avl + (relative flux) = Q f_vl + A lambda drive: the Van Leer value of
         // alpha cancels, so porous faces do not form it
         const double fvl = van_leer(frac_flow(F, uc), frac_flow(F, dc), frac_flow(F, uu));
-        const double drive = (P.rho_l - P.rho_g) * P.g[d] + (F.pc[r] - F.pc[l]) * inv_h;
+        const double drive = P.drho_g[d] + (F.pc[r] - F.pc[l]) * inv_h;
         hi = Q * fvl;
         if (nz(drive)) {
           // liquid from the cell the drive pushes it out of, gas from the other
@@ -355,10 +355,10 @@ __device__ __forceinline__ void b_properties(const Prm& P, const Fld& F, long lo
     pc = P.pc0 * pow(pow(s, -1.0 / P.pc_m) - 1.0, 1.0 - P.pc_m);
   F.Ml[c] = Ml;
   F.Mg[c] = Mg;
-  // a division, not Ml * (1/M): with no gas mobility f must be exactly 1, or a
-  // saturated region would carry a rounding-size antidiffusive flux
-  F.fw[c] = Ml / M;  // M > 0 in porous cells: k0 > 0 and k_rl + k_rg > 0
-  const double inv_M = 1.0 / M;
+  const double inv_M = 1.0 / M;  // M > 0 in porous cells: k0 > 0 and k_rl + k_rg > 0
+  // f = M_l / M, exactly 1 where the gas has no mobility (M_l (1/M) can be 1 - 1 ulp
+  // there, and a saturated region would carry a rounding-size antidiffusive flux)
+  F.fw[c] = nz(Mg) ? Ml * inv_M : 1.0;
   F.drag[c] = inv_M;
   // rho* of Eq. 45, or Appendix B's saturation-weighted rho (its buoyancy remainder
   // c_f (rho_l - rho_g) g joins the porous capillary force)
