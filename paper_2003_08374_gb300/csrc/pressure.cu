@@ -886,7 +886,10 @@ __global__ void k_zero(const CgDom* __restrict__ C, Work w, int l, int rev, int 
 // only the colour-0 cells' residuals are formed and summed: half the FP64 work, the
 // same V-cycle operator.
 template <typename R, bool COH = false>
-__device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci, int mask) {
+// fold: also store the coarse level's zero-guess colour-0 update x = b / diag (the
+// first pre-smoothing half sweep of that level, which then is not launched)
+__device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level<R>& Co, long long ci, int mask,
+                                                 int fold) {
   int Q[3];
   decode_pos(Co, ci, Q[0], Q[1], Q[2]);
   int lo[3], hi[3];
@@ -905,10 +908,11 @@ __device__ __forceinline__ void b_resid_restrict(const Level<R>& Fi, const Level
         s += ldc<COH>(Fi.b + c) - ax;
       }
   Co.b[ci] = s;
+  if (fold && !((Q[0] + Q[1] + Q[2]) & 1)) Co.x[ci] = s * Co.dinv[ci];
 }
 
 template <typename R>
-__global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int rev, int sel, int mask) {
+__global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int rev, int sel, int mask, int fold) {
   MDBS_DEPENDENT_ENTRY();
   FOR_WORK_DIR(w, rev)
     const CgDom& G = C[dm];
@@ -918,7 +922,7 @@ __global__ void k_resid_restrict(const CgDom* __restrict__ C, Work w, int l, int
     if (sel) Fi.x = Fi.x2;  // the buffer holding the fine iterate
     for (int r = 0; r < w.rep; r++) {
       const long long c = ((long long)lb * w.rep + r) * blockDim.x + threadIdx.x;
-      if (c < L[l + 1].cells) b_resid_restrict(Fi, L[l + 1], c, mask);
+      if (c < L[l + 1].cells) b_resid_restrict(Fi, L[l + 1], c, mask, fold);
     }
   }
 }
@@ -1340,7 +1344,7 @@ __global__ void __launch_bounds__(kCoopThreads, 1)
       for (int r = 0; r < w.rep; r++) {
         const long long c = ((long long)lb * w.rep + r) * kBlock + tid;
         if (what == 0) {
-          if (c < Lc.cells) b_resid_restrict<R, true>(Lf, Lc, c, nu1 > 0 ? 1 : 0);
+          if (c < Lc.cells) b_resid_restrict<R, true>(Lf, Lc, c, nu1 > 0 ? 1 : 0, 0);
         } else if (c < Lf.cells) {
           if (what == 1)
             Lf.x[c] = R(0);
@@ -2082,12 +2086,23 @@ static void vcycle(const BatchPlan& B, int nu1, int nu2, int cs, Dirs& D, cudaSt
   // the levels between the finest and the tail in one cooperative launch (split sweeps)
   const bool coop = B.coarse_coop && B.max_first >= 2 && !fused_sweeps<R>(B) && B.coop_grid > 0;
   const int batched_end = coop ? 1 : B.max_first;
+  // FP32 levels, split sweeps: the restriction into a batched coarse level also stores
+  // that level's zero-guess colour-0 half sweep (x = b / diag), which is then not
+  // launched (a domain whose tail starts at that level recomputes the same values
+  // there).  Measured: 0.5 % off the mixed step; the FP64 restriction is FP64-pipe
+  // bound and the step got 0.9 % slower, so FP64 levels keep the separate sweep.
+  const bool fold = nu1 > 0 && !fused_sweeps<R>(B) && std::is_same<R, float>::value;
   for (int l = 0; l < batched_end; l++) {
     if (nu1 == 0)
       MDBS_LAUNCH(K_ZERO, grid_of(B, B.lfine[l]), kBlock, s, k_zero<R>, B.cg, B.lfine[l], l, D.next(l), cur(0));
-    for (int it = 0; it < nu1; it++) sweep<R>(B, l, 0, it == 0, cur(it), D, s);
+    for (int it = 0; it < nu1; it++) {
+      if (it == 0 && l > 0 && fold)
+        smooth_half<R>(B, l, 1, 0, D, s);  // colour 0 came with the restriction
+      else
+        sweep<R>(B, l, 0, it == 0, cur(it), D, s);
+    }
     MDBS_LAUNCH(l == 0 ? K_RESTRICT0 : K_RESTRICTC, grid_of(B, B.lcoarse[l]), kBlock, s, k_resid_restrict<R>, B.cg,
-                B.lcoarse[l], l, D.next(l), cur(nu1), nu1 > 0 ? 1 : 0);
+                B.lcoarse[l], l, D.next(l), cur(nu1), nu1 > 0 ? 1 : 0, (fold && l + 1 < batched_end) ? 1 : 0);
   }
   if (coop) {
     const size_t smem = tail_smem_bytes(B, sizeof(R), 1);
